@@ -1,0 +1,238 @@
+/*
+ * apsm_oracle.c -- plain FP64 CPU oracle of the APSM partially linear multiuser
+ * detector of arXiv 2201.05024 (Sec. II).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this file; the product (the CUDA library and its
+ * binding) never does, and this file shares no code, header, table or helper
+ * with it.
+ *
+ * It is deliberately slow and literal:
+ *   - vectors are the real split of Sec. II-D, formed explicitly
+ *     (x_{2t} = [Re r(t); Im r(t)], x_{2t+1} = [Im r(t); -Re r(t)],
+ *      b_{2t} = Re s(t), b_{2t+1} = Im s(t));
+ *   - Gaussian kernels use the direct difference ||u - v||^2 (Sec. II-A);
+ *   - every window prediction is recomputed from the full expansion of f_n at
+ *     every step (no incremental update, no Gram trick);
+ *   - all projections of one step use the same f_n (Eq. apsm);
+ *   - one user at a time, one step at a time, in FP64.
+ *
+ * Readings of points the paper leaves open (each is a parameter or a choice
+ * made once here):
+ *   - relaxation mu multiplies the projection step (mu = 1 is Eq. apsm as printed);
+ *   - weights q_j are uniform, 1/|J_n|;
+ *   - W counts real-split samples n (Sec. II-D index);
+ *   - the Gaussian dictionary holds at most D entries, one entry per complex
+ *     pilot r(t) carrying both centres x_{2t}, x_{2t+1}; when full, the oldest
+ *     entry (both centres and their coefficients) is dropped before the new one
+ *     joins with zero coefficients; the linear part keeps the dropped samples'
+ *     contribution because the linear dictionary is the fixed Euclidean basis
+ *     (Sec. II-D, decomposition of f_n); 2D > W is required;
+ *   - f_0 has no Gaussian part; its linear part w0 is given (zero by default);
+ *   - w_G = 1 - w_L;
+ *   - kappa(x_j, x_j) = 0 (only possible when w_L = 1 and x_j = 0) gives beta = 0;
+ *   - |e| == eps lies inside the hyperslab (Eq. beta, middle case).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int M;          /* receive antennas; real-split dimension is 2M           */
+    int K;          /* users                                                  */
+    int W;          /* window size |J_n| for n >= W-1 (Sec. II-D)             */
+    int D;          /* dictionary capacity in entries (complex pilots)        */
+    double sigma;   /* Gaussian kernel width: exp(-||u-v||^2 / (2 sigma^2))   */
+    double mu;      /* relaxation of the concurrent projection step           */
+    double eps;     /* hyperslab half-width epsilon (Eq. convex_set)          */
+    double w_L;     /* weight of the linear kernel; w_G = 1 - w_L (Fact 1)    */
+} apsm_oracle_params;
+
+/* Real split of one complex vector r (interleaved re,im, length M) -- Sec. II-D. */
+static void real_split(int M, const double *r, double *x1, double *x2)
+{
+    for (int m = 0; m < M; ++m) {
+        double re = r[2 * m], im = r[2 * m + 1];
+        x1[m] = re;      x1[M + m] = im;    /* r1 = [Re r; Im r]  */
+        x2[m] = im;      x2[M + m] = -re;   /* r2 = [Im r; -Re r] */
+    }
+}
+
+/* Linear kernel kappa_L(u, v) = u^T v -- Sec. II-A. */
+static double kappa_lin(int L, const double *u, const double *v)
+{
+    double s = 0.0;
+    for (int i = 0; i < L; ++i) s += u[i] * v[i];
+    return s;
+}
+
+/* Gaussian kernel kappa_G(u, v) = exp(-||u - v||^2 / (2 sigma^2)) -- Sec. II-A. */
+static double kappa_gauss(int L, const double *u, const double *v, double sigma)
+{
+    double d2 = 0.0;
+    for (int i = 0; i < L; ++i) {
+        double d = u[i] - v[i];
+        d2 += d * d;
+    }
+    return exp(-d2 / (2.0 * sigma * sigma));
+}
+
+/* f(x) = w_L <w, x> + w_G sum_i gamma_i kappa_G(c_i, x): the value <f, kappa(x, .)>_H of an
+ * element of the sum space H = H_L + H_G (Fact 1, Eq. sum_inner_product, with the
+ * decomposition f_n = f_L,n + f_G,n of Sec. II-D).  gamma has stride gstride. */
+static double eval_f(int L, const double *w, int n_c, const double *cent, const double *gamma,
+                     int gstride, const double *x, double sigma, double w_L)
+{
+    double lin = kappa_lin(L, w, x);
+    double gs = 0.0;
+    for (int i = 0; i < n_c; ++i)
+        gs += gamma[(size_t)i * gstride] * kappa_gauss(L, cent + (size_t)i * L, x, sigma);
+    return w_L * lin + (1.0 - w_L) * gs;
+}
+
+/* Real-split centres of complex dictionary entries: entry t holds x_{2t} = r1(t) and
+ * x_{2t+1} = r2(t).  entries [n][M][2] -> centres [2n][2M]. */
+void apsm_oracle_centres(int M, int n, const double *entries, double *centres)
+{
+    for (int t = 0; t < n; ++t)
+        real_split(M, entries + (size_t)t * 2 * M, centres + (size_t)(2 * t) * 2 * M,
+                   centres + (size_t)(2 * t + 1) * 2 * M);
+}
+
+/* Evaluate f^k at real vectors x[q] for q in [q0, q1):
+ *   y[q][k] = w_L w_k^T x_q + w_G sum_i gamma[i][k] kappa_G(c_i, x_q).
+ * cent [n_c][2M], gamma [n_c][K], w [K][2M], x [n_x][2M], y [n_x][K]. */
+void apsm_oracle_eval(const apsm_oracle_params *p, int n_c, const double *cent, const double *gamma,
+                      const double *w, int q0, int q1, const double *x, double *y)
+{
+    const int L = 2 * p->M, K = p->K;
+    for (int q = q0; q < q1; ++q)
+        for (int k = 0; k < K; ++k)
+            y[(size_t)q * K + k] = eval_f(L, w + (size_t)k * L, n_c, cent, gamma + k, K,
+                                          x + (size_t)q * L, p->sigma, p->w_L);
+}
+
+/* Detection (Sec. II-D, Sec. III-B): for complex data vectors r[q] (interleaved [N][M][2]),
+ * y[q][k][0] = f^k(r1(q)), y[q][k][1] = f^k(r2(q)); the complex soft estimate of user k is
+ * g^k(r) = f^k(r1) + i f^k(r2).  Queries [q0, q1). */
+void apsm_oracle_detect(const apsm_oracle_params *p, int n_c, const double *cent,
+                        const double *gamma, const double *w, int q0, int q1,
+                        const double *rx, double *y)
+{
+    const int M = p->M, L = 2 * M, K = p->K;
+    double *x1 = (double *)malloc(sizeof(double) * (size_t)L);
+    double *x2 = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int q = q0; q < q1; ++q) {
+        real_split(M, rx + (size_t)q * 2 * M, x1, x2);
+        for (int k = 0; k < K; ++k) {
+            y[((size_t)q * K + k) * 2 + 0] =
+                eval_f(L, w + (size_t)k * L, n_c, cent, gamma + k, K, x1, p->sigma, p->w_L);
+            y[((size_t)q * K + k) * 2 + 1] =
+                eval_f(L, w + (size_t)k * L, n_c, cent, gamma + k, K, x2, p->sigma, p->w_L);
+        }
+    }
+    free(x1);
+    free(x2);
+}
+
+/*
+ * Training (Eq. apsm with Eq. beta, window J_n of Sec. II-D), users k in [k0, k1).
+ *
+ * Inputs:  rx [P][M][2] pilots, sym [P][K][2] pilot symbols, w0 [K][2M] or NULL.
+ *          n_steps = number of real-split steps n = 0 .. n_steps-1 (<= 2P; < 0 means 2P).
+ * Outputs: w_out [K][2M]            linear coefficients (rows k0..k1-1 written);
+ *          gamma_out [2D][K]        Gaussian coefficients of the alive centres in age order
+ *                                   (columns k0..k1-1 written);
+ *          alive_out [2]            first alive entry, number of alive entries (written when k0 == 0);
+ *          case_log [n_steps][W][K] (nullable) -1: e < -eps, 0: |e| <= eps, +1: e > eps, for window
+ *                                   slot o = j - n + W - 1 (slots with j < 0 are left untouched);
+ *          margin_log [n_steps][W][K] (nullable) | |e| - eps |;
+ *          forced [n_steps][W][K]   (nullable) a value in {-1, 0, 1} forces that case for the slot
+ *                                   (replay of a run that took another branch at a tie); any other
+ *                                   value leaves the slot free.
+ * Returns 0, or -1 on invalid arguments / allocation failure.
+ */
+int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const double *rx,
+                      const double *sym, const double *w0, int k0, int k1, double *w_out,
+                      double *gamma_out, int *alive_out, signed char *case_log,
+                      double *margin_log, const signed char *forced)
+{
+    const int M = p->M, L = 2 * M, K = p->K, W = p->W, D = p->D;
+    if (M < 1 || K < 1 || W < 1 || D < 1 || P < 0 || 2 * D <= W || p->sigma <= 0.0) return -1;
+    if (n_steps < 0 || n_steps > 2 * P) n_steps = 2 * P;
+    const double w_G = 1.0 - p->w_L;
+
+    /* Real-split training samples (x_n, b_n), n = 2t + l (Sec. II-D). */
+    double *x = (double *)malloc(sizeof(double) * (size_t)(2 * P + 1) * L);
+    double *g = (double *)malloc(sizeof(double) * (size_t)(2 * P + 1));
+    double *beta = (double *)malloc(sizeof(double) * (size_t)W);
+    if (!x || !g || !beta) { free(x); free(g); free(beta); return -1; }
+    for (int t = 0; t < P; ++t)
+        real_split(M, rx + (size_t)t * 2 * M, x + (size_t)(2 * t) * L, x + (size_t)(2 * t + 1) * L);
+
+    int first = 0, t_last = 0;
+    for (int k = k0; k < k1; ++k) {
+        double *w = w_out + (size_t)k * L;
+        for (int i = 0; i < L; ++i) w[i] = w0 ? w0[(size_t)k * L + i] : 0.0;
+        for (int i = 0; i < 2 * P + 1; ++i) g[i] = 0.0;
+        first = 0;
+        t_last = 0;
+        for (int n = 0; n < n_steps; ++n) {
+            const int t = n / 2;
+            t_last = t;
+            /* A new pilot t arrives at n = 2t: drop the oldest entry if the dictionary is full;
+             * entry t joins with both centres at zero coefficient. */
+            if (n % 2 == 0 && t - first == D) first += 1;
+            const int c_lo = 2 * first, c_hi = 2 * t + 2;   /* alive centres [c_lo, c_hi) */
+            const int j0 = (n >= W - 1) ? n - W + 1 : 0;   /* J_n = [j0, n] */
+            const int nJ = n - j0 + 1;
+            const double q = 1.0 / (double)nJ;
+            /* All projections of this step are taken from the same f_n (Eq. apsm). */
+            for (int j = j0; j <= n; ++j) {
+                const double *xj = x + (size_t)j * L;
+                const double bj = sym[((size_t)(j / 2) * K + k) * 2 + (j % 2)];
+                const double y = eval_f(L, w, c_hi - c_lo, x + (size_t)c_lo * L, g + c_lo, 1, xj,
+                                        p->sigma, p->w_L);
+                const double e = y - bj;
+                const double kjj = p->w_L * kappa_lin(L, xj, xj) + w_G;   /* kappa(r_j, r_j) */
+                int cs = (e < -p->eps) ? -1 : (e > p->eps ? 1 : 0);
+                const int o = j - n + W - 1;
+                const size_t li = ((size_t)n * W + o) * K + k;
+                if (forced && (forced[li] == -1 || forced[li] == 0 || forced[li] == 1)) cs = forced[li];
+                double b = 0.0;                                                    /* Eq. beta */
+                if (kjj != 0.0) {
+                    if (cs < 0) b = (bj - y - p->eps) / kjj;
+                    else if (cs > 0) b = (bj - y + p->eps) / kjj;
+                }
+                beta[j - j0] = b;
+                if (case_log) case_log[li] = (signed char)cs;
+                if (margin_log) margin_log[li] = fabs(fabs(e) - p->eps);
+            }
+            /* f_{n+1} = f_n + mu sum_j q beta_j kappa(x_j, .): coefficient of centre j and the
+             * linear dictionary (Sec. II-D: kappa_L(x_j, .) = sum_m [x_j]_m kappa_L(e_m, .)). */
+            for (int j = j0; j <= n; ++j) {
+                const double a = p->mu * q * beta[j - j0];
+                g[j] += a;
+                const double *xj = x + (size_t)j * L;
+                for (int i = 0; i < L; ++i) w[i] += a * xj[i];
+            }
+        }
+        if (n_steps == 0) { first = 0; t_last = -1; }
+        const int n_alive = t_last - first + 1;
+        for (int i = 0; i < 2 * n_alive; ++i) gamma_out[(size_t)i * K + k] = g[2 * first + i];
+    }
+    if (k0 == 0 && alive_out) {
+        if (k1 <= k0) {   /* no user trained: still report the dictionary bookkeeping */
+            first = 0;
+            t_last = (n_steps > 0) ? (n_steps - 1) / 2 : -1;
+            for (int n = 0; n < n_steps; n += 2)
+                if (n / 2 - first == D) first += 1;
+        }
+        alive_out[0] = first;
+        alive_out[1] = (n_steps > 0) ? t_last - first + 1 : 0;
+    }
+    free(x);
+    free(g);
+    free(beta);
+    return 0;
+}
