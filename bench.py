@@ -1,0 +1,322 @@
+"""Benchmark of the APSM hot path: one step = train on P pilots + detect N data vectors.
+
+Default workload: 16 antennas, 6 QPSK users, 1024 pilots, window 16, dictionary cap 1024,
+65536 data vectors, sigma 0.5, mu 0.5, eps 0.01, w_L 0.5, SNR 10 dB (synthetic, seeded).
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead (bounded sample).
+
+Multi-GPU (torchrun): every rank trains and detects its own independent instance (a different
+seed); no data-path collective; value = all ranks' detected vectors / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "APSM symbol-vectors/s detect + pilot updates/s train; % roofline; err vs FP64"
+WORKLOAD = dict(M=16, K=6, P=1024, W=16, D=1024, N=65536, sigma=0.5, mu=0.5, eps=0.01, w_L=0.5, snr_db=10.0)
+L2_FLUSH_BYTES = 256 << 20
+# Nominal FP32 FMA-pipe peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+ORACLE_DETECT_SAMPLE = 4096
+
+# DRAM bytes per launch of the detection kernel from one ncu capture, valid only for the kernel
+# source with this digest (a changed kernel reports null until it is re-captured).
+DETECT_TRAFFIC = {"digest": None, "bytes_per_launch": None}
+
+
+def workload_name(w):
+    return (f"APSM 16x6 QPSK paper-scale: M={w['M']} K={w['K']} P={w['P']} W={w['W']} D={w['D']} "
+            f"N={w['N']} sigma={w['sigma']} mu={w['mu']} eps={w['eps']} w_L={w['w_L']} SNR={w['snr_db']}dB")
+
+
+def detect_flops(w, n_entries):
+    """Algorithmic FP32 flops of one detection launch: per (query, entry) pair one complex inner
+    product (4M FMA), three exponent arguments (3 FMA) and the coefficient accumulation (4K FMA)."""
+    return 2.0 * (4 * w["M"] + 4 * w["K"] + 3) * w["N"] * n_entries
+
+
+def kernel_digest():
+    h = hashlib.sha256()
+    for f in ("detect_f32.cuh", "apsm_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2201_05024_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, r[4:8]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_oracle(w, inst, sample, threads=None):
+    """Time the FP64 oracle: full training, detection of `sample` queries."""
+    import oracle
+    op = oracle.Params(M=w["M"], K=w["K"], W=w["W"], D=w["D"], sigma=w["sigma"], mu=w["mu"], eps=w["eps"],
+                       w_L=w["w_L"])
+    t0 = time.perf_counter()
+    st = oracle.train(op, inst.rx_pilot, inst.sym_pilot, threads=threads)
+    t1 = time.perf_counter()
+    ref = oracle.detect(op, st, inst.rx_data[sample], threads=threads)
+    t2 = time.perf_counter()
+    return st, ref, t1 - t0, t2 - t1
+
+
+def oracle_step_rate(w, t_train, t_detect, n_sample):
+    step = t_train + t_detect * (w["N"] / n_sample)
+    return w["N"] / step, step
+
+
+def reference_arm(args, w):
+    from paper_2201_05024_gb300 import synth
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    inst = synth.make_instance(w["M"], w["K"], w["P"], w["N"], w["snr_db"], instance=0)
+    sample = np.arange(min(ORACLE_DETECT_SAMPLE, w["N"]))
+    cores = oracle.default_threads()
+    for _ in range(args.warmup):
+        run_oracle(w, inst, sample[:256])
+    times = []
+    for _ in range(args.steps):
+        _, _, tt, td = run_oracle(w, inst, sample)
+        times.append(oracle_step_rate(w, tt, td, len(sample))[1])
+    step = sum(times) / len(times)
+    value = w["N"] / step
+    desc = (f"full training ({w['P']} pilots, {w['K']} users on {min(cores, w['K'])} threads) + detection of "
+            f"{len(sample)} of {w['N']} vectors on {cores} threads, extrapolated per vector")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "symbol-vectors/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": "symbol-vectors/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "symbol-vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-oracle", action="store_true", help="skip the CPU baseline and FP64 error legs")
+    args = ap.parse_args()
+    w = dict(WORKLOAD)
+    if args.impl == "reference":
+        reference_arm(args, w)
+        return
+
+    import torch
+    from paper_2201_05024_gb300 import apsm, build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    apsm.load_library()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    inst = synth.make_instance(w["M"], w["K"], w["P"], w["N"], w["snr_db"], instance=rank)
+    gp = apsm.Params(M=w["M"], K=w["K"], window=w["W"], dict_cap=w["D"], sigma=w["sigma"], mu=w["mu"],
+                     eps=w["eps"], w_L=w["w_L"])
+    rp = torch.from_numpy(inst.rx_pilot).to(dev)
+    sp = torch.from_numpy(inst.sym_pilot).to(dev)
+    rd = torch.from_numpy(inst.rx_data).to(dev)
+    st = apsm.State(gp, device=dev)
+    ws = torch.empty((max(apsm.train_workspace_bytes(gp, w["P"]), 1),), dtype=torch.uint8, device=dev)
+    soft = torch.empty((w["N"], w["K"]), dtype=torch.complex64, device=dev)
+    hard = torch.empty((w["N"], w["K"]), dtype=torch.uint8, device=dev)
+    flush = torch.empty((L2_FLUSH_BYTES // 4,), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        apsm.train(gp, rp, sp, st, workspace=ws)
+        apsm.detect(gp, st, rd, soft=soft, hard=hard)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = apsm.launch_count()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))           # L2 flush between timed steps (outside the events)
+        ev[i][0].record(stream)
+        apsm.train(gp, rp, sp, st, workspace=ws)
+        ev[i][1].record(stream)
+        apsm.detect(gp, st, rd, soft=soft, hard=hard)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    launches = apsm.launch_count() - launches0
+    clocks = sampler.stop()
+    t_train = [a.elapsed_time(b) for a, b, _ in ev]
+    t_detect = [b.elapsed_time(c) for _, b, c in ev]
+    t_step = sum(t_train) + sum(t_detect)  # ms over K steps
+    mean_train = sum(t_train) / len(t_train)
+    mean_detect = sum(t_detect) / len(t_detect)
+    if dist is not None:
+        t = torch.tensor([t_step, mean_train, mean_detect], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step, mean_train, mean_detect = t.tolist()
+    ms_per_step = t_step / args.steps
+    value = world * w["N"] / (ms_per_step / 1e3)
+    assert apsm.read_status(st) == 0, "device status word set during the benchmark"
+
+    # ---- end to end through the public API on host buffers (pinned), copies inside the timing
+    hp = torch.from_numpy(inst.rx_pilot).pin_memory()
+    hs = torch.from_numpy(inst.sym_pilot).pin_memory()
+    hd = torch.from_numpy(inst.rx_data).pin_memory()
+    for _ in range(2):
+        apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
+    e2e_times = []
+    for _ in range(max(3, min(args.steps, 10))):
+        flush.fill_(0.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        soft_h, hard_h = apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_step = sum(e2e_times) / len(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = t.item()
+    h2d = hp.numel() * 8 + hs.numel() * 8 + hd.numel() * 8
+    d2h = soft_h.numel() * 8 + hard_h.numel()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    n_entries = int(st.meta[0].item())
+    achieved = detect_flops(w, n_entries) / (mean_detect / 1e3) / 1e12
+    peak = FP32_PEAK_TFLOPS
+    traffic = DETECT_TRAFFIC["bytes_per_launch"] if DETECT_TRAFFIC["digest"] == kernel_digest() else None
+    out = {
+        "metric": METRIC, "value": value, "unit": "symbol-vectors/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(w), "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"independent instance per GPU x{world}", "step": "train P pilots + detect N vectors"},
+        "detect": {"value": world * w["N"] / (mean_detect / 1e3), "unit": "symbol-vectors/s",
+                   "ms": mean_detect},
+        "train": {"value": world * w["P"] * w["K"] / (mean_train / 1e3), "unit": "pilot-updates/s",
+                  "ms": mean_train, "us_per_pilot": mean_train * 1e3 / w["P"]},
+        "roofline": {"kernel": "detect_f32_kernel<16,6,2>", "bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": "derived FP32 FMA pipe at max SM clock"},
+        "gpu_launches": int(launches),
+        "wall_s_timed": wall,
+        "e2e": {"value": world * w["N"] / e2e_step, "unit": "symbol-vectors/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_step * 1e3},
+        "clocks": clocks,
+    }
+    if not args.no_oracle:
+        sample = np.random.default_rng(0).choice(w["N"], ORACLE_DETECT_SAMPLE, replace=False)
+        import oracle
+        st_ref, ref, tt, td = run_oracle(w, inst, sample)
+        val_cpu, _ = oracle_step_rate(w, tt, td, len(sample))
+        cores = oracle.default_threads()
+        out["cpu_baseline"] = {
+            "value": val_cpu, "unit": "symbol-vectors/s", "cores": cores, "kind": "oracle",
+            "sample": (f"full FP64 training ({w['P']} pilots, users on {min(cores, w['K'])} threads, {tt:.2f} s) + "
+                       f"detection of {len(sample)} sampled vectors ({td:.2f} s), extrapolated to {w['N']}")}
+        y = soft.cpu().numpy()[sample].astype(np.complex128)
+        cr = np.stack([ref.real, ref.imag])
+        cy = np.stack([y.real, y.imag])
+        rms = float(np.sqrt(np.mean(cr ** 2)))
+        err = np.abs(cy - cr) / np.maximum(np.abs(cr), rms)
+        h_ref = oracle.hard_qpsk(ref)
+        out["err_vs_fp64"] = {"max_scaled": float(err.max()), "rms_scaled": float(np.sqrt(np.mean(err ** 2))),
+                              "sample": len(sample),
+                              "ser_gpu": float(np.mean(hard.cpu().numpy()[sample] != inst.idx_data[sample])),
+                              "ser_oracle": float(np.mean(h_ref != inst.idx_data[sample]))}
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * apsm.h -- C ABI of the GB300 (sm_103a) APSM multiuser detector library (libapsm_gb300.so).
+ *
+ * The method is the adaptive projected subgradient method (APSM) for partially linear
+ * multiuser detection of arXiv 2201.05024:
+ *   - filters live in the weighted sum space H = H_L + H_G with reproducing kernel
+ *     kappa = w_L kappa_L + w_G kappa_G (Sec. II-A/B, Fact 1), kappa_L(u,v) = u^T v and
+ *     kappa_G(u,v) = exp(-||u - v||^2 / (2 sigma^2));
+ *   - a complex received vector r in C^M is processed as the two real vectors
+ *     r1 = [Re r; Im r] and r2 = [Im r; -Re r]; one real filter f per user gives the
+ *     complex soft symbol g(r) = f(r1) + i f(r2) (Sec. II-D);
+ *   - training runs the concurrent hyperslab projections of Eq. apsm / Eq. beta over the
+ *     window J_n of the last W real-split samples (Sec. II-D); detection evaluates the trained
+ *     expansion (Sec. III-B).
+ *
+ * Conventions shared by every entry point:
+ *   - Complex arrays are interleaved (re, im) float32 pairs (the layout of torch.complex64 /
+ *     C99 float _Complex).  Every pointer whose comment says "device" must point to memory of
+ *     the current CUDA device; the caller allocates and owns all of it -- the library keeps no
+ *     allocation between calls and makes none inside them.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work on it and
+ *     return without synchronising; results are valid once the stream has reached them.
+ *   - Host-side argument errors return at once, before any CUDA call.  A device-side error
+ *     (a bounded wait that ran out) is written to meta[3] of the state and reported by
+ *     apsm_read_status().
+ *   - No C++ exception crosses this boundary.  The library runs on sm_103 devices only and
+ *     returns APSM_ERR_NOT_SM103 elsewhere; it has no CPU fallback.
+ *   - Results are deterministic: no floating-point atomics, fixed reduction orders.
+ */
+#ifndef APSM_GB300_H
+#define APSM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    APSM_OK = 0,
+    APSM_ERR_INVALID_ARG = 1,  /* a size, pointer or parameter outside its documented range   */
+    APSM_ERR_UNSUPPORTED = 2,  /* a valid shape this build has no kernel for (see apsm_params) */
+    APSM_ERR_CUDA = 3,         /* a CUDA runtime call failed (no device, launch failure, ...)  */
+    APSM_ERR_TIMEOUT = 4,      /* a device-side bounded wait ran out (reported via meta[3])    */
+    APSM_ERR_NOT_SM103 = 5,    /* the current device is not compute capability 10.3            */
+    APSM_ERR_WORKSPACE = 6     /* the workspace passed is smaller than the size queried        */
+} apsm_status;
+
+typedef enum { APSM_FP32 = 0, APSM_BF16 = 1, APSM_FP16 = 2 } apsm_dtype;
+
+/*
+ * Algorithm parameters (Sec. II-D and Sec. V of the paper; the readings of open points are
+ * stated per field).
+ *   M        antennas, i.e. complex dimension of r(t); the real-split dimension is 2M.
+ *            Supported: 2, 4, 8, 16, 32, 64.
+ *   K        users (one filter per user, all trained on the same received vectors, Sec. III-B).
+ *            Supported: 1..16.
+ *   window   W >= 1: number of hyperslabs projected concurrently, counted in real-split samples
+ *            (J_n = {n-W+1, .., n}, Sec. II-D).  Supported: 1..128.
+ *   dict_cap D: Gaussian dictionary capacity in entries; one entry is one complex pilot r(t)
+ *            and carries both centres r1(t), r2(t).  The paper's dictionary grows without
+ *            bound; here the oldest entry is dropped (FIFO) once D are held.  Requires 2D > W.
+ *   sigma    Gaussian kernel width sigma > 0 (kappa_G uses 2 sigma^2; the paper's default
+ *            variance sigma^2 = 0.05).
+ *   mu       relaxation of the projection step, 0 < mu <= 2; mu = 1 is Eq. apsm as printed.
+ *   eps      hyperslab half-width epsilon >= 0 (Eq. convex_set).
+ *   w_L      weight of the linear kernel in [0, 1]; the Gaussian weight is w_G = 1 - w_L.
+ *   dtype    apsm_dtype of the detection contractions; training always runs in FP32.
+ */
+typedef struct {
+    int32_t M;
+    int32_t K;
+    int32_t window;
+    int32_t dict_cap;
+    float sigma;
+    float mu;
+    float eps;
+    float w_L;
+    int32_t dtype;
+} apsm_params;
+
+/*
+ * Detector state: the trained filters f^k of all users (Sec. II-D decomposition
+ * f_n = f_L,n + f_G,n).  All DEVICE pointers, caller-allocated with the sizes below, where
+ * A = apsm_dict_alloc() >= dict_cap.
+ *   dict       [A][M] complex  ring buffer of dictionary entries r(t); entry t sits in slot t % D
+ *   dict_norm  [A]     float   ||r(t)||^2 of each slot
+ *   gamma      [A][2][K] float Gaussian coefficients of centre r1(t) (index 0) and r2(t)
+ *                               (index 1), unweighted (w_G is applied when evaluating)
+ *   clin       [M][K] complex  linear part as complex filter c_k = w_k[0:M] + i w_k[M:2M], so
+ *                               that w_k^T r1 = Re(c_k^H r) and w_k^T r2 = Im(c_k^H r)
+ *                               (unweighted: w_L is applied when evaluating).
+ *   meta       [4] int32       [0] entries held, [1] slot of the oldest entry,
+ *                               [2] pilots consumed, [3] device status (apsm_status code)
+ * Slots at or beyond meta[0] are never read by the kernels.
+ */
+typedef struct {
+    float *dict;
+    float *dict_norm;
+    float *gamma;
+    float *clin;
+    int32_t *meta;
+} apsm_state;
+
+/* Number of dictionary slots A (>= dict_cap) the state arrays must hold. */
+apsm_status apsm_dict_alloc(const apsm_params *p, int32_t *dict_alloc);
+
+/* Bytes of device workspace apsm_train needs for P pilots (0 is possible). */
+apsm_status apsm_train_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes);
+
+/*
+ * Training (Eq. apsm with Eq. beta over the window J_n, Sec. II-D; Fig. training of Sec. III-B).
+ * Runs the recurrence over the 2P real-split samples of P pilots, starting from f_0 whose
+ * linear part is clin0 (zero when NULL; Sec. I/II-D: f_0 is arbitrary, e.g. a conventional
+ * linear filter) and whose Gaussian part is empty; on return (stream order) the state holds
+ * f_{2P}: at most D entries, their coefficients, clin and meta.  Every state array is
+ * overwritten, so a state can be retrained without clearing it.
+ *   rx_pilot   device [P][M] complex  received pilot vectors r(t)
+ *   sym_pilot  device [P][K] complex  transmitted pilot symbols b_k(t) (targets: b_{2t} = Re,
+ *                                     b_{2t+1} = Im, Sec. II-D)
+ *   P          pilots, >= 0
+ *   clin0      device [M][K] complex, initial linear filter, or NULL for zero; may alias st->clin
+ *   st         state (output)
+ *   workspace  device scratch of at least apsm_train_workspace_bytes(p, P) bytes (may be NULL
+ *              when that size is 0), 256-byte aligned
+ *   case_log   optional device [2P][W][K] int8: for step n and window slot o (sample
+ *              j = n - W + 1 + o) the branch of Eq. beta taken: -1 (residual < -eps),
+ *              0 (inside the slab), +1 (residual > eps); slots with j < 0 are left untouched.
+ * Errors: APSM_ERR_INVALID_ARG (null pointer, P < 0, parameter out of range, 2D <= W),
+ * APSM_ERR_UNSUPPORTED (M, K or W outside the supported sets), APSM_ERR_WORKSPACE,
+ * APSM_ERR_NOT_SM103, APSM_ERR_CUDA.
+ */
+apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                       const float *clin0, const apsm_state *st, void *workspace, size_t workspace_bytes,
+                       int8_t *case_log, void *stream);
+
+/*
+ * Detection (Sec. III-B, Fig. detection): for every data vector r and user k,
+ *   soft[n][k] = f^k(r1) + i f^k(r2),
+ *   f^k(x) = w_L <w_k, x> + w_G sum_{alive centres i} gamma_i^k kappa_G(c_i, x),
+ * and the Gray QPSK decision hard[n][k] = (Re soft < 0) | (Im soft < 0) << 1 (an exact zero
+ * counts as non-negative).  The number of alive entries is read from st->meta[0] on the device,
+ * so a detection queued behind apsm_train on the same stream needs no host synchronisation.
+ *   rx    device [N][M] complex      data vectors
+ *   N     >= 0
+ *   soft  device [N][K] complex      output
+ *   hard  device [N][K] uint8        output, may be NULL
+ * p->dtype selects the contraction precision (APSM_FP32 here).
+ * Errors as for apsm_train.
+ */
+apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
+                        uint8_t *hard, void *stream);
+
+/*
+ * Load a given filter into a state (detection with fixed, externally trained coefficients):
+ * entries [n][M] complex, gamma [n][2][K] and clin [M][K] complex, all DEVICE, in age order
+ * (oldest first), 0 <= n <= dict_cap.  Writes slots 0..n-1, their norms ||r||^2, clin and
+ * meta = {n, 0, n, 0}.  Same expansion as Sec. II-D: f^k = w_L <w_k, .> + w_G sum gamma kappa_G.
+ */
+apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,
+                           int32_t n, const apsm_state *st, void *stream);
+
+/* Synchronise `stream`, then copy meta[3] (the device status word) to *device_status and clear it.
+ * Returns APSM_ERR_CUDA if the synchronisation fails. */
+apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream);
+
+/* Static description of a status code. */
+const char *apsm_status_string(apsm_status s);
+
+/* Number of kernels this library has launched in this process (for launch accounting). */
+int64_t apsm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APSM_GB300_H */

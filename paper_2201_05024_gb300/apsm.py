@@ -1,0 +1,249 @@
+"""Thin Python binding of the C ABI in include/apsm.h (argument marshalling only).
+
+Every step of training and detection runs in the CUDA kernels of libapsm_gb300.so; this
+module loads the library with ctypes, allocates caller-owned device memory with torch and
+passes raw pointers plus torch's current stream.  There is no fallback: if the library is
+missing or the device is not sm_103 the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libapsm_gb300.so")
+
+APSM_OK, APSM_ERR_INVALID_ARG, APSM_ERR_UNSUPPORTED, APSM_ERR_CUDA, APSM_ERR_TIMEOUT, \
+    APSM_ERR_NOT_SM103, APSM_ERR_WORKSPACE = range(7)
+APSM_FP32, APSM_BF16, APSM_FP16 = 0, 1, 2
+_DTYPES = {"fp32": APSM_FP32, "bf16": APSM_BF16, "fp16": APSM_FP16}
+
+
+class ApsmError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} ({code})")
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("K", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("dict_cap", ctypes.c_int32), ("sigma", ctypes.c_float), ("mu", ctypes.c_float),
+                ("eps", ctypes.c_float), ("w_L", ctypes.c_float), ("dtype", ctypes.c_int32)]
+
+
+class _CState(ctypes.Structure):
+    _fields_ = [("dict", ctypes.c_void_p), ("dict_norm", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("clin", ctypes.c_void_p), ("meta", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libapsm_gb300.so (built by paper_2201_05024_gb300.build); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library not built: {p} is missing (run paper_2201_05024_gb300.build.build())")
+        lib = ctypes.CDLL(p)
+        P, S, vp = ctypes.POINTER(_CParams), ctypes.POINTER(_CState), ctypes.c_void_p
+        lib.apsm_dict_alloc.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+        lib.apsm_train_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.apsm_train.argtypes = [P, vp, vp, ctypes.c_int32, vp, S, vp, ctypes.c_size_t, vp, vp]
+        lib.apsm_detect.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp]
+        lib.apsm_read_status.argtypes = [S, ctypes.POINTER(ctypes.c_int32), vp]
+        lib.apsm_state_set.argtypes = [P, vp, vp, vp, ctypes.c_int32, S, vp]
+        lib.apsm_status_string.argtypes = [ctypes.c_int]
+        lib.apsm_status_string.restype = ctypes.c_char_p
+        lib.apsm_launch_count.restype = ctypes.c_int64
+        for f in ("apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_train", "apsm_detect",
+                  "apsm_read_status", "apsm_state_set"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    try:
+        return load_library().apsm_status_string(code).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def _check(code: int, what: str):
+    if code != APSM_OK:
+        raise ApsmError(code, what)
+
+
+@dataclass
+class Params:
+    """APSM parameters (Sec. II-D / Sec. V); w_G = 1 - w_L; sigma is the kernel width."""
+    M: int
+    K: int
+    window: int
+    dict_cap: int
+    sigma: float = 0.5
+    mu: float = 0.5
+    eps: float = 0.01
+    w_L: float = 0.5
+    dtype: str = "fp32"
+
+    def c(self) -> _CParams:
+        return _CParams(self.M, self.K, self.window, self.dict_cap, self.sigma, self.mu, self.eps, self.w_L,
+                        _DTYPES[self.dtype])
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype, shape, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def dict_alloc(p: Params) -> int:
+    lib = load_library()
+    out = ctypes.c_int32()
+    _check(lib.apsm_dict_alloc(ctypes.byref(p.c()), ctypes.byref(out)), "apsm_dict_alloc")
+    return out.value
+
+
+def train_workspace_bytes(p: Params, P: int) -> int:
+    lib = load_library()
+    out = ctypes.c_size_t()
+    _check(lib.apsm_train_workspace_bytes(ctypes.byref(p.c()), int(P), ctypes.byref(out)),
+           "apsm_train_workspace_bytes")
+    return out.value
+
+
+class State:
+    """Caller-owned device state (include/apsm.h: apsm_state) held as torch tensors."""
+
+    def __init__(self, p: Params, device="cuda"):
+        A = dict_alloc(p)
+        self.p = p
+        self.dict = torch.zeros((A, p.M), dtype=torch.complex64, device=device)
+        self.dict_norm = torch.zeros((A,), dtype=torch.float32, device=device)
+        self.gamma = torch.zeros((A, 2, p.K), dtype=torch.float32, device=device)
+        self.clin = torch.zeros((p.M, p.K), dtype=torch.complex64, device=device)
+        self.meta = torch.zeros((4,), dtype=torch.int32, device=device)
+
+    def c(self) -> _CState:
+        return _CState(self.dict.data_ptr(), self.dict_norm.data_ptr(), self.gamma.data_ptr(),
+                       self.clin.data_ptr(), self.meta.data_ptr())
+
+    def entries(self):
+        """(entries [n][M], gamma [n][2][K]) in age order (oldest first), copied to the host."""
+        size, head = (int(v) for v in self.meta[:2].tolist())
+        D = self.p.dict_cap
+        order = [(head + i) % D for i in range(size)]
+        idx = torch.tensor(order, dtype=torch.long, device=self.dict.device)
+        return self.dict[idx].cpu().numpy(), self.gamma[idx].cpu().numpy()
+
+
+def train(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, state: State, *,
+          clin0: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+          case_log: torch.Tensor | None = None) -> State:
+    """apsm_train: run the APSM recurrence over the pilots into `state`, from f_0 with linear
+    part clin0 ([M][K] complex64, zero when None) and no Gaussian part."""
+    lib = load_library()
+    P = int(rx_pilot.shape[0])
+    _dev(rx_pilot, torch.complex64, (P, p.M), "rx_pilot")
+    _dev(sym_pilot, torch.complex64, (P, p.K), "sym_pilot")
+    if clin0 is not None:
+        _dev(clin0, torch.complex64, (p.M, p.K), "clin0")
+    nb = train_workspace_bytes(p, P)
+    if workspace is None and nb > 0:
+        workspace = torch.empty((nb,), dtype=torch.uint8, device=rx_pilot.device)
+    if case_log is not None:
+        _dev(case_log, torch.int8, (2 * P, p.window, p.K), "case_log")
+    st = state.c()
+    _check(lib.apsm_train(ctypes.byref(p.c()), _ptr(rx_pilot), _ptr(sym_pilot), P, _ptr(clin0), ctypes.byref(st),
+                          _ptr(workspace), nb if workspace is None else workspace.numel(), _ptr(case_log),
+                          _stream()), "apsm_train")
+    return state
+
+
+def detect(p: Params, state: State, rx: torch.Tensor, *, soft: torch.Tensor | None = None,
+           hard: torch.Tensor | None = None, want_hard: bool = True):
+    """apsm_detect: soft [N][K] complex64 estimates and Gray QPSK decisions [N][K] uint8."""
+    lib = load_library()
+    N = int(rx.shape[0])
+    _dev(rx, torch.complex64, (N, p.M), "rx")
+    if soft is None:
+        soft = torch.empty((N, p.K), dtype=torch.complex64, device=rx.device)
+    _dev(soft, torch.complex64, (N, p.K), "soft")
+    if hard is None and want_hard:
+        hard = torch.empty((N, p.K), dtype=torch.uint8, device=rx.device)
+    if hard is not None:
+        _dev(hard, torch.uint8, (N, p.K), "hard")
+    st = state.c()
+    _check(lib.apsm_detect(ctypes.byref(p.c()), ctypes.byref(st), _ptr(rx), N, _ptr(soft), _ptr(hard), _stream()),
+           "apsm_detect")
+    return soft, hard
+
+
+def state_set(p: Params, state: State, entries: torch.Tensor, gamma: torch.Tensor, clin: torch.Tensor) -> State:
+    """apsm_state_set: load entries [n][M] complex64, gamma [n][2][K] float32 and clin [M][K]
+    complex64 (device tensors, age order) into `state`."""
+    lib = load_library()
+    n = int(entries.shape[0])
+    _dev(entries, torch.complex64, (n, p.M), "entries")
+    _dev(gamma, torch.float32, (n, 2, p.K), "gamma")
+    _dev(clin, torch.complex64, (p.M, p.K), "clin")
+    st = state.c()
+    _check(lib.apsm_state_set(ctypes.byref(p.c()), _ptr(entries), _ptr(gamma), _ptr(clin), n, ctypes.byref(st),
+                              _stream()), "apsm_state_set")
+    return state
+
+
+def read_status(state: State) -> int:
+    lib = load_library()
+    out = ctypes.c_int32()
+    st = state.c()
+    _check(lib.apsm_read_status(ctypes.byref(st), ctypes.byref(out), _stream()), "apsm_read_status")
+    return out.value
+
+
+def launch_count() -> int:
+    return int(load_library().apsm_launch_count())
+
+
+def train_detect_host(p: Params, rx_pilot, sym_pilot, rx_data, *, state: State | None = None,
+                      device="cuda"):
+    """End-to-end call on HOST tensors: copy pilots, symbols and data vectors to the device,
+    train, detect, and copy the soft and hard outputs back.  Host inputs should be pinned for
+    asynchronous copies.  Returns (soft, hard) as host tensors."""
+    dev = torch.device(device)
+    rp = rx_pilot.to(dev, non_blocking=True)
+    sp = sym_pilot.to(dev, non_blocking=True)
+    rd = rx_data.to(dev, non_blocking=True)
+    st = state if state is not None else State(p, device=dev)
+    train(p, rp, sp, st)
+    soft, hard = detect(p, st, rd)
+    soft_h = torch.empty(soft.shape, dtype=soft.dtype, pin_memory=True)
+    hard_h = torch.empty(hard.shape, dtype=hard.dtype, pin_memory=True)
+    soft_h.copy_(soft, non_blocking=True)
+    hard_h.copy_(hard, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return soft_h, hard_h

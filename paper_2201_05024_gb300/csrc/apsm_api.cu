@@ -1,0 +1,380 @@
+// apsm_api.cu -- host side of the C ABI declared in include/apsm.h.
+//
+// Validates arguments before any CUDA call, checks for an sm_103 device, picks launch
+// shapes and enqueues the kernels on the caller's stream.  Nothing is allocated here: state
+// and workspace are caller-owned device memory.
+#include <atomic>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "apsm_common.cuh"
+#include "detect_f32.cuh"
+#include "train_f32.cuh"
+
+namespace apsm {
+
+std::atomic<long long> g_launches{0};
+
+DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
+
+namespace {
+
+bool supported_M(int M) { return M == 2 || M == 4 || M == 8 || M == 16 || M == 32 || M == 64; }
+
+apsm_status check_params(const apsm_params *p) {
+    if (!p) return APSM_ERR_INVALID_ARG;
+    if (p->M < 1 || p->K < 1 || p->window < 1 || p->dict_cap < 1) return APSM_ERR_INVALID_ARG;
+    if (!(p->sigma > 0.f) || !std::isfinite(p->sigma)) return APSM_ERR_INVALID_ARG;
+    if (!(p->mu > 0.f) || !(p->mu <= 2.f)) return APSM_ERR_INVALID_ARG;
+    if (!(p->eps >= 0.f) || !std::isfinite(p->eps)) return APSM_ERR_INVALID_ARG;
+    if (!(p->w_L >= 0.f) || !(p->w_L <= 1.f)) return APSM_ERR_INVALID_ARG;
+    if (2LL * p->dict_cap <= p->window) return APSM_ERR_INVALID_ARG;
+    if (p->dtype != APSM_FP32 && p->dtype != APSM_BF16 && p->dtype != APSM_FP16) return APSM_ERR_INVALID_ARG;
+    if (p->dict_cap > (1 << 26)) return APSM_ERR_INVALID_ARG;
+    if (!supported_M(p->M) || p->K > 16 || p->window > 128) return APSM_ERR_UNSUPPORTED;
+    return APSM_OK;
+}
+
+apsm_status check_state(const apsm_state *st) {
+    if (!st || !st->dict || !st->dict_norm || !st->gamma || !st->clin || !st->meta) return APSM_ERR_INVALID_ARG;
+    return APSM_OK;
+}
+
+// sm_103 check, cached per device.
+apsm_status check_device() {
+    static std::mutex mu;
+    static int cached[64];  // 0 unknown, 1 ok, 2 not sm_103
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return APSM_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 64) return APSM_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[dev] == 0) {
+        int major = 0, minor = 0;
+        if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return APSM_ERR_CUDA;
+        }
+        cached[dev] = (major == 10 && minor == 3) ? 1 : 2;
+    }
+    return cached[dev] == 1 ? APSM_OK : APSM_ERR_NOT_SM103;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+    }
+    return sms;
+}
+
+int env_int(const char *name, int dflt) {
+    const char *v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+inline apsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APSM_OK : APSM_ERR_CUDA; }
+
+float k2_of(float sigma) { return kLog2e / (2.f * sigma * sigma); }
+
+// ---- detection launch shape -------------------------------------------------------------
+struct DetectShape {
+    int threads, qpt;
+};
+
+DetectShape detect_shape(int M, int N) {
+    DetectShape s;
+    s.qpt = (M <= 16) ? 2 : 1;
+    s.threads = env_int("APSM_DETECT_THREADS", 64);
+    if (s.threads < 32 || s.threads > 256 || s.threads % 32) s.threads = 64;
+    (void)N;
+    return s;
+}
+
+// ---- training geometry --------------------------------------------------------------------
+TrainGeom train_geom(const apsm_params *p, int P) {
+    TrainGeom g;
+    g.M = p->M;
+    g.K = p->K;
+    g.W = p->window;
+    g.D = p->dict_cap;
+    g.P = P;
+    // Entries dropped inside a chunk must be older than the chunk's live range: 2D > 2T + W - 2.
+    int T = env_int("APSM_TRAIN_CHUNK", 32);
+    if (T < 1) T = 32;
+    T = std::min(T, (2 * g.D - g.W + 1) / 2);
+    T = std::min(T, (160 - g.W + 1) / 2);  // live range fits 5 registers per lane
+    T = std::max(T, 1);
+    g.T = T;
+    g.n_chunks = P > 0 ? (P + T - 1) / T : 0;
+    g.RMAX = 2 * T + g.W - 1;
+    g.slice = kTileEntries * 2;
+    return g;
+}
+
+struct TrainWs {
+    size_t kmat, gev, partial, carry, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+TrainWs train_ws(const TrainGeom &g) {
+    TrainWs w;
+    size_t off = 0;
+    w.kmat = off;
+    off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.RMAX * g.RMAX);
+    w.gev = off;
+    off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.T * 2 * g.RMAX);
+    w.partial = off;
+    const int max_slices = (g.D + g.slice - 1) / g.slice;
+    off = align256(off + sizeof(float) * (size_t)max_slices * g.T * 2 * g.K);
+    w.carry = off;
+    off = align256(off + sizeof(float) * (size_t)g.W * g.K);
+    w.total = g.n_chunks > 0 ? off : 0;
+    return w;
+}
+
+__global__ void state_set_kernel(const float2 *__restrict__ entries, const float *__restrict__ gamma,
+                                 const float2 *__restrict__ clin, int n, int M, int K, float2 *dict, float *dict_norm,
+                                 float *gam_out, float2 *clin_out, int *meta) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    for (int i = tid; i < n * M; i += nthr) dict[i] = entries[i];
+    for (int i = tid; i < n * 2 * K; i += nthr) gam_out[i] = gamma[i];
+    for (int i = tid; i < M * K; i += nthr) clin_out[i] = clin[i];
+    for (int t = tid; t < n; t += nthr) {
+        float s = 0.f;
+        for (int m = 0; m < M; ++m) {
+            const float2 v = entries[(size_t)t * M + m];
+            s = fmaf(v.x, v.x, fmaf(v.y, v.y, s));
+        }
+        dict_norm[t] = s;
+    }
+    if (tid == 0) {
+        meta[0] = n;
+        meta[1] = 0;
+        meta[2] = n;
+        meta[3] = 0;
+    }
+}
+
+template <int S>
+cudaError_t launch_chunk(const ChunkArgs &a, int smem, cudaStream_t stream) {
+    auto fn = train_chunk_kernel<S>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fn<<<1, 32 * a.g.K, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace apsm
+
+using namespace apsm;
+
+extern "C" {
+
+apsm_status apsm_dict_alloc(const apsm_params *p, int32_t *dict_alloc) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if (!dict_alloc) return APSM_ERR_INVALID_ARG;
+    *dict_alloc = round_up(p->dict_cap, kTileEntries);
+    return APSM_OK;
+}
+
+apsm_status apsm_train_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if (!bytes || P < 0) return APSM_ERR_INVALID_ARG;
+    *bytes = train_ws(train_geom(p, P)).total;
+    return APSM_OK;
+}
+
+apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                       const float *clin0, const apsm_state *st, void *workspace, size_t workspace_bytes,
+                       int8_t *case_log, void *stream) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if ((s = check_state(st)) != APSM_OK) return s;
+    if (P < 0 || (P > 0 && (!rx_pilot || !sym_pilot))) return APSM_ERR_INVALID_ARG;
+    if (P > (1 << 26)) return APSM_ERR_INVALID_ARG;
+    const TrainGeom g = train_geom(p, P);
+    const TrainWs ws = train_ws(g);
+    if (ws.total > 0 && (!workspace || workspace_bytes < ws.total)) return APSM_ERR_WORKSPACE;
+    if (ws.total > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255)) return APSM_ERR_INVALID_ARG;
+    if ((s = check_device()) != APSM_OK) return s;
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+
+    // f_0: linear part clin0 (or zero), empty Gaussian part
+    const size_t clin_bytes = sizeof(float) * 2 * (size_t)p->M * p->K;
+    cudaError_t ce = clin0 == nullptr ? cudaMemsetAsync(st->clin, 0, clin_bytes, strm)
+                     : clin0 != st->clin ? cudaMemcpyAsync(st->clin, clin0, clin_bytes, cudaMemcpyDeviceToDevice, strm)
+                                         : cudaSuccess;
+    if (ce != cudaSuccess) return APSM_ERR_CUDA;
+    if (P == 0) return cuda_status(cudaMemsetAsync(st->meta, 0, 3 * sizeof(int32_t), strm));
+
+    unsigned char *wsb = static_cast<unsigned char *>(workspace);
+    float *kmat = reinterpret_cast<float *>(wsb + ws.kmat);
+    float *gev = reinterpret_cast<float *>(wsb + ws.gev);
+    float *partial = reinterpret_cast<float *>(wsb + ws.partial);
+    float *carry = reinterpret_cast<float *>(wsb + ws.carry);
+    const float k2 = k2_of(p->sigma);
+    const float wL = p->w_L, wG = 1.f - p->w_L;
+    const float2 *rx = reinterpret_cast<const float2 *>(rx_pilot);
+
+    {   // kernel values of every chunk's live range, and of dropped entries against it
+        const int per_chunk = g.RMAX * g.RMAX + g.T * 2 * g.RMAX;
+        dim3 grid((per_chunk + 255) / 256, g.n_chunks);
+        train_gram_kernel<<<grid, 256, 0, strm>>>(rx, g, k2, wL, wG, kmat, gev);
+        g_launches++;
+        if (cudaGetLastError() != cudaSuccess) return APSM_ERR_CUDA;
+    }
+
+    DetectLauncher det = detect_f32_launcher(p->M, p->K);
+    if (!det) return APSM_ERR_UNSUPPORTED;
+    const ChunkSmem layout(g);
+    const int S = (g.RMAX + 31) / 32;
+    for (int c = 0; c < g.n_chunks; ++c) {
+        int t0, Tc, s0, s1, l0;
+        chunk_range(g, c, t0, Tc, s0, s1, l0);
+        const int n_alive = std::min(t0, g.D);
+        const int n_slices = (n_alive + g.slice - 1) / g.slice;
+        if (n_alive > 0) {  // phase A: f at chunk start, evaluated at the chunk's pilots
+            DetectArgs da{};
+            da.rx = rx + (size_t)t0 * g.M;
+            da.N = Tc;
+            da.dict = reinterpret_cast<const float2 *>(st->dict);
+            da.dict_norm = st->dict_norm;
+            da.gamma = st->gamma;
+            da.clin = reinterpret_cast<const float2 *>(st->clin);
+            da.meta = nullptr;
+            da.n_entries = n_alive;
+            da.slice_entries = g.slice;
+            da.k2 = k2;
+            da.wL = wL;
+            da.wG = wG;
+            da.partial = partial;
+            da.status = st->meta + 3;
+            const int threads = std::min(256, round_up(Tc, 32));
+            if (det(da, n_slices, threads, 1, strm) != cudaSuccess) return APSM_ERR_CUDA;
+            g_launches++;
+        }
+        ChunkArgs ca{};
+        ca.g = g;
+        ca.chunk = c;
+        ca.mu = p->mu;
+        ca.eps = p->eps;
+        ca.wL = wL;
+        ca.wG = wG;
+        ca.rx = rx;
+        ca.sym = reinterpret_cast<const float2 *>(sym_pilot);
+        ca.dict = reinterpret_cast<float2 *>(st->dict);
+        ca.dict_norm = st->dict_norm;
+        ca.gamma = st->gamma;
+        ca.clin = reinterpret_cast<float2 *>(st->clin);
+        ca.meta = st->meta;
+        ca.kmat = kmat;
+        ca.gev = gev;
+        ca.partial = partial;
+        ca.n_slices = n_slices;
+        ca.carry = carry;
+        ca.case_log = case_log;
+        cudaError_t e;
+        switch (S) {
+            case 1: e = launch_chunk<1>(ca, layout.bytes, strm); break;
+            case 2: e = launch_chunk<2>(ca, layout.bytes, strm); break;
+            case 3: e = launch_chunk<3>(ca, layout.bytes, strm); break;
+            case 4: e = launch_chunk<4>(ca, layout.bytes, strm); break;
+            case 5: e = launch_chunk<5>(ca, layout.bytes, strm); break;
+            default: return APSM_ERR_UNSUPPORTED;
+        }
+        if (e != cudaSuccess) return APSM_ERR_CUDA;
+        g_launches++;
+    }
+    return APSM_OK;
+}
+
+apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
+                        uint8_t *hard, void *stream) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if ((s = check_state(st)) != APSM_OK) return s;
+    if (N < 0 || (N > 0 && (!rx || !soft))) return APSM_ERR_INVALID_ARG;
+    if (p->dtype != APSM_FP32) return APSM_ERR_UNSUPPORTED;
+    if ((s = check_device()) != APSM_OK) return s;
+    if (N == 0) return APSM_OK;
+    DetectLauncher det = detect_f32_launcher(p->M, p->K);
+    if (!det) return APSM_ERR_UNSUPPORTED;
+    DetectArgs da{};
+    da.rx = reinterpret_cast<const float2 *>(rx);
+    da.N = N;
+    da.dict = reinterpret_cast<const float2 *>(st->dict);
+    da.dict_norm = st->dict_norm;
+    da.gamma = st->gamma;
+    da.clin = reinterpret_cast<const float2 *>(st->clin);
+    da.meta = st->meta;
+    da.n_entries = p->dict_cap;
+    da.slice_entries = round_up(p->dict_cap, kTileEntries);
+    da.k2 = k2_of(p->sigma);
+    da.wL = p->w_L;
+    da.wG = 1.f - p->w_L;
+    da.soft = reinterpret_cast<float2 *>(soft);
+    da.hard = hard;
+    da.partial = nullptr;
+    da.status = st->meta + 3;
+    const DetectShape sh = detect_shape(p->M, N);
+    if (det(da, 1, sh.threads, sh.qpt, static_cast<cudaStream_t>(stream)) != cudaSuccess) return APSM_ERR_CUDA;
+    g_launches++;
+    return APSM_OK;
+}
+
+apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,
+                           int32_t n, const apsm_state *st, void *stream) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if ((s = check_state(st)) != APSM_OK) return s;
+    if (n < 0 || n > p->dict_cap || !clin || (n > 0 && (!entries || !gamma))) return APSM_ERR_INVALID_ARG;
+    if ((s = check_device()) != APSM_OK) return s;
+    const int work = std::max(n * p->M, std::max(n * 2 * p->K, p->M * p->K));
+    const int blocks = std::max(1, std::min(1024, (work + 255) / 256));
+    state_set_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const float2 *>(entries), gamma, reinterpret_cast<const float2 *>(clin), n, p->M, p->K,
+        reinterpret_cast<float2 *>(st->dict), st->dict_norm, st->gamma, reinterpret_cast<float2 *>(st->clin),
+        st->meta);
+    g_launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream) {
+    if (!st || !st->meta || !device_status) return APSM_ERR_INVALID_ARG;
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(strm) != cudaSuccess) return APSM_ERR_CUDA;
+    int32_t v = 0;
+    if (cudaMemcpy(&v, st->meta + 3, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return APSM_ERR_CUDA;
+    if (cudaMemset(st->meta + 3, 0, sizeof(int32_t)) != cudaSuccess) return APSM_ERR_CUDA;
+    *device_status = v;
+    return APSM_OK;
+}
+
+const char *apsm_status_string(apsm_status s) {
+    switch (s) {
+        case APSM_OK: return "ok";
+        case APSM_ERR_INVALID_ARG: return "invalid argument";
+        case APSM_ERR_UNSUPPORTED: return "unsupported shape";
+        case APSM_ERR_CUDA: return "CUDA runtime error";
+        case APSM_ERR_TIMEOUT: return "device-side wait timed out";
+        case APSM_ERR_NOT_SM103: return "device is not sm_103";
+        case APSM_ERR_WORKSPACE: return "workspace too small";
+    }
+    return "unknown status";
+}
+
+int64_t apsm_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI (no GPU work): the library builds, loads, exports every
+function include/apsm.h declares, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "apsm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:apsm_status|const char|int64_t|void)\s*\**\s*(apsm_\w+)\s*\(", text,
+                                 flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_05024_gb300 import build, apsm
+    build.build()
+    return apsm.load_library()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for f in ("apsm_train", "apsm_detect", "apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_status_string"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_built_for_sm103a_only():
+    from paper_2201_05024_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    assert not any("sm_90" in a or "sm_100" in a for a in build.ARCH)
+
+
+def params(**kw):
+    from paper_2201_05024_gb300 import apsm
+    base = dict(M=16, K=6, window=16, dict_cap=1024)
+    base.update(kw)
+    return apsm.Params(**base)
+
+
+def test_dict_alloc_rounds_to_whole_tiles(lib):
+    from paper_2201_05024_gb300 import apsm
+    assert apsm.dict_alloc(params(dict_cap=1000)) == 1024
+    assert apsm.dict_alloc(params(dict_cap=1024)) == 1024
+    assert apsm.dict_alloc(params(dict_cap=9, window=16)) == 32
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(sigma=0.0), 1), (dict(sigma=-1.0), 1), (dict(mu=0.0), 1), (dict(mu=2.5), 1), (dict(eps=-0.1), 1),
+    (dict(w_L=1.5), 1), (dict(window=0), 1), (dict(dict_cap=8, window=16), 1), (dict(K=0), 1),
+    (dict(M=3), 2), (dict(M=128), 2), (dict(K=17), 2), (dict(window=129, dict_cap=4096), 2),
+])
+def test_parameter_validation(lib, bad, code):
+    from paper_2201_05024_gb300 import apsm
+    with pytest.raises(apsm.ApsmError) as ei:
+        apsm.dict_alloc(params(**bad))
+    assert ei.value.code == code
+
+
+def test_workspace_query(lib):
+    from paper_2201_05024_gb300 import apsm
+    assert apsm.train_workspace_bytes(params(), 0) == 0
+    nb = apsm.train_workspace_bytes(params(), 1024)
+    assert nb > 0 and nb % 256 == 0
+    assert apsm.train_workspace_bytes(params(), 2048) > nb
+
+
+def _cstate(ptr=1):
+    from paper_2201_05024_gb300 import apsm
+    return apsm._CState(ptr, ptr, ptr, ptr, ptr)
+
+
+def test_null_pointers_rejected_before_device(lib):
+    from paper_2201_05024_gb300 import apsm
+    p = params().c()
+    st = _cstate(0)
+    assert lib.apsm_train(ctypes.byref(p), None, None, 0, None, ctypes.byref(st), None, 0, None, None) == 1
+    assert lib.apsm_detect(ctypes.byref(p), ctypes.byref(_cstate()), None, 5, None, None, None) == 1
+    assert lib.apsm_detect(ctypes.byref(p), ctypes.byref(_cstate()), None, -1, None, None, None) == 1
+    assert lib.apsm_train(ctypes.byref(p), None, None, -3, None, ctypes.byref(_cstate()), None, 0, None, None) == 1
+    # too-small workspace
+    assert lib.apsm_train(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(256), 64, None,
+                          ctypes.byref(_cstate()), ctypes.c_void_p(256), 16, None, None) == apsm.APSM_ERR_WORKSPACE
+    assert lib.apsm_read_status(None, None, None) == 1
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")
+def test_valid_call_without_a_device_fails_loudly(lib):
+    from paper_2201_05024_gb300 import apsm
+    p = params().c()
+    rc = lib.apsm_detect(ctypes.byref(p), ctypes.byref(_cstate(256)), ctypes.c_void_p(256), 4,
+                         ctypes.c_void_p(256), None, None)
+    assert rc == apsm.APSM_ERR_CUDA
+
+
+def test_status_strings(lib):
+    from paper_2201_05024_gb300 import apsm
+    for c in range(7):
+        assert apsm.status_string(c) not in ("", "unknown status")
+    assert lib.apsm_launch_count() >= 0

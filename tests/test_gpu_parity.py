@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical seeded
+inputs.  Detection is compared element by element; training compares the trained coefficients,
+the branch of Eq. beta taken at every (step, window slot, user), and the detections of the
+two trained filters.  Tolerances are in tests/parity.py."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_05024_gb300 import apsm, synth
+
+from parity import (TOL_FP32, assert_hard_match, assert_soft_close, gpu_params, load_state, oracle_state_fp32,
+                    rms, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    apsm.load_library()
+
+
+# ------------------------------------------------------------------------------------------
+# detection
+# ------------------------------------------------------------------------------------------
+
+DETECT_CASES = [
+    # M, K, D entries, N queries, sigma, w_L
+    (4, 2, 200, 1000, 0.5, 0.5),        # 1-pilot-config shapes
+    (16, 6, 1000, 3001, 0.5, 0.5),      # several tiles, ragged entry tile and query tail
+    (2, 1, 33, 65, 0.7, 0.3),
+    (8, 3, 100, 257, 0.4, 0.8),
+    (32, 12, 300, 513, 0.6, 0.5),
+    (64, 16, 130, 300, 0.5, 0.5),
+    (16, 16, 64, 70, 0.3, 0.0),         # Gaussian part only
+    (8, 5, 40, 129, 0.5, 1.0),          # linear part only
+    (16, 6, 1, 31, 0.5, 0.5),           # a single entry
+]
+
+
+@pytest.mark.parametrize("M,K,D,N,sigma,wL", DETECT_CASES)
+def test_detect_matches_oracle(M, K, D, N, sigma, wL):
+    ent, gam, clin = synth.random_state(M, K, D, instance=D + 7 * M + K)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=M * 100 + K)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=sigma, w_L=wL)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
+    assert_soft_close(soft.cpu().numpy(), ref)
+    assert_hard_match(hard.cpu().numpy(), ref)
+    assert apsm.read_status(st) == 0
+
+
+def test_detect_empty_dictionary_is_linear_filter():
+    M, K, N = 16, 6, 200
+    ent, gam, clin = synth.random_state(M, K, 0)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=3)
+    op = oracle.Params(M=M, K=K, W=1, D=8)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    soft, _ = apsm.detect(gp, st, to_dev(inst.rx_data))
+    ref = 0.5 * (inst.rx_data.astype(np.complex128) @ np.conj(clin.astype(np.complex128)))
+    assert_soft_close(soft.cpu().numpy(), ref)
+
+
+def test_detect_zero_queries_is_a_no_op():
+    op = oracle.Params(M=8, K=2, W=1, D=8)
+    gp = gpu_params(op)
+    ent, gam, clin = synth.random_state(8, 2, 8)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, torch.empty((0, 8), dtype=torch.complex64, device="cuda"))
+    assert soft.shape == (0, 2) and hard.shape == (0, 2)
+
+
+def test_detect_is_deterministic():
+    M, K, D, N = 16, 6, 700, 5000
+    ent, gam, clin = synth.random_state(M, K, D, instance=1)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=2)
+    gp = gpu_params(oracle.Params(M=M, K=K, W=1, D=D))
+    st = load_state(gp, ent, gam, clin)
+    rx = to_dev(inst.rx_data)
+    a, _ = apsm.detect(gp, st, rx)
+    b, _ = apsm.detect(gp, st, rx)
+    assert torch.equal(a, b)
+
+
+def test_detect_rejects_a_wrong_shape():
+    gp = apsm.Params(M=16, K=6, window=4, dict_cap=16)
+    st = apsm.State(gp)
+    with pytest.raises(ValueError):
+        apsm.detect(gp, st, torch.zeros((10, 8), dtype=torch.complex64, device="cuda"))
+
+
+# ------------------------------------------------------------------------------------------
+# training
+# ------------------------------------------------------------------------------------------
+
+def _train_both(op, inst, *, w0=None, log=True):
+    gp = gpu_params(op)
+    P = inst.rx_pilot.shape[0]
+    st = apsm.State(gp)
+    cl = torch.full((2 * P, op.W, op.K), 127, dtype=torch.int8, device="cuda") if log else None
+    clin0 = None if w0 is None else to_dev(oracle.clin_from_w(op.M, w0).astype(np.complex64))
+    apsm.train(gp, to_dev(inst.rx_pilot), to_dev(inst.sym_pilot), st, clin0=clin0, case_log=cl)
+    ref = oracle.train(op, inst.rx_pilot, inst.sym_pilot, w0=w0, log_cases=log)
+    torch.cuda.synchronize()
+    return gp, st, cl, ref
+
+
+def _compare_training(op, inst, gp, st, cl, ref, *, tol_coef, tol_soft=TOL_FP32, tie=1e-4):
+    fst, cases, margins = ref
+    P = inst.rx_pilot.shape[0]
+    meta = st.meta.cpu().numpy()
+    assert meta[0] == min(P, op.D) and meta[2] == P
+    assert meta[1] == (P % op.D if P >= op.D else 0)
+    ent, gam = st.entries()
+    # dictionary entries are copies of the last pilots, bit for bit
+    np.testing.assert_array_equal(ent, inst.rx_pilot[fst.first_entry:fst.first_entry + fst.n_entries])
+    # branch of Eq. beta: identical except at near-ties of |e| with eps in the FP64 run
+    gcl = cl.cpu().numpy()
+    valid = cases != 127
+    assert np.array_equal(gcl == 127, ~valid)
+    diff = valid & (gcl != cases)
+    if diff.any():
+        assert np.all(margins[diff] < tie), f"branch differs away from a tie: margins {margins[diff].max():.2e}"
+    # coefficients, rms-normalised
+    g_ref = fst.gamma.reshape(-1, 2, op.K)
+    dg = np.abs(gam.astype(np.float64) - g_ref).max() / max(rms(g_ref), 1e-30)
+    c_gpu = st.clin.cpu().numpy().astype(np.complex128)
+    c_ref = oracle.clin_from_w(op.M, fst.w)
+    dc = np.abs(c_gpu - c_ref).max() / max(rms(np.abs(c_ref)), 1e-30)
+    assert dg <= tol_coef, f"gamma error {dg:.3e}"
+    assert dc <= tol_coef, f"clin error {dc:.3e}"
+    # the two trained filters detect the same soft symbols
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+    ref_soft = oracle.detect(op, fst, inst.rx_data)
+    err = assert_soft_close(soft.cpu().numpy(), ref_soft, tol=tol_soft, what="soft after training")
+    assert_hard_match(hard.cpu().numpy(), ref_soft, tol=tol_soft)
+    assert apsm.read_status(st) == 0
+    return dg, dc, err, int(diff.sum())
+
+
+TRAIN_CASES = [
+    # M, K, P, W, D, sigma, mu, eps, w_L, N
+    (4, 2, 200, 8, 200, 0.5, 0.5, 0.01, 0.5, 1000),     # the small APSM configuration
+    (4, 2, 100, 8, 20, 0.5, 0.5, 0.01, 0.5, 300),       # FIFO eviction, chunk limited by D
+    (8, 3, 150, 5, 9, 0.6, 1.0, 0.02, 0.4, 300),        # small D: one- or few-pilot chunks
+    (4, 1, 77, 1, 40, 0.5, 1.0, 0.0, 0.5, 100),         # W = 1, ragged last chunk, eps = 0
+    (16, 6, 5, 16, 64, 0.5, 0.5, 0.01, 0.5, 100),       # fewer pilots than one chunk
+    (2, 4, 1, 3, 4, 0.5, 0.5, 0.01, 0.5, 50),           # a single pilot
+    (32, 12, 90, 31, 50, 0.7, 1.9, 0.05, 0.7, 200),     # odd window, strong relaxation
+    (8, 16, 70, 16, 70, 0.5, 0.5, 0.01, 1.0, 100),      # linear-only kernel
+    (8, 2, 70, 16, 70, 0.5, 0.5, 0.01, 0.0, 100),       # Gaussian-only kernel
+    (64, 4, 60, 10, 60, 0.5, 0.5, 0.01, 0.5, 100),
+]
+
+
+@pytest.mark.parametrize("M,K,P,W,D,sigma,mu,eps,wL,N", TRAIN_CASES)
+def test_train_matches_oracle(M, K, P, W, D, sigma, mu, eps, wL, N):
+    inst = synth.make_instance(M, K, P, N, 10.0, instance=P + M + K)
+    op = oracle.Params(M=M, K=K, W=W, D=D, sigma=sigma, mu=mu, eps=eps, w_L=wL)
+    gp, st, cl, ref = _train_both(op, inst)
+    _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
+
+
+def test_train_with_initial_linear_filter():
+    M, K, P = 8, 3, 60
+    inst = synth.make_instance(M, K, P, 200, 10.0, instance=41)
+    op = oracle.Params(M=M, K=K, W=6, D=30)
+    w0 = np.random.default_rng(4).standard_normal((K, 2 * M)) * 0.3
+    gp, st, cl, ref = _train_both(op, inst, w0=w0)
+    _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
+
+
+def test_train_zero_pilots_leaves_empty_filter():
+    gp = apsm.Params(M=8, K=2, window=4, dict_cap=16)
+    st = apsm.State(gp)
+    st.meta.fill_(7)
+    apsm.train(gp, torch.empty((0, 8), dtype=torch.complex64, device="cuda"),
+               torch.empty((0, 2), dtype=torch.complex64, device="cuda"), st)
+    assert st.meta[:3].tolist() == [0, 0, 0]
+    soft, _ = apsm.detect(gp, st, torch.ones((3, 8), dtype=torch.complex64, device="cuda"))
+    assert torch.count_nonzero(soft) == 0
+
+
+def test_retraining_a_state_is_deterministic():
+    M, K, P = 16, 6, 300
+    inst = synth.make_instance(M, K, P, 10, 10.0, instance=42)
+    gp = apsm.Params(M=M, K=K, window=16, dict_cap=128)
+    st = apsm.State(gp)
+    rp, sp = to_dev(inst.rx_pilot), to_dev(inst.sym_pilot)
+    apsm.train(gp, rp, sp, st)
+    a = [t.clone() for t in (st.dict, st.gamma, st.clin, st.meta)]
+    apsm.train(gp, rp, sp, st)
+    for x, y in zip(a, (st.dict, st.gamma, st.clin, st.meta)):
+        assert torch.equal(x, y)
+
+
+def test_paper_default_parameters():
+    """Sec. V defaults (w_L = w_G = 0.5, W = 20, sigma^2 = 0.05, 16 antennas, 6 users, 685 pilots,
+    3840 data vectors; tests/golden/paper_defaults.txt) on synthetic data."""
+    M, K, P, N = 16, 6, 685, 3840
+    inst = synth.make_instance(M, K, P, N, 15.0, instance=43)
+    op = oracle.Params(M=M, K=K, W=20, D=P, sigma=math.sqrt(0.05), mu=0.5, eps=0.01, w_L=0.5)
+    gp, st, cl, ref = _train_both(op, inst)
+    _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
+
+
+@pytest.mark.slow
+def test_full_size_16x6_train_and_sampled_detect():
+    """The 16-antenna, 6-user workload at full size (1024 pilots, window 16, D = 1024, 65536 data
+    vectors) in the launch configuration the benchmark times; detection checked on a sample."""
+    M, K, P, N = 16, 6, 1024, 65536
+    inst = synth.make_instance(M, K, P, N, 10.0, instance=0)
+    op = oracle.Params(M=M, K=K, W=16, D=1024, sigma=0.5, mu=0.5, eps=0.01, w_L=0.5)
+    gp, st, cl, ref = _train_both(op, inst)
+    fst = ref[0]
+    sample = np.random.default_rng(0).choice(N, 2048, replace=False)
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+    soft = soft.cpu().numpy()[sample]
+    ref_soft = oracle.detect(op, fst, inst.rx_data[sample])
+    assert_soft_close(soft, ref_soft, what="soft after training")
+    assert_hard_match(hard.cpu().numpy()[sample], ref_soft)
+    # detection alone from the oracle's own trained filter
+    ent = inst.rx_pilot[fst.first_entry:fst.first_entry + fst.n_entries]
+    gam = fst.gamma.reshape(-1, 2, K)
+    clin = oracle.clin_from_w(M, fst.w)
+    st2 = load_state(gp, ent, gam, clin)
+    soft2, _ = apsm.detect(gp, st2, to_dev(inst.rx_data))
+    ref2 = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data[sample])
+    assert_soft_close(soft2.cpu().numpy()[sample], ref2)
+    ser = float(np.mean(hard.cpu().numpy() != inst.idx_data))
+    assert ser < 0.05
