@@ -136,6 +136,27 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
                        int8_t *case_log, void *stream);
 
 /*
+ * apsm_train_noalloc -- apsm_train for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment variant of apsm_train, not part of the
+ * method.  Callers such as a real-time receive loop that must not allocate once it runs, or a
+ * plug-in whose host framework owns all device memory, cannot provide apsm_train's workspace;
+ * this entry point uses scratch memory that is part of the library instead: a fixed array of
+ * APSM_NOALLOC_SCRATCH_BYTES that every device loading the library holds until process exit.
+ * Arguments and results are those of apsm_train without workspace/workspace_bytes.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - Training that needs more scratch than the array holds (apsm_train_workspace_bytes(p, P)
+ *     > APSM_NOALLOC_SCRATCH_BYTES) is rejected with APSM_ERR_WORKSPACE before any work.
+ *   - The first call on a device, with that device current, looks up the array's device
+ *     address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the one array, which keeps the last call's contents (the
+ *     training writes every scratch word before reading it).  Calls whose GPU work overlaps --
+ *     on different streams, or from different threads -- race on it: serialise them.
+ */
+#define APSM_NOALLOC_SCRATCH_BYTES (4u << 20)
+apsm_status apsm_train_noalloc(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                               const float *clin0, const apsm_state *st, int8_t *case_log, void *stream);
+
+/*
  * Detection (Sec. III-B, Fig. detection): for every data vector r and user k,
  *   soft[n][k] = f^k(r1) + i f^k(r2),
  *   f^k(x) = w_L <w_k, x> + w_G sum_{alive centres i} gamma_i^k kappa_G(c_i, x),
