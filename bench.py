@@ -160,6 +160,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the CPU baseline and FP64 error legs")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
+                    help="MiB written between timed steps to flush L2 (0: none, for profiler captures)")
     args = ap.parse_args()
     w = dict(WORKLOAD)
     if args.impl == "reference":
@@ -196,7 +199,8 @@ def main():
     ws = torch.empty((max(apsm.train_workspace_bytes(gp, w["P"]), 1),), dtype=torch.uint8, device=dev)
     soft = torch.empty((w["N"], w["K"]), dtype=torch.complex64, device=dev)
     hard = torch.empty((w["N"], w["K"]), dtype=torch.uint8, device=dev)
-    flush = torch.empty((L2_FLUSH_BYTES // 4,), dtype=torch.float32, device=dev)
+    flush = torch.empty((max(args.flush_mb, 1) << 18,), dtype=torch.float32, device=dev)
+    do_flush = args.flush_mb > 0
     stream = torch.cuda.current_stream()
 
     def step():
@@ -204,7 +208,8 @@ def main():
         apsm.detect(gp, st, rd, soft=soft, hard=hard)
 
     for _ in range(max(args.warmup, 3)):
-        flush.fill_(1.0)
+        if do_flush:
+            flush.fill_(1.0)
         step()
     torch.cuda.synchronize()
 
@@ -219,7 +224,8 @@ def main():
     launches0 = apsm.launch_count()
     wall0 = time.perf_counter()
     for i in range(args.steps):
-        flush.fill_(float(i))           # L2 flush between timed steps (outside the events)
+        if do_flush:
+            flush.fill_(float(i))       # L2 flush between timed steps (outside the events)
         ev[i][0].record(stream)
         apsm.train(gp, rp, sp, st, workspace=ws)
         ev[i][1].record(stream)
@@ -245,25 +251,30 @@ def main():
     assert apsm.read_status(st) == 0, "device status word set during the benchmark"
 
     # ---- end to end through the public API on host buffers (pinned), copies inside the timing
-    hp = torch.from_numpy(inst.rx_pilot).pin_memory()
-    hs = torch.from_numpy(inst.sym_pilot).pin_memory()
-    hd = torch.from_numpy(inst.rx_data).pin_memory()
-    for _ in range(2):
-        apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
-    e2e_times = []
-    for _ in range(max(3, min(args.steps, 10))):
-        flush.fill_(0.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        soft_h, hard_h = apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
-        e2e_times.append(time.perf_counter() - t0)
-    e2e_step = sum(e2e_times) / len(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = t.item()
-    h2d = hp.numel() * 8 + hs.numel() * 8 + hd.numel() * 8
-    d2h = soft_h.numel() * 8 + hard_h.numel()
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(inst.rx_pilot).pin_memory()
+        hs = torch.from_numpy(inst.sym_pilot).pin_memory()
+        hd = torch.from_numpy(inst.rx_data).pin_memory()
+        for _ in range(2):
+            apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
+        e2e_times = []
+        for _ in range(max(3, min(args.steps, 10))):
+            if do_flush:
+                flush.fill_(0.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            soft_h, hard_h = apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
+            e2e_times.append(time.perf_counter() - t0)
+        e2e_step = sum(e2e_times) / len(e2e_times)
+        if dist is not None:
+            t = torch.tensor([e2e_step], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_step = t.item()
+        h2d = hp.numel() * 8 + hs.numel() * 8 + hd.numel() * 8
+        d2h = soft_h.numel() * 8 + hard_h.numel()
+        e2e = {"value": world * w["N"] / e2e_step, "unit": "symbol-vectors/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_step * 1e3}
 
     if rank != 0:
         if dist is not None:
@@ -278,7 +289,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "symbol-vectors/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_name(w), "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+        "config": {"workload": workload_name(w),
+                   "l2": f"flushed between timed steps ({args.flush_mb} MiB write)" if do_flush else "not flushed",
                    "parallelism": f"independent instance per GPU x{world}", "step": "train P pilots + detect N vectors"},
         "detect": {"value": world * w["N"] / (mean_detect / 1e3), "unit": "symbol-vectors/s",
                    "ms": mean_detect},
@@ -289,8 +301,7 @@ def main():
                      "peak_kind": "derived FP32 FMA pipe at max SM clock"},
         "gpu_launches": int(launches),
         "wall_s_timed": wall,
-        "e2e": {"value": world * w["N"] / e2e_step, "unit": "symbol-vectors/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_step * 1e3},
+        "e2e": e2e,
         "clocks": clocks,
     }
     if not args.no_oracle:

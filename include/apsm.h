@@ -20,6 +20,9 @@
  *     allocation between calls and makes none inside them.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue work on it and
  *     return without synchronising; results are valid once the stream has reached them.
+ *   - Arrays of received vectors (rx_pilot, rx) and the state's dict, dict_norm and gamma must be
+ *     16-byte aligned (they are read with 16-byte vector loads and bulk copies); other arrays
+ *     need the alignment of their element type.  Misaligned pointers give APSM_ERR_INVALID_ARG.
  *   - Host-side argument errors return at once, before any CUDA call.  A device-side error
  *     (a bounded wait that ran out) is written to meta[3] of the state and reported by
  *     apsm_read_status().

@@ -18,6 +18,9 @@ namespace apsm {
 std::atomic<long long> g_launches{0};
 
 DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
+using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
+ChunkLauncher chunk_launcher(int S, int WP);        // train_chunk.cu
+int padded_window(int W);                           // train_chunk.cu
 
 namespace {
 
@@ -37,8 +40,14 @@ apsm_status check_params(const apsm_params *p) {
     return APSM_OK;
 }
 
+bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; }
+
 apsm_status check_state(const apsm_state *st) {
     if (!st || !st->dict || !st->dict_norm || !st->gamma || !st->clin || !st->meta) return APSM_ERR_INVALID_ARG;
+    // dictionary tiles are moved by the bulk-copy engine: 16-byte aligned sources
+    if (!aligned16(st->dict) || !aligned16(st->dict_norm) || !aligned16(st->gamma)) return APSM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(st->clin) & 7) || (reinterpret_cast<uintptr_t>(st->meta) & 3))
+        return APSM_ERR_INVALID_ARG;
     return APSM_OK;
 }
 
@@ -75,6 +84,9 @@ int num_sms() {
     return sms;
 }
 
+constexpr int kMaxChunkThreads = 160;      // phase-B CTA size limit (S <= 5 warps)
+constexpr int kMaxSmemBytes = 227 * 1024;  // opt-in shared memory per CTA
+
 int env_int(const char *name, int dflt) {
     const char *v = std::getenv(name);
     return (v && *v) ? std::atoi(v) : dflt;
@@ -85,15 +97,14 @@ inline apsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APSM_O
 float k2_of(float sigma) { return kLog2e / (2.f * sigma * sigma); }
 
 // ---- detection launch shape -------------------------------------------------------------
-struct DetectShape {
-    int threads, qpt;
-};
-
 DetectShape detect_shape(int M, int N) {
     DetectShape s;
-    s.qpt = (M <= 16) ? 2 : 1;
+    s.qpt = env_int("APSM_DETECT_QPT", 1);
+    if (s.qpt != 1 && s.qpt != 2) s.qpt = 1;
     s.threads = env_int("APSM_DETECT_THREADS", 64);
     if (s.threads < 32 || s.threads > 256 || s.threads % 32) s.threads = 64;
+    s.split = env_int("APSM_DETECT_SPLIT", 2);
+    if (s.split < 1 || s.split * s.threads > 256) s.split = 1;
     (void)N;
     return s;
 }
@@ -107,15 +118,20 @@ TrainGeom train_geom(const apsm_params *p, int P) {
     g.D = p->dict_cap;
     g.P = P;
     // Entries dropped inside a chunk must be older than the chunk's live range: 2D > 2T + W - 2.
-    int T = env_int("APSM_TRAIN_CHUNK", 32);
-    if (T < 1) T = 32;
+    int T = env_int("APSM_TRAIN_CHUNK", 64);
+    if (T < 1) T = 64;
     T = std::min(T, (2 * g.D - g.W + 1) / 2);
-    T = std::min(T, (160 - g.W + 1) / 2);  // live range fits 5 registers per lane
+    T = std::min(T, (kMaxChunkThreads - g.W + 1) / 2);  // one thread per live-range sample
     T = std::max(T, 1);
-    g.T = T;
+    g.WP = padded_window(g.W);
+    g.slice = kTileEntries;
+    for (;; --T) {  // the largest chunk whose phase-B tables fit in shared memory
+        g.T = T;
+        g.RMAX = 2 * T + g.W - 1;
+        g.RS = round_up(g.RMAX, 32);
+        if (T == 1 || ChunkSmem(g).bytes <= kMaxSmemBytes) break;
+    }
     g.n_chunks = P > 0 ? (P + T - 1) / T : 0;
-    g.RMAX = 2 * T + g.W - 1;
-    g.slice = kTileEntries * 2;
     return g;
 }
 
@@ -129,9 +145,9 @@ TrainWs train_ws(const TrainGeom &g) {
     TrainWs w;
     size_t off = 0;
     w.kmat = off;
-    off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.RMAX * g.RMAX);
+    off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.RS * g.RS);
     w.gev = off;
-    off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.T * 2 * g.RMAX);
+    off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.T * 2 * g.RS);
     w.partial = off;
     const int max_slices = (g.D + g.slice - 1) / g.slice;
     off = align256(off + sizeof(float) * (size_t)max_slices * g.T * 2 * g.K);
@@ -162,15 +178,6 @@ __global__ void state_set_kernel(const float2 *__restrict__ entries, const float
         meta[2] = n;
         meta[3] = 0;
     }
-}
-
-template <int S>
-cudaError_t launch_chunk(const ChunkArgs &a, int smem, cudaStream_t stream) {
-    auto fn = train_chunk_kernel<S>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    fn<<<1, 32 * a.g.K, smem, stream>>>(a);
-    return cudaGetLastError();
 }
 
 }  // namespace
@@ -204,6 +211,8 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
     if ((s = check_state(st)) != APSM_OK) return s;
     if (P < 0 || (P > 0 && (!rx_pilot || !sym_pilot))) return APSM_ERR_INVALID_ARG;
     if (P > (1 << 26)) return APSM_ERR_INVALID_ARG;
+    if (P > 0 && (!aligned16(rx_pilot) || (reinterpret_cast<uintptr_t>(sym_pilot) & 7))) return APSM_ERR_INVALID_ARG;
+    if (clin0 && (reinterpret_cast<uintptr_t>(clin0) & 7)) return APSM_ERR_INVALID_ARG;
     const TrainGeom g = train_geom(p, P);
     const TrainWs ws = train_ws(g);
     if (ws.total > 0 && (!workspace || workspace_bytes < ws.total)) return APSM_ERR_WORKSPACE;
@@ -229,17 +238,15 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
     const float2 *rx = reinterpret_cast<const float2 *>(rx_pilot);
 
     {   // kernel values of every chunk's live range, and of dropped entries against it
-        const int per_chunk = g.RMAX * g.RMAX + g.T * 2 * g.RMAX;
-        dim3 grid((per_chunk + 255) / 256, g.n_chunks);
-        train_gram_kernel<<<grid, 256, 0, strm>>>(rx, g, k2, wL, wG, kmat, gev);
+        if (launch_train_gram(rx, g, k2, wL, wG, kmat, gev, strm) != cudaSuccess) return APSM_ERR_CUDA;
         g_launches++;
-        if (cudaGetLastError() != cudaSuccess) return APSM_ERR_CUDA;
     }
 
     DetectLauncher det = detect_f32_launcher(p->M, p->K);
     if (!det) return APSM_ERR_UNSUPPORTED;
     const ChunkSmem layout(g);
-    const int S = (g.RMAX + 31) / 32;
+    const ChunkLauncher chunk = chunk_launcher(g.RS / 32, g.WP);
+    if (!chunk) return APSM_ERR_UNSUPPORTED;
     for (int c = 0; c < g.n_chunks; ++c) {
         int t0, Tc, s0, s1, l0;
         chunk_range(g, c, t0, Tc, s0, s1, l0);
@@ -261,8 +268,9 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
             da.wG = wG;
             da.partial = partial;
             da.status = st->meta + 3;
-            const int threads = std::min(256, round_up(Tc, 32));
-            if (det(da, n_slices, threads, 1, strm) != cudaSuccess) return APSM_ERR_CUDA;
+            const int thr = std::min(256, round_up(Tc, 32));
+            const DetectShape sh{thr, std::max(1, 256 / thr), 1};  // entry groups share each tile
+            if (det(da, n_slices, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
             g_launches++;
         }
         ChunkArgs ca{};
@@ -285,16 +293,7 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         ca.n_slices = n_slices;
         ca.carry = carry;
         ca.case_log = case_log;
-        cudaError_t e;
-        switch (S) {
-            case 1: e = launch_chunk<1>(ca, layout.bytes, strm); break;
-            case 2: e = launch_chunk<2>(ca, layout.bytes, strm); break;
-            case 3: e = launch_chunk<3>(ca, layout.bytes, strm); break;
-            case 4: e = launch_chunk<4>(ca, layout.bytes, strm); break;
-            case 5: e = launch_chunk<5>(ca, layout.bytes, strm); break;
-            default: return APSM_ERR_UNSUPPORTED;
-        }
-        if (e != cudaSuccess) return APSM_ERR_CUDA;
+        if (chunk(ca, layout.bytes, strm) != cudaSuccess) return APSM_ERR_CUDA;
         g_launches++;
     }
     return APSM_OK;
@@ -306,6 +305,7 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     if (s != APSM_OK) return s;
     if ((s = check_state(st)) != APSM_OK) return s;
     if (N < 0 || (N > 0 && (!rx || !soft))) return APSM_ERR_INVALID_ARG;
+    if (N > 0 && (!aligned16(rx) || (reinterpret_cast<uintptr_t>(soft) & 7))) return APSM_ERR_INVALID_ARG;
     if (p->dtype != APSM_FP32) return APSM_ERR_UNSUPPORTED;
     if ((s = check_device()) != APSM_OK) return s;
     if (N == 0) return APSM_OK;
@@ -329,7 +329,7 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     da.partial = nullptr;
     da.status = st->meta + 3;
     const DetectShape sh = detect_shape(p->M, N);
-    if (det(da, 1, sh.threads, sh.qpt, static_cast<cudaStream_t>(stream)) != cudaSuccess) return APSM_ERR_CUDA;
+    if (det(da, 1, sh, static_cast<cudaStream_t>(stream)) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches++;
     return APSM_OK;
 }

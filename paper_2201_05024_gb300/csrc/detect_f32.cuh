@@ -10,13 +10,28 @@
 // One complex inner product per (query, entry) pair yields all four real-split Gaussian kernel
 // values of Sec. II-A (r2 is r1 rotated, so distances between like halves coincide).
 //
+// With k2 = log2(e)/s2 the exponentials factor as
+//   E_A = 2^(-k2 n_s) * 2^(-k2 n_t) * 2^(2 k2 Re z)      (likewise E_B, E_C with +-Im z),
+// so the query factor is applied once after the sum, the entry factor is folded into the
+// entry's coefficients once per tile, and a pair costs its inner product, three MUFU ex2 and
+// the coefficient FMAs -- no per-pair adds.  The factored form is exact in real arithmetic and
+// keeps every factor inside the FP32 range while k2 n <= kFactorLimit for all queries and
+// entries involved (then |2 k2 z| <= k2 (n_s + n_t) <= 2 kFactorLimit); a tile or a CTA outside
+// that range takes a guarded form that forms each squared distance by direct differences.
+// Inside the range the norm expansion costs at most ~2 kFactorLimit FP32 roundings of absolute
+// error in the exponent (a relative error of a few 1e-5 in E at the range's edge, ~1e-6 for
+// unit-energy inputs); outside it the guarded form has no cancellation at all.
+//
 // Layout and schedule (GB300):
 //  - each thread keeps QPT query vectors in registers and streams the whole dictionary past
 //    them, so accumulators never leave the thread and no reduction is needed;
 //  - dictionary tiles (entries, norms, coefficients; contiguous in the state) are staged into a
 //    two-stage shared-memory ring by the bulk-copy engine (cp.async.bulk + mbarrier), issued by
 //    one thread one tile ahead of the compute; all threads read a tile entry by broadcast;
-//  - exponentials run on MUFU (ex2.approx); the norm-expansion distance is clamped at 0.
+//  - the CTA's threadIdx.y groups take alternate entries of every staged tile for the same
+//    queries (more resident warps without more shared-memory traffic) and merge their partial
+//    sums in a fixed order at the end, so results are deterministic;
+//  - exponentials run on MUFU (ex2.approx);
 //  - partial mode (training, phase A): the grid's y dimension splits the entries into slices;
 //    each slice writes its raw Gaussian sums [slice][query][2K] without the linear part.
 #pragma once
@@ -24,6 +39,13 @@
 #include "apsm_common.cuh"
 
 namespace apsm {
+
+constexpr float kFactorLimit = 60.f;
+
+#ifndef APSM_DETECT_UNROLL
+#define APSM_DETECT_UNROLL 2
+#endif
+constexpr int kDetectUnroll = APSM_DETECT_UNROLL;
 
 struct DetectArgs {
     const float2 *rx;          // [N][M] queries
@@ -49,9 +71,39 @@ struct DetectSmem {
     static constexpr int kNormBytes = kTileEntries * 4;
     static constexpr int kGamBytes = kTileEntries * 2 * K * 4;
     static constexpr int kStageBytes = round_up(kDictBytes + kNormBytes + kGamBytes, 128);
-    static constexpr int kClinOffset = 128 + 2 * kStageBytes;
-    static constexpr int kBytes = kClinOffset + M * K * 8;
+    static constexpr int kScaledOffset = 128 + 2 * kStageBytes;          // coefficients x entry factor
+    static constexpr int kFlagOffset = kScaledOffset + kGamBytes;        // tile in factor range
+    static constexpr int kClinOffset = round_up(kFlagOffset + 16, 16);
+    static constexpr int kReduceOffset = round_up(kClinOffset + M * K * 8, 16);  // entry-split merge
+    // total for a CTA of `threads` x `split` threads with `qpt` queries per thread
+    static constexpr int bytes(int threads, int split, int qpt) {
+        return kReduceOffset + (split > 1 ? (split - 1) * threads * qpt * 2 * K * 4 : 0);
+    }
 };
+
+// 2K consecutive floats from shared memory with the widest aligned vector loads.
+template <int K>
+__device__ __forceinline__ void load_coef(const float *src, float (&g1)[K], float (&g2)[K]) {
+    float v[2 * K];
+    if constexpr ((2 * K) % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < 2 * K; j += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(src + j);
+            v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 2 * K; j += 2) {
+            const float2 x = *reinterpret_cast<const float2 *>(src + j);
+            v[j] = x.x; v[j + 1] = x.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        g1[k] = v[k];
+        g2[k] = v[K + k];
+    }
+}
 
 template <int M, int K, int QPT>
 __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
@@ -59,7 +111,11 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     unsigned char *stage0 = smem + 128;
+    float *s_gs = reinterpret_cast<float *>(smem + S::kScaledOffset);
+    int *s_flag = reinterpret_cast<int *>(smem + S::kFlagOffset);
     float2 *s_clin = reinterpret_cast<float2 *>(smem + S::kClinOffset);
+    float *s_red = reinterpret_cast<float *>(smem + S::kReduceOffset);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
 
     int n_ent = a.n_entries;
     if (a.meta) n_ent = min(n_ent, max(__ldg(a.meta), 0));
@@ -76,23 +132,26 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
         bulk_g2s(st + S::kDictBytes + S::kNormBytes, a.gamma + (size_t)e0 * 2 * K, S::kGamBytes, &bar[tile & 1]);
     };
 
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
     if (a.partial == nullptr)
-        for (int i = threadIdx.x; i < M * K; i += blockDim.x) s_clin[i] = a.clin[i];
+        for (int i = tid; i < M * K; i += nthreads) s_clin[i] = a.clin[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         if (n_tiles > 0) issue(0);
         if (n_tiles > 1) issue(1);
     }
 
-    // Queries of this thread, in registers.
+    // Queries of this thread, in registers, pre-scaled by g2 = 2 k2 so that the inner product
+    // directly gives the exponent 2 k2 z of the factored form.
+    const float g2 = 2.f * a.k2;
     const int q_base = blockIdx.x * blockDim.x * QPT + threadIdx.x;
     float2 r[QPT][M];
     float hq[QPT];  // -k2 * n_s
+    bool q_in_range = true;
 #pragma unroll
     for (int i = 0; i < QPT; ++i) {
         const int q = q_base + i * blockDim.x;
@@ -112,7 +171,16 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 #pragma unroll
         for (int m = 0; m < M; ++m) n = fmaf(r[i][m].x, r[i][m].x, fmaf(r[i][m].y, r[i][m].y, n));
         hq[i] = -a.k2 * n;
+        q_in_range = q_in_range && (a.k2 * n <= kFactorLimit);
+#pragma unroll
+        for (int m = 0; m < M; ++m) r[i][m] = make_float2(g2 * r[i][m].x, g2 * r[i][m].y);
     }
+    const bool cta_in_range = __syncthreads_and(q_in_range);
+    // The query factor 2^(-k2 n_s) multiplies the sum at the end when the CTA is in range; the
+    // direct form then pre-multiplies its terms by the inverse factor (at most 2^kFactorLimit).
+    float qs[QPT];
+#pragma unroll
+    for (int i = 0; i < QPT; ++i) qs[i] = cta_in_range ? ex2(-hq[i]) : 1.f;
 
     float acc1[QPT][K], acc2[QPT][K];
 #pragma unroll
@@ -120,21 +188,34 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 #pragma unroll
         for (int k = 0; k < K; ++k) acc1[i][k] = acc2[i][k] = 0.f;
 
-    const float g2 = 2.f * a.k2;
     for (int tile = 0; tile < n_tiles; ++tile) {
         const bool ok = mbar_wait_bounded(&bar[tile & 1], (tile >> 1) & 1);
+        const unsigned char *st = stage0 + (tile & 1) * S::kStageBytes;
+        const float2 *sd = reinterpret_cast<const float2 *>(st);
+        const float *sn = reinterpret_cast<const float *>(st + S::kDictBytes);
+        const float *sg = reinterpret_cast<const float *>(st + S::kDictBytes + S::kNormBytes);
+        const int cnt = min(kTileEntries, e_end - (e_begin + tile * kTileEntries));
+        // fold the entry factor 2^(-k2 n_t) into the tile's coefficients
+        if (tid == 0) *s_flag = 1;
+        __syncthreads();
         if (ok) {
-            const unsigned char *st = stage0 + (tile & 1) * S::kStageBytes;
-            const float2 *sd = reinterpret_cast<const float2 *>(st);
-            const float *sn = reinterpret_cast<const float *>(st + S::kDictBytes);
-            const float *sg = reinterpret_cast<const float *>(st + S::kDictBytes + S::kNormBytes);
-            const int cnt = min(kTileEntries, e_end - (e_begin + tile * kTileEntries));
-#pragma unroll 1
-            for (int t = 0; t < cnt; ++t) {
-                // complex inner product z = r_t^H r_s for every query of the thread
-                float zr0[QPT], zi0[QPT], zr1[QPT], zi1[QPT];
+            for (int i = tid; i < cnt * 2 * K; i += nthreads) {
+                const float ht = a.k2 * sn[i / (2 * K)];
+                if (ht > kFactorLimit) *s_flag = 0;
+                s_gs[i] = sg[i] * ex2(-ht);
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) report(a.status, APSM_ERR_TIMEOUT);
+            return;
+        }
+        if (cta_in_range && *s_flag) {
+            // factored form: E = ex2(2 k2 z) against coefficients already scaled by 2^(-k2 n_t)
+#pragma unroll kDetectUnroll
+            for (int t = threadIdx.y; t < cnt; t += blockDim.y) {
+                float zr[QPT], zi[QPT];
 #pragma unroll
-                for (int i = 0; i < QPT; ++i) zr0[i] = zi0[i] = zr1[i] = zi1[i] = 0.f;
+                for (int i = 0; i < QPT; ++i) zr[i] = zi[i] = 0.f;
                 const float4 *d4 = reinterpret_cast<const float4 *>(sd + t * M);
 #pragma unroll
                 for (int m = 0; m < M / 2; ++m) {
@@ -142,30 +223,21 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 #pragma unroll
                     for (int i = 0; i < QPT; ++i) {
                         const float2 x0 = r[i][2 * m], x1 = r[i][2 * m + 1];
-                        zr0[i] = fmaf(d.x, x0.x, zr0[i]);
-                        zr0[i] = fmaf(d.y, x0.y, zr0[i]);
-                        zi0[i] = fmaf(d.x, x0.y, zi0[i]);
-                        zi0[i] = fmaf(-d.y, x0.x, zi0[i]);
-                        zr1[i] = fmaf(d.z, x1.x, zr1[i]);
-                        zr1[i] = fmaf(d.w, x1.y, zr1[i]);
-                        zi1[i] = fmaf(d.z, x1.y, zi1[i]);
-                        zi1[i] = fmaf(-d.w, x1.x, zi1[i]);
+                        zr[i] = fmaf(d.x, x0.x, zr[i]);
+                        zi[i] = fmaf(d.x, x0.y, zi[i]);
+                        zr[i] = fmaf(d.y, x0.y, zr[i]);
+                        zi[i] = fmaf(-d.y, x0.x, zi[i]);
+                        zr[i] = fmaf(d.z, x1.x, zr[i]);
+                        zi[i] = fmaf(d.z, x1.y, zi[i]);
+                        zr[i] = fmaf(d.w, x1.y, zr[i]);
+                        zi[i] = fmaf(-d.w, x1.x, zi[i]);
                     }
                 }
-                const float ht = -a.k2 * sn[t];
                 float gm1[K], gm2[K];
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    gm1[k] = sg[t * 2 * K + k];
-                    gm2[k] = sg[t * 2 * K + K + k];
-                }
+                load_coef<K>(s_gs + t * 2 * K, gm1, gm2);
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) {
-                    const float zr = zr0[i] + zr1[i], zi = zi0[i] + zi1[i];
-                    const float h = hq[i] + ht;  // -k2 (n_s + n_t)
-                    const float eA = ex2(fminf(fmaf(g2, zr, h), 0.f));
-                    const float eB = ex2(fminf(fmaf(g2, zi, h), 0.f));
-                    const float eC = ex2(fminf(fmaf(-g2, zi, h), 0.f));
+                    const float eA = ex2(zr[i]), eB = ex2(zi[i]), eC = ex2(-zi[i]);
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         acc1[i][k] = fmaf(gm1[k], eA, fmaf(gm2[k], eC, acc1[i][k]));
@@ -173,39 +245,104 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
                     }
                 }
             }
+        } else {
+            // guarded form for norms outside the factor range: the three squared distances by
+            // direct differences (no norm expansion, so no cancellation when ||r||^2 dominates):
+            //   A = ||r_t - r_s||^2,  B = ||r_t + i r_s||^2 (= ||r1(t) - r2(s)||^2),
+            //   C = ||r_t - i r_s||^2 (= ||r2(t) - r1(s)||^2)
+            const float inv_g2 = 1.f / g2;
+#pragma unroll 1
+            for (int t = threadIdx.y; t < cnt; t += blockDim.y) {
+                float dA[QPT], dB[QPT], dC[QPT];
+#pragma unroll
+                for (int i = 0; i < QPT; ++i) dA[i] = dB[i] = dC[i] = 0.f;
+#pragma unroll
+                for (int m = 0; m < M; ++m) {
+                    const float2 d = sd[t * M + m];
+#pragma unroll
+                    for (int i = 0; i < QPT; ++i) {
+                        const float sx = r[i][m].x * inv_g2, sy = r[i][m].y * inv_g2;
+                        const float ax = d.x - sx, ay = d.y - sy;
+                        const float bx = d.x - sy, by = d.y + sx;
+                        const float cx = d.x + sy, cy = d.y - sx;
+                        dA[i] = fmaf(ax, ax, fmaf(ay, ay, dA[i]));
+                        dB[i] = fmaf(bx, bx, fmaf(by, by, dB[i]));
+                        dC[i] = fmaf(cx, cx, fmaf(cy, cy, dC[i]));
+                    }
+                }
+                float gm1[K], gm2[K];
+                load_coef<K>(sg + t * 2 * K, gm1, gm2);
+#pragma unroll
+                for (int i = 0; i < QPT; ++i) {
+                    const float eA = ex2(-a.k2 * dA[i]), eB = ex2(-a.k2 * dB[i]), eC = ex2(-a.k2 * dC[i]);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        acc1[i][k] = fmaf(gm1[k] * qs[i], eA, fmaf(gm2[k] * qs[i], eC, acc1[i][k]));
+                        acc2[i][k] = fmaf(gm1[k] * qs[i], eB, fmaf(gm2[k] * qs[i], eA, acc2[i][k]));
+                    }
+                }
+            }
         }
         if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) report(a.status, APSM_ERR_TIMEOUT);
+            if (tid == 0) report(a.status, APSM_ERR_TIMEOUT);
             return;
         }
-        if (threadIdx.x == 0 && tile + 2 < n_tiles) issue(tile + 2);
+        if (tid == 0 && tile + 2 < n_tiles) issue(tile + 2);
     }
 
+    // merge the entry groups' partial sums in group order (group 0 keeps and finishes them)
+    if (blockDim.y > 1) {
+        if (threadIdx.y > 0) {
+            float *dst = s_red + ((size_t)(threadIdx.y - 1) * blockDim.x + threadIdx.x) * QPT * 2 * K;
+#pragma unroll
+            for (int i = 0; i < QPT; ++i)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    dst[(i * 2 + 0) * K + k] = acc1[i][k];
+                    dst[(i * 2 + 1) * K + k] = acc2[i][k];
+                }
+        }
+        __syncthreads();
+        if (threadIdx.y > 0) return;
+        for (int y = 1; y < (int)blockDim.y; ++y) {
+            const float *src = s_red + ((size_t)(y - 1) * blockDim.x + threadIdx.x) * QPT * 2 * K;
+#pragma unroll
+            for (int i = 0; i < QPT; ++i)
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    acc1[i][k] += src[(i * 2 + 0) * K + k];
+                    acc2[i][k] += src[(i * 2 + 1) * K + k];
+                }
+        }
+    }
+
+    const float inv_g2 = 1.f / g2;
 #pragma unroll
     for (int i = 0; i < QPT; ++i) {
         const int q = q_base + i * blockDim.x;
         if (q >= a.N) continue;
+        const float fq = cta_in_range ? ex2(hq[i]) : 1.f;  // query factor 2^(-k2 n_s)
         if (a.partial != nullptr) {
             float *dst = a.partial + ((size_t)blockIdx.y * a.N + q) * 2 * K;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                dst[k] = acc1[i][k];
-                dst[K + k] = acc2[i][k];
+                dst[k] = fq * acc1[i][k];
+                dst[K + k] = fq * acc2[i][k];
             }
             continue;
         }
         unsigned char hbits[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            float l1 = 0.f, l2 = 0.f;  // c_k^H r = sum_m conj(c[m][k]) r[m]
+            float l1 = 0.f, l2 = 0.f;  // c_k^H r = sum_m conj(c[m][k]) r[m]  (r held as g2 r)
 #pragma unroll
             for (int m = 0; m < M; ++m) {
                 const float2 c = s_clin[m * K + k];
                 l1 = fmaf(c.x, r[i][m].x, fmaf(c.y, r[i][m].y, l1));
                 l2 = fmaf(c.x, r[i][m].y, fmaf(-c.y, r[i][m].x, l2));
             }
-            const float y1 = fmaf(a.wL, l1, a.wG * acc1[i][k]);
-            const float y2 = fmaf(a.wL, l2, a.wG * acc2[i][k]);
+            const float y1 = fmaf(a.wL * inv_g2, l1, a.wG * fq * acc1[i][k]);
+            const float y2 = fmaf(a.wL * inv_g2, l2, a.wG * fq * acc2[i][k]);
             a.soft[(size_t)q * K + k] = make_float2(y1, y2);
             hbits[k] = (unsigned char)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
         }
@@ -217,31 +354,38 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 }
 
 // Host-side launcher for one (M, K) instantiation.
+// Launch shape: `threads` query lanes x `split` entry groups per CTA, `qpt` queries per lane.
+struct DetectShape {
+    int threads, split, qpt;
+};
+
 template <int M, int K>
-cudaError_t launch_detect_f32(const DetectArgs &a, int grid_y, int threads, int qpt, cudaStream_t stream) {
+cudaError_t launch_detect_f32(const DetectArgs &a, int grid_y, DetectShape sh, cudaStream_t stream) {
     using S = DetectSmem<M, K>;
-    const int per_cta = threads * qpt;
+    if constexpr (M > 16) sh.qpt = 1;
+    const int per_cta = sh.threads * sh.qpt;
     const int gx = (a.N + per_cta - 1) / per_cta;
     if (gx == 0 || grid_y == 0) return cudaSuccess;
-    dim3 grid(gx, grid_y);
+    const dim3 grid(gx, grid_y), block(sh.threads, sh.split);
+    const int smem = S::bytes(sh.threads, sh.split, sh.qpt);
     if constexpr (M <= 16) {
-        if (qpt == 2) {
+        if (sh.qpt == 2) {
             auto fn = detect_f32_kernel<M, K, 2>;
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
-            fn<<<grid, threads, S::kBytes, stream>>>(a);
+            fn<<<grid, block, smem, stream>>>(a);
             return cudaGetLastError();
         }
     }
     {
         auto fn = detect_f32_kernel<M, K, 1>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        fn<<<grid, threads, S::kBytes, stream>>>(a);
+        fn<<<grid, block, smem, stream>>>(a);
     }
     return cudaGetLastError();
 }
 
-using DetectLauncher = cudaError_t (*)(const DetectArgs &, int, int, int, cudaStream_t);
+using DetectLauncher = cudaError_t (*)(const DetectArgs &, int, DetectShape, cudaStream_t);
 
 }  // namespace apsm

@@ -11,8 +11,8 @@
 // kernel values kappa(x_i, x_m) between samples of L; dropping a dictionary entry subtracts its
 // Gaussian terms.  The expensive part -- f at the start of the chunk evaluated at the chunk's
 // new samples against the whole dictionary -- is the detection kernel in partial mode, run on
-// all SMs between chunks (phase A).  The serial part (phase B) is one CTA with one warp per
-// user: users are independent, so a step needs only warp-level synchronisation.
+// all SMs between chunks (phase A).  The serial part (phase B) runs one CTA per user (users are
+// independent) with one thread per live-range sample, so a step is one CTA barrier.
 //
 // Kernels:
 //   train_gram_kernel   kappa(x_u, x_v) for all u, v in L of every chunk (sum kernel, Fact 1)
@@ -29,6 +29,8 @@ struct TrainGeom {
     int T;         // pilots per chunk
     int n_chunks;
     int RMAX;      // 2T + W - 1: live-range capacity
+    int RS;        // row stride of the per-chunk kernel tables: RMAX rounded up to 32
+    int WP;        // window W rounded up to a supported multiple of 4
     int slice;     // entries per phase-A slice
 };
 
@@ -59,41 +61,12 @@ __device__ inline void sample_pair(const float2 *ra, const float2 *rb, int M, in
     dist2 = fmaxf(na + nb - 2.f * dot, 0.f);
 }
 
-__global__ void train_gram_kernel(const float2 *__restrict__ rx, TrainGeom g, float k2, float wL, float wG,
-                                  float *__restrict__ kmat, float *__restrict__ gev) {
-    const int c = blockIdx.y;
-    int t0, Tc, s0, s1, l0;
-    chunk_range(g, c, t0, Tc, s0, s1, l0);
-    const int R = s1 - l0;
-    const int RM = g.RMAX;
-    const int n_k = RM * RM, n_e = g.T * 2 * RM;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_k + n_e; idx += gridDim.x * blockDim.x) {
-        if (idx < n_k) {
-            const int u = idx / RM, v = idx % RM;
-            float val = 0.f;
-            if (u < R && v < R) {
-                const int mu_ = l0 + u, mv = l0 + v;
-                float dot, d2;
-                sample_pair(rx + (size_t)(mu_ >> 1) * g.M, rx + (size_t)(mv >> 1) * g.M, g.M, mu_ & 1, mv & 1, dot,
-                            d2);
-                val = fmaf(wL, dot, wG * ex2(-k2 * d2));  // kappa = w_L kappa_L + w_G kappa_G (Fact 1)
-            }
-            kmat[(size_t)c * n_k + idx] = val;
-        } else {
-            const int j = idx - n_k;
-            const int e = j / (2 * RM), l = (j / RM) & 1, v = j % RM;
-            const int t = t0 + e;
-            float val = 0.f;
-            if (e < Tc && t >= g.D && v < R) {
-                const int mv = l0 + v;
-                float dot, d2;
-                sample_pair(rx + (size_t)(t - g.D) * g.M, rx + (size_t)(mv >> 1) * g.M, g.M, l, mv & 1, dot, d2);
-                val = ex2(-k2 * d2);
-            }
-            gev[(size_t)c * n_e + j] = val;
-        }
-    }
-}
+// Tables per chunk c (row stride RS, zero outside the live range):
+//   kmat[c][u][v] = kappa(x_{l0+u}, x_{l0+v})                       u, v < R
+//   gev[c][e][l][v] = kappa_G(x_{2(t0+e-D)+l}, x_{l0+v})            entry t0+e-D dropped at n = 2(t0+e)
+// (train_gram_kernel, defined in train_chunk.cu).
+cudaError_t launch_train_gram(const float2 *rx, const TrainGeom &g, float k2, float wL, float wG, float *kmat,
+                              float *gev, cudaStream_t stream);
 
 struct ChunkArgs {
     TrainGeom g;
@@ -106,192 +79,203 @@ struct ChunkArgs {
     float *gamma;           // [A][2][K]
     float2 *clin;           // [M][K]
     int *meta;              // [4]
-    const float *kmat;      // [n_chunks][RMAX][RMAX]
-    const float *gev;       // [n_chunks][T][2][RMAX]
+    const float *kmat;      // [n_chunks][RS][RS]
+    const float *gev;       // [n_chunks][T][2][RS]
     const float *partial;   // [n_slices][Tc][2K]
     int n_slices;
     float *carry;           // [W][K]
     int8_t *case_log;       // [2P][W][K] nullable
 };
 
+// Shared-memory layout of phase B (bytes; every region 16-byte aligned).
 struct ChunkSmem {
-    int kmat, gev, egam, beta, dg, pil, bytes;
+    int bar, kmat, gev, egam, beta, dg, clin, pil, bytes;
     __host__ __device__ ChunkSmem(const TrainGeom &g) {
-        const int RM = g.RMAX;
+        const int RS = g.RS;
         const int npil = g.T + (g.W + 1) / 2 + 1;
-        kmat = 0;
-        gev = kmat + RM * RM * 4;
-        egam = gev + g.T * 2 * RM * 4;
-        beta = egam + g.T * 2 * g.K * 4;
-        dg = beta + g.K * 2 * RM * 4;
-        pil = round_up(dg + g.K * RM * 4, 16);
+        bar = 0;
+        kmat = 16;                                   // WP zero rows, then RS rows of RS
+        gev = kmat + (g.WP + RS) * RS * 4;
+        egam = gev + (g.P > g.D ? g.T * 2 * RS * 4 : 0);   // dropped-entry table only when P > D
+        beta = egam + round_up(g.T * 2 * 4, 16);
+        dg = beta + 2 * (RS + g.WP) * 4;
+        clin = dg + RS * 4;
+        pil = clin + round_up(g.M * 8, 16);
         bytes = pil + npil * g.M * 8;
     }
 };
 
-template <int S>
-__global__ void __launch_bounds__(512) train_chunk_kernel(const ChunkArgs a) {
+// Phase B of one chunk for one user (blockIdx.x = k).  Thread u owns live-range sample u
+// (RS = 32 S threads); a step is one CTA barrier: window threads publish their beta, then every
+// thread adds the window's contribution to its own prediction.  WP is the window rounded up to a
+// multiple of 4; the WP slots below the window hold zero so the sum has a fixed length.
+template <int S, int WP>
+__global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int RS = 32 * S;
     const TrainGeom &g = a.g;
     const ChunkSmem L(g);
-    float *s_kmat = reinterpret_cast<float *>(smem + L.kmat);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
+    float *s_kmat = reinterpret_cast<float *>(smem + L.kmat) + WP * RS;  // row 0 after WP zero rows
     float *s_gev = reinterpret_cast<float *>(smem + L.gev);
     float *s_egam = reinterpret_cast<float *>(smem + L.egam);
     float *s_beta = reinterpret_cast<float *>(smem + L.beta);
     float *s_dg = reinterpret_cast<float *>(smem + L.dg);
+    float2 *s_clin = reinterpret_cast<float2 *>(smem + L.clin);
     float2 *s_pil = reinterpret_cast<float2 *>(smem + L.pil);
 
-    const int M = g.M, K = g.K, W = g.W, D = g.D, RM = g.RMAX;
+    const int M = g.M, K = g.K, W = g.W, D = g.D;
     int t0, Tc, s0, s1, l0;
     chunk_range(g, a.chunk, t0, Tc, s0, s1, l0);
     const int R = s1 - l0;
-    const int pa0 = l0 >> 1;            // first pilot touching L
+    const int pa0 = l0 >> 1;  // first pilot touching L
     const int npil = t0 + Tc - pa0;
-    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int k = blockIdx.x;  // user
+    const int u = threadIdx.x;  // live-range sample of this thread
+    const bool evict = (t0 + Tc - 1) >= D;
 
-    // ---- stage the chunk's kernel values, dropped-entry data and pilots -------------------
-    {
-        const float *src = a.kmat + (size_t)a.chunk * RM * RM;
-        for (int i = tid; i < RM * RM; i += nthr) s_kmat[i] = src[i];
-        const bool evict = (t0 + Tc - 1) >= D;
-        if (evict) {
-            const float *gs = a.gev + (size_t)a.chunk * g.T * 2 * RM;
-            for (int i = tid; i < g.T * 2 * RM; i += nthr) s_gev[i] = gs[i];
-            for (int i = tid; i < Tc * 2 * K; i += nthr) {
-                const int e = i / (2 * K), r = i % (2 * K);
-                const int t = t0 + e;
-                s_egam[i] = (t >= D) ? a.gamma[(size_t)((t - D) % D) * 2 * K + r] : 0.f;
+    // ---- stage the chunk's kernel tables and pilots with the bulk-copy engine ---------------
+    if (u == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        const uint32_t kb = (uint32_t)R * RS * 4, gb = evict ? (uint32_t)Tc * 2 * RS * 4 : 0u,
+                       pb = (uint32_t)npil * M * 8;
+        mbar_arrive_expect_tx(bar, kb + gb + pb);
+        bulk_g2s(s_kmat, a.kmat + (size_t)a.chunk * RS * RS, kb, bar);
+        if (evict) bulk_g2s(s_gev, a.gev + (size_t)a.chunk * g.T * 2 * RS, gb, bar);
+        bulk_g2s(s_pil, a.rx + (size_t)pa0 * M, pb, bar);
+    }
+    for (int mm = u; mm < M; mm += RS) s_clin[mm] = a.clin[mm * K + k];
+    for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
+    for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
+    // coefficients of the entries dropped in this chunk (entry t0+e-D at step 2(t0+e))
+    if (evict && u < 2 * Tc) {
+        const int e = u >> 1, l = u & 1;
+        s_egam[u] = (t0 + e >= D) ? a.gamma[((size_t)((t0 + e - D) % D) * 2 + l) * K + k] : 0.f;
+    }
+
+    // ---- this thread's sample: target, coefficient, prediction at chunk start ---------------
+    float p = 0.f, gam = 0.f, b = 0.f;
+    const bool valid = u < R;
+    const int m = l0 + u, pa = m >> 1, l = m & 1;
+    if (valid) {
+        const float2 sy = a.sym[(size_t)pa * K + k];
+        b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
+        if (m < s0) {
+            p = a.carry[u * K + k];
+            gam = a.gamma[((size_t)(pa % D) * 2 + l) * K + k];
+        } else {
+            // Gaussian part of f_{s0}(x_m) from the phase-A slices: eight interleaved partial sums
+            // (loads in flight together), combined in a fixed order
+            const float *src = a.partial + (size_t)(pa - t0) * 2 * K + l * K + k;
+            const size_t stride = (size_t)Tc * 2 * K;
+            float gs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            int sl = 0;
+            for (; sl + 8 <= a.n_slices; sl += 8) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) gs[j] += src[(sl + j) * stride];
             }
+            for (int j = 0; sl + j < a.n_slices; ++j) gs[j] += src[(sl + j) * stride];
+            p = a.wG * (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])));
         }
-        for (int i = tid; i < npil * M; i += nthr) s_pil[i] = a.rx[(size_t)pa0 * M + i];
+    }
+    const float gam0 = gam;
+    __syncthreads();
+    if (!mbar_wait_bounded(bar, 0)) {
+        if (u == 0) report(a.meta + 3, APSM_ERR_TIMEOUT);
+        return;
+    }
+    float rk = 0.f;  // 1 / kappa(x_j, x_j)
+    if (valid) {
+        const float kjj = s_kmat[u * RS + u];
+        rk = kjj != 0.f ? 1.f / kjj : 0.f;
+        if (m >= s0) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
+            const float2 *rv = s_pil + (pa - pa0) * M;
+            float lin = 0.f;
+            for (int mm = 0; mm < M; ++mm) {
+                const float2 c = s_clin[mm], x = rv[mm];
+                lin = l ? fmaf(c.x, x.y, fmaf(-c.y, x.x, lin)) : fmaf(c.x, x.x, fmaf(c.y, x.y, lin));
+            }
+            p = fmaf(a.wL, lin, p);
+        }
+    }
+
+    // ---- the recurrence over the chunk's samples -----------------------------------------------
+    const bool log_cases = a.case_log != nullptr;
+    const float muq_full = a.mu / (float)W;  // mu q with q = 1/W once the window is full
+    const float *kcol = s_kmat + u;          // column u of the kernel table
+    for (int n = s0; n < s1; ++n) {
+        const int un = n - l0;
+        // a new pilot arrives at n = 2t: the oldest entry is dropped once D are held
+        if (evict && !(n & 1) && (n >> 1) >= D) {
+            const int e = (n >> 1) - t0;
+            p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u], s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
+        }
+        const int ujlo = max(0, n - W + 1) - l0;
+        const float muq = (n >= W - 1) ? muq_full : a.mu / (float)(n + 1);  // mu q, q = 1/|J_n|
+        float *bb = s_beta + (n & 1) * (WP + RS) + WP;
+        if (u >= ujlo && u <= un) {
+            const float e = p - b;  // <f_n, kappa(x_j,.)> - b_j
+            // Eq. beta without branches: (-e - eps) below the slab, (eps - e) above it, 0 inside
+            const float beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
+            gam = fmaf(muq, beta, gam);
+            bb[u] = beta;
+            if (log_cases)
+                a.case_log[((size_t)n * W + (m - n + W - 1)) * K + k] = (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
+        } else if (u < ujlo && u > un - WP) {
+            bb[u] = 0.f;
+        }
+        __syncthreads();
+        // p_u += mu q sum_{i in J_n} beta_i kappa(x_i, x_u)
+        const float *kp = kcol + (un - WP + 1) * RS;
+        const float *bp = bb + (un - WP + 1);
+        float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+        for (int d = 0; d < WP; d += 2) {
+            acc0 = fmaf(bp[d], kp[d * RS], acc0);
+            acc1 = fmaf(bp[d + 1], kp[(d + 1) * RS], acc1);
+        }
+        p = fmaf(muq, acc0 + acc1, p);
+    }
+
+    // ---- write back: coefficients, carried predictions, linear filter ---------------------------
+    if (valid) {
+        a.gamma[((size_t)(pa % D) * 2 + l) * K + k] = gam;
+        s_dg[u] = gam - gam0;
+        const int l0n = max(0, s1 - W + 1);
+        if (m >= l0n) a.carry[(m - l0n) * K + k] = p;
     }
     __syncthreads();
-
-    const int k = tid >> 5, lane = tid & 31;
-    if (k < K) {
-        float p[S], gam[S], gam0[S], b[S];
-        // ---- initial predictions p_m = f_{s0}(x_m) and coefficients ------------------------
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int u = lane + 32 * s;
-            p[s] = gam[s] = gam0[s] = b[s] = 0.f;
-            if (u < R) {
-                const int m = l0 + u, pa = m >> 1, l = m & 1;
-                const float2 sy = a.sym[(size_t)pa * K + k];
-                b[s] = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
-                if (m < s0) {
-                    p[s] = a.carry[u * K + k];
-                    gam[s] = a.gamma[((size_t)(pa % D) * 2 + l) * K + k];
-                } else {
-                    float lin = 0.f;  // Re / Im of c_k^H r
-                    const float2 *rv = s_pil + (pa - pa0) * M;
-                    for (int mm = 0; mm < M; ++mm) {
-                        const float2 c = a.clin[mm * K + k], x = rv[mm];
-                        lin = l ? fmaf(c.x, x.y, fmaf(-c.y, x.x, lin)) : fmaf(c.x, x.x, fmaf(c.y, x.y, lin));
-                    }
-                    float gs = 0.f;
-                    for (int sl = 0; sl < a.n_slices; ++sl)
-                        gs += a.partial[((size_t)sl * Tc + (pa - t0)) * 2 * K + l * K + k];
-                    p[s] = fmaf(a.wL, lin, a.wG * gs);
-                }
-                gam0[s] = gam[s];
-            }
+    // c_k += sum_u dgamma_u x~_u, with x~ = r(t) for r1(t) and -i r(t) for r2(t)
+    for (int mm = u; mm < M; mm += RS) {
+        float2 c = s_clin[mm];
+        for (int v = 0; v < R; ++v) {
+            const int mv = l0 + v;
+            const float d = s_dg[v];
+            const float2 x = s_pil[((mv >> 1) - pa0) * M + mm];
+            if (mv & 1) { c.x = fmaf(d, x.y, c.x); c.y = fmaf(-d, x.x, c.y); }
+            else        { c.x = fmaf(d, x.x, c.x); c.y = fmaf(d, x.y, c.y); }
         }
-
-        // ---- the recurrence over the chunk's samples -----------------------------------------
-        float *beta_buf = s_beta + k * 2 * RM;
-        for (int n = s0; n < s1; ++n) {
-            const int un = n - l0;
-            // a new pilot arrives at n = 2t: the oldest entry is dropped once D are held
-            if (!(n & 1) && (n >> 1) >= D) {
-                const int e = (n >> 1) - t0;
-                const float ge1 = s_egam[(e * 2 + 0) * K + k], ge2 = s_egam[(e * 2 + 1) * K + k];
-                const float *gv = s_gev + e * 2 * RM;
-#pragma unroll
-                for (int s = 0; s < S; ++s) {
-                    const int u = lane + 32 * s;
-                    if (u < R && u >= un - W + 1) p[s] -= a.wG * fmaf(ge1, gv[u], ge2 * gv[RM + u]);
-                }
-            }
-            const int jlo = max(0, n - W + 1);
-            const int ujlo = jlo - l0;
-            const float muq = a.mu / (float)(n - jlo + 1);  // mu q, q = 1/|J_n|
-            float *bb = beta_buf + (n & 1) * RM;
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int u = lane + 32 * s;
-                if (u >= ujlo && u <= un) {
-                    const float e = p[s] - b[s];                 // <f_n, kappa(x_j,.)> - b_j
-                    const float kjj = s_kmat[u * RM + u];         // kappa(x_j, x_j)
-                    int cs = 0;
-                    float beta = 0.f;                              // Eq. beta
-                    if (e < -a.eps) { cs = -1; beta = (-e - a.eps) / kjj; }
-                    else if (e > a.eps) { cs = 1; beta = (-e + a.eps) / kjj; }
-                    if (kjj == 0.f) beta = 0.f;
-                    gam[s] = fmaf(muq, beta, gam[s]);
-                    bb[u] = beta;
-                    if (a.case_log) a.case_log[((size_t)n * W + (l0 + u - n + W - 1)) * K + k] = (int8_t)cs;
-                }
-            }
-            __syncwarp();
-#pragma unroll
-            for (int s = 0; s < S; ++s) {
-                const int u = lane + 32 * s;
-                if (u < R && u >= un - W + 2) {
-                    float acc = 0.f;
-                    for (int i = ujlo; i <= un; ++i) acc = fmaf(bb[i], s_kmat[i * RM + u], acc);
-                    p[s] = fmaf(muq, acc, p[s]);
-                }
-            }
-        }
-
-        // ---- write back: coefficients, linear filter, carried predictions -------------------
-        float *dg = s_dg + k * RM;
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int u = lane + 32 * s;
-            if (u < R) {
-                const int m = l0 + u, pa = m >> 1, l = m & 1;
-                a.gamma[((size_t)(pa % D) * 2 + l) * K + k] = gam[s];
-                dg[u] = gam[s] - gam0[s];
-            }
-        }
-        const int l0n = max(0, s1 - W + 1);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const int u = lane + 32 * s;
-            if (u < R && l0 + u >= l0n) a.carry[(l0 + u - l0n) * K + k] = p[s];
-        }
-        __syncwarp();
-        // c_k += sum_u dgamma_u x~_u, with x~ = r(t) for r1(t) and -i r(t) for r2(t)
-        for (int mm = lane; mm < M; mm += 32) {
-            float2 c = a.clin[mm * K + k];
-            for (int u = 0; u < R; ++u) {
-                const int m = l0 + u, pa = m >> 1;
-                const float d = dg[u];
-                const float2 x = s_pil[(pa - pa0) * M + mm];
-                if (m & 1) { c.x = fmaf(d, x.y, c.x); c.y = fmaf(-d, x.x, c.y); }
-                else       { c.x = fmaf(d, x.x, c.x); c.y = fmaf(d, x.y, c.y); }
-            }
-            a.clin[mm * K + k] = c;
-        }
+        a.clin[mm * K + k] = c;
     }
 
     // ---- new dictionary entries of this chunk (slot t % D), their norms, bookkeeping -------
-    for (int i = tid; i < Tc * M; i += nthr) {
-        const int t = t0 + i / M, mm = i % M;
-        a.dict[(size_t)(t % D) * M + mm] = s_pil[(t - pa0) * M + mm];
-    }
-    for (int i = tid; i < Tc; i += nthr) {
-        const float2 *rv = s_pil + (t0 + i - pa0) * M;
-        float nrm = 0.f;
-        for (int mm = 0; mm < M; ++mm) nrm = fmaf(rv[mm].x, rv[mm].x, fmaf(rv[mm].y, rv[mm].y, nrm));
-        a.dict_norm[(t0 + i) % D] = nrm;
-    }
-    if (a.chunk == g.n_chunks - 1 && tid == 0) {
-        a.meta[0] = min(g.P, D);
-        a.meta[1] = g.P >= D ? g.P % D : 0;
-        a.meta[2] = g.P;
+    if (k == 0) {
+        for (int i = u; i < Tc * M; i += RS) {
+            const int t = t0 + i / M, mm = i % M;
+            a.dict[(size_t)(t % D) * M + mm] = s_pil[(t - pa0) * M + mm];
+        }
+        for (int i = u; i < Tc; i += RS) {
+            const float2 *rv = s_pil + (t0 + i - pa0) * M;
+            float nrm = 0.f;
+            for (int mm = 0; mm < M; ++mm) nrm = fmaf(rv[mm].x, rv[mm].x, fmaf(rv[mm].y, rv[mm].y, nrm));
+            a.dict_norm[(t0 + i) % D] = nrm;
+        }
+        if (a.chunk == g.n_chunks - 1 && u == 0) {
+            a.meta[0] = min(g.P, D);
+            a.meta[1] = g.P >= D ? g.P % D : 0;
+            a.meta[2] = g.P;
+        }
     }
 }
 

@@ -76,7 +76,7 @@ def test_workspace_query(lib):
     assert apsm.train_workspace_bytes(params(), 2048) > nb
 
 
-def _cstate(ptr=1):
+def _cstate(ptr=256):
     from paper_2201_05024_gb300 import apsm
     return apsm._CState(ptr, ptr, ptr, ptr, ptr)
 
@@ -93,6 +93,26 @@ def test_null_pointers_rejected_before_device(lib):
     assert lib.apsm_train(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(256), 64, None,
                           ctypes.byref(_cstate()), ctypes.c_void_p(256), 16, None, None) == apsm.APSM_ERR_WORKSPACE
     assert lib.apsm_read_status(None, None, None) == 1
+
+
+def test_misaligned_arrays_rejected_before_device(lib):
+    p = params().c()
+    good = _cstate(256)
+    from paper_2201_05024_gb300 import apsm
+    bad_state = apsm._CState(256 + 8, 256, 256, 256, 256)     # dict only 8-byte aligned
+    rc = lib.apsm_detect(ctypes.byref(p), ctypes.byref(bad_state), ctypes.c_void_p(256), 4, ctypes.c_void_p(256),
+                         None, None)
+    assert rc == apsm.APSM_ERR_INVALID_ARG
+    rc = lib.apsm_detect(ctypes.byref(p), ctypes.byref(good), ctypes.c_void_p(256 + 8), 4, ctypes.c_void_p(256),
+                         None, None)                          # rx only 8-byte aligned
+    assert rc == apsm.APSM_ERR_INVALID_ARG
+    nb = apsm.train_workspace_bytes(params(), 64)
+    rc = lib.apsm_train(ctypes.byref(p), ctypes.c_void_p(256 + 8), ctypes.c_void_p(256), 64, None, ctypes.byref(good),
+                        ctypes.c_void_p(256), nb, None, None)
+    assert rc == apsm.APSM_ERR_INVALID_ARG
+    rc = lib.apsm_train(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(256), 64, None, ctypes.byref(good),
+                        ctypes.c_void_p(256 + 64), nb, None, None)   # workspace not 256-byte aligned
+    assert rc == apsm.APSM_ERR_INVALID_ARG
 
 
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-device path")

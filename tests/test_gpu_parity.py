@@ -54,6 +54,36 @@ def test_detect_matches_oracle(M, K, D, N, sigma, wL):
     assert apsm.read_status(st) == 0
 
 
+@pytest.mark.parametrize("case", ["offset", "mixed_entries", "mixed_queries"])
+def test_detect_unnormalised_inputs(case):
+    """Inputs outside the range where the factored exponentials are used: a large common offset
+    (||r||^2 >> ||r - r_t||^2, where a norm expansion would cancel), a dictionary whose tiles are
+    partly out of range, and query blocks that are partly out of range."""
+    M, K, D, N = 16, 6, 200, 700
+    rng = np.random.default_rng(11)
+    ent, gam, clin = synth.random_state(M, K, D, instance=5)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=6)
+    rx = inst.rx_data.copy()
+    sigma = 0.5
+    if case == "offset":
+        base = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) * 1.6
+        ent = (ent + base).astype(np.complex64)
+        rx = (rx * 0.5 + base).astype(np.complex64)
+        sigma = 0.8
+    elif case == "mixed_entries":
+        ent = ent.copy()
+        ent[64:128] *= 6.0                      # tiles 2 and 3 out of range
+    else:
+        rx[::97] *= 5.0                          # a few queries out of range
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=sigma, w_L=0.5)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, to_dev(rx))
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), rx)
+    assert_soft_close(soft.cpu().numpy(), ref)
+    assert_hard_match(hard.cpu().numpy(), ref)
+
+
 def test_detect_empty_dictionary_is_linear_filter():
     M, K, N = 16, 6, 200
     ent, gam, clin = synth.random_state(M, K, 0)
