@@ -35,7 +35,7 @@ ORACLE_DETECT_SAMPLE = 4096
 
 # DRAM bytes per launch of the detection kernel from one ncu capture, valid only for the kernel
 # source with this digest (a changed kernel reports null until it is re-captured).
-DETECT_TRAFFIC = {"digest": None, "bytes_per_launch": None}
+DETECT_TRAFFIC = {"digest": "31dca97cec9976ae", "bytes_per_launch": 8.612864e6}
 
 
 def workload_name(w):
@@ -296,7 +296,7 @@ def main():
                    "ms": mean_detect},
         "train": {"value": world * w["P"] * w["K"] / (mean_train / 1e3), "unit": "pilot-updates/s",
                   "ms": mean_train, "us_per_pilot": mean_train * 1e3 / w["P"]},
-        "roofline": {"kernel": "detect_f32_kernel<16,6,2>", "bound": "alu", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "detect_f32_kernel<16,6,1>", "bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": "derived FP32 FMA pipe at max SM clock"},
         "gpu_launches": int(launches),

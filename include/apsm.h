@@ -176,6 +176,30 @@ apsm_status apsm_train_noalloc(const apsm_params *p, const float *rx_pilot, cons
 apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
                         uint8_t *hard, void *stream);
 
+/* Bytes of device workspace apsm_detect_backward needs for N data vectors. */
+apsm_status apsm_detect_backward_workspace_bytes(const apsm_params *p, int32_t N, size_t *bytes);
+
+/*
+ * Adjoint of apsm_detect (not in the paper: the gradient of the detection of Sec. III-B with
+ * respect to the filter and the kernel parameters).  Given dsoft = dL/d(soft) for a real loss L
+ * (as complex numbers: dL/dRe + i dL/dIm), with soft = f(r1) + i f(r2) and
+ * f(x) = w_L <w, x> + w_G sum_i gamma_i kappa_G(c_i, x) (Fact 1, Sec. II-D):
+ *   dgamma[t][l][k] = w_G sum_s (dRe_s^k kappa_G(c_tl, r1(s)) + dIm_s^k kappa_G(c_tl, r2(s)))
+ *   dclin[m][k]     = w_L sum_s conj(dsoft[s][k]) r_s[m]      (gradient with respect to Re c + i Im c)
+ *   dscalars[0]     = dL/dsigma,  dscalars[1] = dL/dw_L  (with w_G = 1 - w_L)
+ * Exponentials are recomputed.  Deterministic (fixed-order reductions, no atomics).
+ *   rx        device [N][M] complex, the data vectors of the forward call
+ *   dsoft     device [N][K] complex
+ *   dgamma    device [A][2][K] float out (slots beyond the entries held are set to 0)
+ *   dclin     device [M][K] complex out
+ *   dscalars  device [2] float out
+ *   workspace device scratch of apsm_detect_backward_workspace_bytes(p, N) bytes, 256-byte aligned
+ * Errors as for apsm_detect, plus APSM_ERR_WORKSPACE.
+ */
+apsm_status apsm_detect_backward(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N,
+                                 const float *dsoft, float *dgamma, float *dclin, float *dscalars, void *workspace,
+                                 size_t workspace_bytes, void *stream);
+
 /*
  * Load a given filter into a state (detection with fixed, externally trained coefficients):
  * entries [n][M] complex, gamma [n][2][K] and clin [M][K] complex, all DEVICE, in age order

@@ -66,6 +66,9 @@ def _load():
             lib.apsm_oracle_detect.restype = None
             lib.apsm_oracle_detect.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp, dp, dp,
                                                ctypes.c_int, ctypes.c_int, dp, dp]
+            lib.apsm_oracle_detect_grad.restype = None
+            lib.apsm_oracle_detect_grad.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp, dp, dp, ctypes.c_int,
+                                                    ctypes.c_int, dp, dp, dp, dp, dp]
             lib.apsm_oracle_centres.restype = None
             lib.apsm_oracle_centres.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp]
             _lib = lib
@@ -215,6 +218,35 @@ def detect(p: Params, st: State, rx, threads: int | None = None) -> np.ndarray:
         with ThreadPoolExecutor(len(parts)) as ex:
             list(ex.map(run, parts))
     return y[..., 0] + 1j * y[..., 1]
+
+
+def detect_grad(p: Params, st: State, rx, dsoft, threads: int | None = None):
+    """Gradient of L = sum Re(conj(dsoft) * soft) = sum dy1 f(r1) + dy2 f(r2) with respect to the
+    Gaussian coefficients, the linear coefficients, sigma and w_L (plain partial derivatives,
+    FP64).  Returns (dgamma [n_c][K], dw [K][2M], dsigma, dw_L); per-thread partial sums are
+    combined in thread order."""
+    lib = _load()
+    N = int(np.asarray(rx).shape[0])
+    r = _cplx_to_f64(rx).reshape(N, p.M, 2)
+    dy = _cplx_to_f64(dsoft).reshape(N, p.K, 2)
+    c, g, w = _f64(st.centres), _f64(st.gamma), _f64(st.w)
+    pc = p.c()
+    parts = _split(N, threads or default_threads())
+    outs = [(np.zeros((c.shape[0], p.K)), np.zeros((p.K, 2 * p.M)), np.zeros(2)) for _ in parts]
+
+    def run(i):
+        rg = parts[i]
+        dg, dw, ds = outs[i]
+        lib.apsm_oracle_detect_grad(ctypes.byref(pc), c.shape[0], _dp(c), _dp(g), _dp(w), rg[0], rg[1], _dp(r),
+                                    _dp(dy), _dp(dg), _dp(dw), _dp(ds))
+
+    if N:
+        with ThreadPoolExecutor(len(parts)) as ex:
+            list(ex.map(run, range(len(parts))))
+    dg = sum(o[0] for o in outs)
+    dw = sum(o[1] for o in outs)
+    ds = sum(o[2] for o in outs)
+    return dg, dw, float(ds[0]), float(ds[1])
 
 
 def hard_qpsk(soft) -> np.ndarray:

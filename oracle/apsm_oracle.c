@@ -236,3 +236,50 @@ int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const dou
     free(beta);
     return 0;
 }
+
+/*
+ * Gradient of a linear functional of the detection outputs (for the adjoint of detection):
+ *   L = sum_{q,k} dy[q][k][0] f^k(r1(q)) + dy[q][k][1] f^k(r2(q)),
+ *   f^k(x) = w_L <w_k, x> + w_G sum_i gamma_i^k kappa_G(c_i, x)      (Fact 1, Sec. II-D)
+ * with the plain partial derivatives
+ *   dL/dgamma_i^k = w_G sum_q sum_l dy[q][k][l] kappa_G(c_i, x_l(q))
+ *   dL/dw_k       = w_L sum_q sum_l dy[q][k][l] x_l(q)
+ *   dL/dsigma     = w_G sum_{q,k,l,i} dy[q][k][l] gamma_i^k kappa_G(c_i, x_l(q)) ||c_i - x_l(q)||^2 / sigma^3
+ *   dL/dw_L       = sum_{q,k,l} dy[q][k][l] (<w_k, x_l(q)> - sum_i gamma_i^k kappa_G(c_i, x_l(q)))
+ * where x_0(q) = r1(q), x_1(q) = r2(q).  Queries [q0, q1); results are ADDED to the outputs
+ * (dgamma [n_c][K], dw [K][2M], dscal [2] = {dL/dsigma, dL/dw_L}).
+ */
+void apsm_oracle_detect_grad(const apsm_oracle_params *p, int n_c, const double *cent, const double *gamma,
+                             const double *w, int q0, int q1, const double *rx, const double *dy, double *dgamma,
+                             double *dw, double *dscal)
+{
+    const int M = p->M, L = 2 * M, K = p->K;
+    const double w_G = 1.0 - p->w_L, s = p->sigma;
+    double *x[2];
+    x[0] = (double *)malloc(sizeof(double) * (size_t)L);
+    x[1] = (double *)malloc(sizeof(double) * (size_t)L);
+    for (int q = q0; q < q1; ++q) {
+        real_split(M, rx + (size_t)q * 2 * M, x[0], x[1]);
+        for (int l = 0; l < 2; ++l) {
+            for (int i = 0; i < n_c; ++i) {
+                const double *c = cent + (size_t)i * L;
+                double d2 = 0.0;
+                for (int j = 0; j < L; ++j) d2 += (c[j] - x[l][j]) * (c[j] - x[l][j]);
+                const double kg = exp(-d2 / (2.0 * s * s));
+                for (int k = 0; k < K; ++k) {
+                    const double g = dy[((size_t)q * K + k) * 2 + l];
+                    dgamma[(size_t)i * K + k] += w_G * g * kg;
+                    dscal[0] += w_G * g * gamma[(size_t)i * K + k] * kg * d2 / (s * s * s);
+                    dscal[1] -= g * gamma[(size_t)i * K + k] * kg;
+                }
+            }
+            for (int k = 0; k < K; ++k) {
+                const double g = dy[((size_t)q * K + k) * 2 + l];
+                dscal[1] += g * kappa_lin(L, w + (size_t)k * L, x[l]);
+                for (int j = 0; j < L; ++j) dw[(size_t)k * L + j] += p->w_L * g * x[l][j];
+            }
+        }
+    }
+    free(x[0]);
+    free(x[1]);
+}

@@ -61,11 +61,14 @@ def load_library(path: str | None = None):
         lib.apsm_detect.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp]
         lib.apsm_read_status.argtypes = [S, ctypes.POINTER(ctypes.c_int32), vp]
         lib.apsm_state_set.argtypes = [P, vp, vp, vp, ctypes.c_int32, S, vp]
+        lib.apsm_detect_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.apsm_detect_backward.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.apsm_status_string.argtypes = [ctypes.c_int]
         lib.apsm_status_string.restype = ctypes.c_char_p
         lib.apsm_launch_count.restype = ctypes.c_int64
         for f in ("apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_train", "apsm_detect",
-                  "apsm_read_status", "apsm_state_set"):
+                  "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
+                  "apsm_detect_backward"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -215,6 +218,58 @@ def state_set(p: Params, state: State, entries: torch.Tensor, gamma: torch.Tenso
     _check(lib.apsm_state_set(ctypes.byref(p.c()), _ptr(entries), _ptr(gamma), _ptr(clin), n, ctypes.byref(st),
                               _stream()), "apsm_state_set")
     return state
+
+
+def detect_backward(p: Params, state: State, rx: torch.Tensor, dsoft: torch.Tensor, *,
+                    workspace: torch.Tensor | None = None):
+    """apsm_detect_backward: gradients (dgamma [A][2][K], dclin [M][K] complex64, dsigma, dw_L as a
+    [2] float32 tensor) of a loss whose gradient with respect to soft is dsoft."""
+    lib = load_library()
+    N = int(rx.shape[0])
+    _dev(rx, torch.complex64, (N, p.M), "rx")
+    _dev(dsoft, torch.complex64, (N, p.K), "dsoft")
+    nb = ctypes.c_size_t()
+    _check(lib.apsm_detect_backward_workspace_bytes(ctypes.byref(p.c()), N, ctypes.byref(nb)),
+           "apsm_detect_backward_workspace_bytes")
+    if workspace is None:
+        workspace = torch.empty((max(nb.value, 1),), dtype=torch.uint8, device=rx.device)
+    dgamma = torch.empty_like(state.gamma)
+    dclin = torch.empty_like(state.clin)
+    dscal = torch.empty((2,), dtype=torch.float32, device=rx.device)
+    st = state.c()
+    _check(lib.apsm_detect_backward(ctypes.byref(p.c()), ctypes.byref(st), _ptr(rx), N, _ptr(dsoft), _ptr(dgamma),
+                                    _ptr(dclin), _ptr(dscal), _ptr(workspace), workspace.numel(), _stream()),
+           "apsm_detect_backward")
+    return dgamma, dclin, dscal
+
+
+class DetectFunction(torch.autograd.Function):
+    """soft = detect(gamma, clin, sigma, w_L) with the dictionary entries fixed; backward runs
+    apsm_detect_backward.  sigma and w_L are 0-d tensors (their values parametrise the kernels)."""
+
+    @staticmethod
+    def forward(ctx, gamma, clin, sigma, w_L, p: Params, state: State, rx):
+        q = Params(**{**p.__dict__, "sigma": float(sigma), "w_L": float(w_L)})
+        st = State.__new__(State)
+        st.p, st.dict, st.dict_norm, st.meta = q, state.dict, state.dict_norm, state.meta
+        st.gamma, st.clin = gamma.detach().contiguous(), clin.detach().contiguous()
+        soft, _ = detect(q, st, rx, want_hard=False)
+        ctx.q, ctx.st, ctx.rx = q, st, rx
+        ctx.sigma_dtype, ctx.wl_dtype = sigma.dtype, w_L.dtype
+        return soft
+
+    @staticmethod
+    def backward(ctx, dsoft):
+        # torch's gradient for a complex output is conj(dL/dz*) convention: dL/dRe + i dL/dIm
+        dgamma, dclin, dscal = detect_backward(ctx.q, ctx.st, ctx.rx, dsoft.contiguous())
+        ds = dscal.cpu()
+        return (dgamma, dclin, ds[0].to(ctx.sigma_dtype), ds[1].to(ctx.wl_dtype), None, None, None)
+
+
+def detect_autograd(p: Params, state: State, rx: torch.Tensor, gamma: torch.Tensor, clin: torch.Tensor,
+                    sigma: torch.Tensor, w_L: torch.Tensor) -> torch.Tensor:
+    """Differentiable detection: gradients flow to gamma, clin, sigma and w_L."""
+    return DetectFunction.apply(gamma, clin, sigma, w_L, p, state, rx)
 
 
 def read_status(state: State) -> int:

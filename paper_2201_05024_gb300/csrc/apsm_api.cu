@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "apsm_common.cuh"
+#include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "train_f32.cuh"
 
@@ -18,6 +19,7 @@ namespace apsm {
 std::atomic<long long> g_launches{0};
 
 DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
+DetectBwdLauncher detect_bwd_launcher(int M, int K);  // detect_f32_m*.cu
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
 ChunkLauncher chunk_launcher(int S, int WP);        // train_chunk.cu
 int padded_window(int W);                           // train_chunk.cu
@@ -178,6 +180,32 @@ __global__ void state_set_kernel(const float2 *__restrict__ entries, const float
         meta[2] = n;
         meta[3] = 0;
     }
+}
+
+// ---- detection adjoint geometry -----------------------------------------------------------
+struct BwdGeom {
+    int A, n_qslices, q_per_slice, n_cslices;
+    size_t gh, cpart, scal, total;
+};
+
+BwdGeom bwd_geom(const apsm_params *p, int N) {
+    BwdGeom b;
+    b.A = round_up(p->dict_cap, kTileEntries);
+    const int entry_ctas = (p->dict_cap + kBwdEntriesPerCta - 1) / kBwdEntriesPerCta;
+    const int want = std::max(1, (2 * 152 + entry_ctas - 1) / entry_ctas);  // ~2 CTAs per SM
+    b.n_qslices = N > 0 ? std::min(want, (N + kBwdQueryTile - 1) / kBwdQueryTile) : 0;
+    b.q_per_slice = b.n_qslices ? round_up((N + b.n_qslices - 1) / b.n_qslices, kBwdQueryTile) : 0;
+    if (b.q_per_slice) b.n_qslices = (N + b.q_per_slice - 1) / b.q_per_slice;
+    b.n_cslices = N > 0 ? std::min(256, (N + 255) / 256) : 0;
+    size_t off = 0;
+    b.gh = off;
+    off = align256(off + sizeof(float) * (size_t)b.n_qslices * b.A * 4 * p->K);
+    b.cpart = off;
+    off = align256(off + sizeof(float) * 2 * (size_t)b.n_cslices * p->M * p->K);
+    b.scal = off;
+    off = align256(off + sizeof(float) * 2 * (size_t)b.A);
+    b.total = off;
+    return b;
 }
 
 }  // namespace
@@ -349,6 +377,62 @@ apsm_status apsm_state_set(const apsm_params *p, const float *entries, const flo
         st->meta);
     g_launches++;
     return cuda_status(cudaGetLastError());
+}
+
+apsm_status apsm_detect_backward_workspace_bytes(const apsm_params *p, int32_t N, size_t *bytes) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if (!bytes || N < 0) return APSM_ERR_INVALID_ARG;
+    *bytes = bwd_geom(p, N).total;
+    return APSM_OK;
+}
+
+apsm_status apsm_detect_backward(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N,
+                                 const float *dsoft, float *dgamma, float *dclin, float *dscalars, void *workspace,
+                                 size_t workspace_bytes, void *stream) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if ((s = check_state(st)) != APSM_OK) return s;
+    if (N < 0 || (N > 0 && (!rx || !dsoft)) || !dgamma || !dclin || !dscalars) return APSM_ERR_INVALID_ARG;
+    if (N > 0 && (!aligned16(rx) || (reinterpret_cast<uintptr_t>(dsoft) & 7))) return APSM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(dgamma) & 3) || (reinterpret_cast<uintptr_t>(dclin) & 7) ||
+        (reinterpret_cast<uintptr_t>(dscalars) & 3))
+        return APSM_ERR_INVALID_ARG;
+    if (p->dtype != APSM_FP32) return APSM_ERR_UNSUPPORTED;
+    const BwdGeom b = bwd_geom(p, N);
+    if (!workspace || workspace_bytes < b.total) return APSM_ERR_WORKSPACE;
+    if (reinterpret_cast<uintptr_t>(workspace) & 255) return APSM_ERR_INVALID_ARG;
+    if ((s = check_device()) != APSM_OK) return s;
+    DetectBwdLauncher bwd = detect_bwd_launcher(p->M, p->K);
+    if (!bwd) return APSM_ERR_UNSUPPORTED;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    DetectBwdArgs a{};
+    a.rx = reinterpret_cast<const float2 *>(rx);
+    a.dsoft = reinterpret_cast<const float2 *>(dsoft);
+    a.N = N;
+    a.dict = reinterpret_cast<const float2 *>(st->dict);
+    a.dict_norm = st->dict_norm;
+    a.gamma = st->gamma;
+    a.clin = reinterpret_cast<const float2 *>(st->clin);
+    a.meta = st->meta;
+    a.n_entries = p->dict_cap;
+    a.A = b.A;
+    a.q_per_slice = b.q_per_slice;
+    a.n_qslices = b.n_qslices;
+    a.n_cslices = b.n_cslices;
+    a.k2 = k2_of(p->sigma);
+    a.wL = p->w_L;
+    a.wG = 1.f - p->w_L;
+    a.sigma = p->sigma;
+    a.gh = reinterpret_cast<float *>(ws + b.gh);
+    a.cpart = reinterpret_cast<float2 *>(ws + b.cpart);
+    a.scal = reinterpret_cast<float *>(ws + b.scal);
+    a.dgamma = dgamma;
+    a.dclin = reinterpret_cast<float2 *>(dclin);
+    a.dscalars = dscalars;
+    if (bwd(a, static_cast<cudaStream_t>(stream)) != cudaSuccess) return APSM_ERR_CUDA;
+    g_launches += N > 0 ? 4 : 2;
+    return APSM_OK;
 }
 
 apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream) {

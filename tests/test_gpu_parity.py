@@ -264,3 +264,87 @@ def test_full_size_16x6_train_and_sampled_detect():
     assert_soft_close(soft2.cpu().numpy()[sample], ref2)
     ser = float(np.mean(hard.cpu().numpy() != inst.idx_data))
     assert ser < 0.05
+
+
+# ------------------------------------------------------------------------------------------
+# adjoint of detection
+# ------------------------------------------------------------------------------------------
+
+BWD_CASES = [
+    # M, K, D, N, sigma, w_L
+    (4, 2, 60, 300, 0.5, 0.5),
+    (16, 6, 200, 1100, 0.5, 0.5),       # several entry CTAs, query slices and a ragged tail
+    (8, 3, 33, 70, 0.7, 0.3),
+    (32, 12, 100, 257, 0.6, 0.8),
+]
+
+
+@pytest.mark.parametrize("M,K,D,N,sigma,wL", BWD_CASES)
+def test_detect_backward_matches_oracle_gradient(M, K, D, N, sigma, wL):
+    ent, gam, clin = synth.random_state(M, K, D, instance=D + M)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=N + K)
+    G = (np.random.default_rng(D).standard_normal((N, K)) + 1j * np.random.default_rng(N).standard_normal((N, K)))
+    G = G.astype(np.complex64)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=sigma, w_L=wL)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    dgamma, dclin, dscal = apsm.detect_backward(gp, st, to_dev(inst.rx_data), to_dev(G))
+    ref_g, ref_w, ref_sig, ref_wl = oracle.detect_grad(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data, G)
+    dg = dgamma.cpu().numpy()
+    ref_g = ref_g.reshape(D, 2, K)
+    assert np.abs(dg[:D] - ref_g).max() <= TOL_FP32 * max(np.abs(ref_g).max(), 1e-30)
+    assert np.all(dg[D:] == 0)
+    ref_c = oracle.clin_from_w(M, ref_w)
+    dc = dclin.cpu().numpy()
+    assert np.abs(dc - ref_c).max() <= TOL_FP32 * np.abs(ref_c).max()
+    ds = dscal.cpu().numpy()
+    assert ds[0] == pytest.approx(ref_sig, rel=1e-3, abs=1e-4 * abs(ref_sig) + 1e-6)
+    assert ds[1] == pytest.approx(ref_wl, rel=1e-3, abs=1e-6)
+
+
+def test_detect_autograd_matches_finite_differences():
+    """torch.autograd through the adjoint: gradient of an MSE loss to the transmitted symbols with
+    respect to sigma, w_L, the coefficients and the linear filter, against FP64 central finite
+    differences of the oracle's detection."""
+    M, K, D, N = 8, 3, 40, 200
+    ent, gam, clin = synth.random_state(M, K, D, instance=77)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=78)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.6, w_L=0.4)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    g_t = st.gamma.clone().requires_grad_(True)
+    c_t = st.clin.clone().requires_grad_(True)
+    sig = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+    wl = torch.tensor(0.4, dtype=torch.float64, requires_grad=True)
+    target = to_dev(inst.sym_data)
+    soft = apsm.detect_autograd(gp, st, to_dev(inst.rx_data), g_t, c_t, sig, wl)
+    loss = (soft - target).abs().pow(2).sum()
+    loss.backward()
+
+    gam64, clin128 = gam.astype(np.float64), clin.astype(np.complex128)   # the FP32 values, exactly
+
+    def L(sigma=0.6, w_L=0.4, gam_=gam64, clin_=clin128):
+        p = oracle.Params(M=M, K=K, W=1, D=D, sigma=sigma, w_L=w_L)
+        y = oracle.detect(p, oracle.state_from_arrays(M, ent, gam_, clin_), inst.rx_data)
+        return float(np.sum(np.abs(y - inst.sym_data) ** 2))
+
+    h = 1e-5
+    assert sig.grad.item() == pytest.approx((L(sigma=0.6 + h) - L(sigma=0.6 - h)) / (2 * h), rel=2e-3)
+    assert wl.grad.item() == pytest.approx((L(w_L=0.4 + h) - L(w_L=0.4 - h)) / (2 * h), rel=2e-3)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        t, l, k = int(rng.integers(D)), int(rng.integers(2)), int(rng.integers(K))
+        gp_, gm_ = gam64.copy(), gam64.copy()
+        gp_[t, l, k] += h
+        gm_[t, l, k] -= h
+        fd = (L(gam_=gp_) - L(gam_=gm_)) / (2 * h)
+        assert g_t.grad[t, l, k].item() == pytest.approx(fd, rel=2e-3, abs=1e-4)
+    for _ in range(3):
+        m, k = int(rng.integers(M)), int(rng.integers(K))
+        for unit in (1.0, 1j):
+            cp_, cm_ = clin128.copy(), clin128.copy()
+            cp_[m, k] += h * unit
+            cm_[m, k] -= h * unit
+            fd = (L(clin_=cp_) - L(clin_=cm_)) / (2 * h)
+            got = c_t.grad[m, k].item()
+            assert (got.real if unit == 1.0 else got.imag) == pytest.approx(fd, rel=2e-3, abs=1e-4)

@@ -306,3 +306,42 @@ def test_paper_default_parameters_detect_qpsk_cleanly():
     f = oracle.train(p, inst.rx_pilot, inst.sym_pilot)
     y = oracle.detect(p, f, inst.rx_data)
     assert np.mean(oracle.hard_qpsk(y) != inst.idx_data) < 0.01
+
+
+def _loss(p, st, rx, G):
+    """L = sum Re(conj(G) soft) for the oracle's detection."""
+    return float(np.sum((np.conj(G) * oracle.detect(p, st, rx)).real))
+
+
+def test_detect_gradient_matches_finite_differences():
+    """The oracle's detection gradient (plain partial derivatives) against FP64 finite differences
+    of the oracle's own detection: exact (any step) for the coefficients, in which the output is
+    linear, and central differences for sigma and w_L."""
+    M, K, n = 3, 2, 5
+    rng = np.random.default_rng(8)
+    ent = (rng.standard_normal((n, M)) + 1j * rng.standard_normal((n, M))) * 0.4
+    gam = rng.standard_normal((n, 2, K))
+    clin = rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))
+    rx = (rng.standard_normal((7, M)) + 1j * rng.standard_normal((7, M))) * 0.4
+    G = rng.standard_normal((7, K)) + 1j * rng.standard_normal((7, K))
+    p = oracle.Params(M=M, K=K, W=1, D=n, sigma=0.6, w_L=0.35)
+    st = oracle.state_from_arrays(M, ent, gam, clin)
+    dg, dw, dsig, dwl = oracle.detect_grad(p, st, rx, G)
+    base = _loss(p, st, rx, G)
+    for i in range(2 * n):
+        for k in range(K):
+            s2 = oracle.State(centres=st.centres, gamma=st.gamma.copy(), w=st.w)
+            s2.gamma[i, k] += 1.0
+            assert _loss(p, s2, rx, G) - base == pytest.approx(dg[i, k], rel=1e-10, abs=1e-12)
+    for k in range(K):
+        for j in range(2 * M):
+            s2 = oracle.State(centres=st.centres, gamma=st.gamma, w=st.w.copy())
+            s2.w[k, j] += 1.0
+            assert _loss(p, s2, rx, G) - base == pytest.approx(dw[k, j], rel=1e-10, abs=1e-12)
+    h = 1e-6
+    ps = [oracle.Params(M=M, K=K, W=1, D=n, sigma=0.6 + e, w_L=0.35) for e in (h, -h)]
+    fd = (_loss(ps[0], st, rx, G) - _loss(ps[1], st, rx, G)) / (2 * h)
+    assert dsig == pytest.approx(fd, rel=1e-6)
+    ps = [oracle.Params(M=M, K=K, W=1, D=n, sigma=0.6, w_L=0.35 + e) for e in (h, -h)]
+    fd = (_loss(ps[0], st, rx, G) - _loss(ps[1], st, rx, G)) / (2 * h)
+    assert dwl == pytest.approx(fd, rel=1e-6)
