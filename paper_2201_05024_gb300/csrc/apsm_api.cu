@@ -12,6 +12,7 @@
 #include "apsm_common.cuh"
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
+#include "detect_tc.cuh"
 #include "train_f32.cuh"
 
 namespace apsm {
@@ -20,6 +21,7 @@ std::atomic<long long> g_launches{0};
 
 DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
 DetectBwdLauncher detect_bwd_launcher(int M, int K);  // detect_f32_m*.cu
+TcLauncher detect_tc_launcher(int M, int K, int prec);  // detect_tc_m*.cu
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
 ChunkLauncher chunk_launcher(int S, int WP);        // train_chunk.cu
 int padded_window(int W);                           // train_chunk.cu
@@ -334,9 +336,40 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     if ((s = check_state(st)) != APSM_OK) return s;
     if (N < 0 || (N > 0 && (!rx || !soft))) return APSM_ERR_INVALID_ARG;
     if (N > 0 && (!aligned16(rx) || (reinterpret_cast<uintptr_t>(soft) & 7))) return APSM_ERR_INVALID_ARG;
-    if (p->dtype != APSM_FP32) return APSM_ERR_UNSUPPORTED;
     if ((s = check_device()) != APSM_OK) return s;
     if (N == 0) return APSM_OK;
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    // Engine: the Gram on the tensor cores (TF32 x3 for FP32, BF16/FP16 as requested) where a
+    // kernel exists for (M, K); FFMA otherwise (APSM_DETECT_ENGINE=ffma forces it for FP32).
+    const char *eng = std::getenv("APSM_DETECT_ENGINE");
+    const bool force_ffma = eng && std::strcmp(eng, "ffma") == 0;
+    if (p->dtype != APSM_FP32 || !force_ffma) {
+        const int prec = p->dtype == APSM_FP32 ? kTF32x3 : kHalf;
+        TcLauncher tc = detect_tc_launcher(p->M, p->K, prec);
+        if (tc) {
+            TcArgs ta{};
+            ta.rx = reinterpret_cast<const float2 *>(rx);
+            ta.N = N;
+            ta.dict = reinterpret_cast<const float2 *>(st->dict);
+            ta.dict_norm = st->dict_norm;
+            ta.gamma = st->gamma;
+            ta.clin = reinterpret_cast<const float2 *>(st->clin);
+            ta.meta = st->meta;
+            ta.n_entries = p->dict_cap;
+            ta.K = p->K;
+            ta.half_fmt = p->dtype == APSM_BF16 ? 1 : 0;
+            ta.k2 = k2_of(p->sigma);
+            ta.wL = p->w_L;
+            ta.wG = 1.f - p->w_L;
+            ta.soft = reinterpret_cast<float2 *>(soft);
+            ta.hard = hard;
+            ta.status = st->meta + 3;
+            if (tc(ta, strm) != cudaSuccess) return APSM_ERR_CUDA;
+            g_launches++;
+            return APSM_OK;
+        }
+        if (p->dtype != APSM_FP32) return APSM_ERR_UNSUPPORTED;
+    }
     DetectLauncher det = detect_f32_launcher(p->M, p->K);
     if (!det) return APSM_ERR_UNSUPPORTED;
     DetectArgs da{};
@@ -357,7 +390,7 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     da.partial = nullptr;
     da.status = st->meta + 3;
     const DetectShape sh = detect_shape(p->M, N);
-    if (det(da, 1, sh, static_cast<cudaStream_t>(stream)) != cudaSuccess) return APSM_ERR_CUDA;
+    if (det(da, 1, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches++;
     return APSM_OK;
 }

@@ -1,6 +1,7 @@
 // detect_dispatch.cu -- maps (M, K) to the FP32 detection kernels (and adjoint) instantiated for it.
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
+#include "detect_tc.cuh"
 
 namespace apsm {
 
@@ -17,6 +18,35 @@ DetectBwdLauncher detect_bwd_launcher_m8(int K);
 DetectBwdLauncher detect_bwd_launcher_m16(int K);
 DetectBwdLauncher detect_bwd_launcher_m32(int K);
 DetectBwdLauncher detect_bwd_launcher_m64(int K);
+
+TcLauncher detect_tc_launcher_m2(int kb, int prec);
+TcLauncher detect_tc_launcher_m4(int kb, int prec);
+TcLauncher detect_tc_launcher_m8(int kb, int prec);
+TcLauncher detect_tc_launcher_m16(int kb, int prec);
+TcLauncher detect_tc_launcher_m32(int kb, int prec);
+TcLauncher detect_tc_launcher_m64(int kb, int prec);
+
+// Smallest supported user bucket >= K for the tensor-core kernels (0 if none).
+int tc_user_bucket(int K) {
+    static const int kB[] = {2, 4, 6, 8, 12, 16};
+    for (int b : kB)
+        if (b >= K) return b;
+    return 0;
+}
+
+TcLauncher detect_tc_launcher(int M, int K, int prec) {
+    const int kb = tc_user_bucket(K);
+    if (!kb) return nullptr;
+    switch (M) {
+        case 2: return detect_tc_launcher_m2(kb, prec);
+        case 4: return detect_tc_launcher_m4(kb, prec);
+        case 8: return detect_tc_launcher_m8(kb, prec);
+        case 16: return detect_tc_launcher_m16(kb, prec);
+        case 32: return detect_tc_launcher_m32(kb, prec);
+        case 64: return detect_tc_launcher_m64(kb, prec);
+        default: return nullptr;
+    }
+}
 
 DetectBwdLauncher detect_bwd_launcher(int M, int K) {
     switch (M) {

@@ -1,0 +1,39 @@
+// detect_tc_inst.cuh -- instantiates the tensor-core detection kernel for one antenna count
+// (APSM_TC_M) and every user-count bucket, in both precisions where supported.
+#pragma once
+
+#include "detect_tc.cuh"
+
+#define APSM_TC_CAT2(a, b) a##b
+#define APSM_TC_CAT(a, b) APSM_TC_CAT2(a, b)
+
+namespace apsm {
+
+// kb: user bucket (2, 4, 6, 8, 12, 16); prec: kTF32x3 or kHalf.
+TcLauncher APSM_TC_CAT(detect_tc_launcher_m, APSM_TC_M)(int kb, int prec) {
+    constexpr int M = APSM_TC_M;
+    if (prec == kTF32x3) {
+        if constexpr (M <= 32) {
+            switch (kb) {
+                case 2: return launch_detect_tc<M, 2, kTF32x3>;
+                case 4: return launch_detect_tc<M, 4, kTF32x3>;
+                case 6: return launch_detect_tc<M, 6, kTF32x3>;
+                case 8: return launch_detect_tc<M, 8, kTF32x3>;
+                case 12: return launch_detect_tc<M, 12, kTF32x3>;
+                case 16: return launch_detect_tc<M, 16, kTF32x3>;
+            }
+        }
+        return nullptr;
+    }
+    switch (kb) {
+        case 2: return launch_detect_tc<M, 2, kHalf>;
+        case 4: return launch_detect_tc<M, 4, kHalf>;
+        case 6: return launch_detect_tc<M, 6, kHalf>;
+        case 8: return launch_detect_tc<M, 8, kHalf>;
+        case 12: return launch_detect_tc<M, 12, kHalf>;
+        case 16: return launch_detect_tc<M, 16, kHalf>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace apsm

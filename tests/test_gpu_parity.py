@@ -40,8 +40,19 @@ DETECT_CASES = [
 ]
 
 
+@pytest.fixture(params=["tensor", "ffma"])
+def engine(request, monkeypatch):
+    """FP32 detection engine: Gram on the tensor cores (TF32 x3, the default where a kernel exists)
+    or on the FP32 FMA pipe."""
+    if request.param == "ffma":
+        monkeypatch.setenv("APSM_DETECT_ENGINE", "ffma")
+    else:
+        monkeypatch.delenv("APSM_DETECT_ENGINE", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("M,K,D,N,sigma,wL", DETECT_CASES)
-def test_detect_matches_oracle(M, K, D, N, sigma, wL):
+def test_detect_matches_oracle(M, K, D, N, sigma, wL, engine):
     ent, gam, clin = synth.random_state(M, K, D, instance=D + 7 * M + K)
     inst = synth.make_instance(M, K, 4, N, 10.0, instance=M * 100 + K)
     op = oracle.Params(M=M, K=K, W=1, D=D, sigma=sigma, w_L=wL)
@@ -55,7 +66,7 @@ def test_detect_matches_oracle(M, K, D, N, sigma, wL):
 
 
 @pytest.mark.parametrize("case", ["offset", "mixed_entries", "mixed_queries"])
-def test_detect_unnormalised_inputs(case):
+def test_detect_unnormalised_inputs(case, engine):
     """Inputs outside the range where the factored exponentials are used: a large common offset
     (||r||^2 >> ||r - r_t||^2, where a norm expansion would cancel), a dictionary whose tiles are
     partly out of range, and query blocks that are partly out of range."""
@@ -82,6 +93,34 @@ def test_detect_unnormalised_inputs(case):
     ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), rx)
     assert_soft_close(soft.cpu().numpy(), ref)
     assert_hard_match(hard.cpu().numpy(), ref)
+
+
+HALF_CASES = [
+    # M, K, D, N, dtype
+    (64, 16, 300, 1000, "bf16"),    # the 64-antenna, 16-user precision-form shape, small
+    (64, 16, 300, 1000, "fp16"),
+    (16, 6, 200, 700, "bf16"),
+    (8, 3, 65, 129, "fp16"),
+    (2, 1, 5, 40, "bf16"),
+]
+TOL_HALF = 2e-2
+
+
+@pytest.mark.parametrize("M,K,D,N,dtype", HALF_CASES)
+def test_detect_reduced_precision_matches_oracle(M, K, D, N, dtype):
+    """BF16 / FP16 Gram on the tensor cores with FP32 accumulation, exponentials and sums:
+    soft outputs within 2e-2 (scaled) of the FP64 oracle, decisions identical away from a
+    boundary; the error against the FP32 path is reported by the benchmark."""
+    ent, gam, clin = synth.random_state(M, K, D, instance=D + M + 3)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=N + M)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.5, w_L=0.5)
+    gp = gpu_params(op, dtype=dtype)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
+    err = assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what=dtype)
+    assert err > 1e-6  # really the reduced-precision path
+    assert_hard_match(hard.cpu().numpy(), ref, tol=TOL_HALF)
 
 
 def test_detect_empty_dictionary_is_linear_filter():
