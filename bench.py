@@ -29,13 +29,18 @@ if ROOT not in sys.path:
 METRIC = "APSM symbol-vectors/s detect + pilot updates/s train; % roofline; err vs FP64"
 WORKLOAD = dict(M=16, K=6, P=1024, W=16, D=1024, N=65536, sigma=0.5, mu=0.5, eps=0.01, w_L=0.5, snr_db=10.0)
 L2_FLUSH_BYTES = 256 << 20
-# Nominal FP32 FMA-pipe peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz max SM clock.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Peaks (per GPU) for the detection roofline, derived from unit counts and the 2070 MHz maximum
+# SM clock: FP32 FMA pipe 152 SM x 128 lanes x 2 flop; MUFU ex2 152 SM x 32 per clock (both
+# unit counts confirmed by an FFMA / ex2 throughput microbenchmark on this GPU); TF32 tensor =
+# the measured dense BF16 peak x the nominal TF32/BF16 ratio (1.1 / 2.25).
+SM_CLOCK_HZ = 2.070e9
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * SM_CLOCK_HZ / 1e12
+MUFU_PEAK_PER_S = 152 * 32 * SM_CLOCK_HZ
 ORACLE_DETECT_SAMPLE = 4096
 
 # DRAM bytes per launch of the detection kernel from one ncu capture, valid only for the kernel
 # source with this digest (a changed kernel reports null until it is re-captured).
-DETECT_TRAFFIC = {"digest": "31dca97cec9976ae", "bytes_per_launch": 8.612864e6}
+DETECT_TRAFFIC = {"digest": "be3d92432de5432b", "bytes_per_launch": 8.608512e6}
 
 
 def workload_name(w):
@@ -43,15 +48,45 @@ def workload_name(w):
             f"N={w['N']} sigma={w['sigma']} mu={w['mu']} eps={w['eps']} w_L={w['w_L']} SNR={w['snr_db']}dB")
 
 
-def detect_flops(w, n_entries):
-    """Algorithmic FP32 flops of one detection launch: per (query, entry) pair one complex inner
-    product (4M FMA), three exponent arguments (3 FMA) and the coefficient accumulation (4K FMA)."""
-    return 2.0 * (4 * w["M"] + 4 * w["K"] + 3) * w["N"] * n_entries
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def detect_roofline(w, n_entries, seconds):
+    """Roofline of the tensor-core detection launch: algorithmic work per (query, entry) pair is
+    the complex Gram (2M x 2 MACs, issued as three TF32 products for FP32 accuracy) on the tensor
+    pipe, the three exponentials on MUFU, and the exponent arguments plus the coefficient
+    accumulation (4K + 3 FMA) on the FP32 pipe.  The bound is the resource with the largest
+    minimum time; `frac` = that minimum time / measured time."""
+    pairs = w["N"] * n_entries
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tf32_peak = bf16 * (1.1 / 2.25) * 1e12
+    res = {
+        "tensor": (3 * 2 * (2 * w["M"]) * 2 * pairs, tf32_peak, "TFLOP/s"),
+        "alu": (2 * (4 * w["K"] + 3) * pairs, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s"),
+        "mufu": (3 * pairs, MUFU_PEAK_PER_S, "Gex2/s"),
+    }
+    tmin = {k: v[0] / v[1] for k, v in res.items()}
+    bound = max(tmin, key=tmin.get)
+    work, peak, unit = res[bound]
+    scale = 1e12 if unit == "TFLOP/s" else 1e9
+    others = {k: round(tmin[k] / seconds, 4) for k in res}
+    return {"bound": bound, "achieved": work / seconds / scale, "peak": peak / scale, "unit": unit,
+            "frac": tmin[bound] / seconds, "frac_by_resource": others,
+            "peak_kind": ("FP32 pipe derived (152 SM x 128 FMA x 2070 MHz)" if bound == "alu" else
+                          "MUFU derived (152 SM x 32 ex2 x 2070 MHz)" if bound == "mufu" else
+                          "TF32 = measured BF16 x nominal 1.1/2.25")}
 
 
 def kernel_digest():
     h = hashlib.sha256()
-    for f in ("detect_f32.cuh", "apsm_common.cuh"):
+    for f in ("detect_tc.cuh", "detect_f32.cuh", "apsm_common.cuh"):
         with open(os.path.join(ROOT, "paper_2201_05024_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -282,9 +317,8 @@ def main():
         return
 
     n_entries = int(st.meta[0].item())
-    achieved = detect_flops(w, n_entries) / (mean_detect / 1e3) / 1e12
-    peak = FP32_PEAK_TFLOPS
-    traffic = DETECT_TRAFFIC["bytes_per_launch"] if DETECT_TRAFFIC["digest"] == kernel_digest() else None
+    roof = detect_roofline(w, n_entries, mean_detect / 1e3)
+    roof["traffic"] = DETECT_TRAFFIC["bytes_per_launch"] if DETECT_TRAFFIC["digest"] == kernel_digest() else None
     out = {
         "metric": METRIC, "value": value, "unit": "symbol-vectors/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -296,9 +330,7 @@ def main():
                    "ms": mean_detect},
         "train": {"value": world * w["P"] * w["K"] / (mean_train / 1e3), "unit": "pilot-updates/s",
                   "ms": mean_train, "us_per_pilot": mean_train * 1e3 / w["P"]},
-        "roofline": {"kernel": "detect_f32_kernel<16,6,1>", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                     "peak_kind": "derived FP32 FMA pipe at max SM clock"},
+        "roofline": {"kernel": "detect_tc_kernel<16,6,TF32x3>", **roof},
         "gpu_launches": int(launches),
         "wall_s_timed": wall,
         "e2e": e2e,
