@@ -209,6 +209,49 @@ apsm_status apsm_detect_backward(const apsm_params *p, const apsm_state *st, con
 apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,
                            int32_t n, const apsm_state *st, void *stream);
 
+/*
+ * Detection launch choice for one class (M, K, dtype), set by the autotuner
+ * (paper_2201_05024_gb300/autotune.py, not part of the method): engine 0 = Gram on the tensor
+ * cores, 1 = FP32 FMA pipe with `threads` query lanes x `split` entry groups per CTA and `qpt`
+ * queries per lane (ignored for engine 0).  Classes never set use built-in defaults.  The table
+ * is process-wide; apsm_tune_clear empties it.
+ */
+apsm_status apsm_tune_set(int32_t M, int32_t K, int32_t dtype, int32_t engine, int32_t threads, int32_t split,
+                          int32_t qpt);
+apsm_status apsm_tune_clear(void);
+
+/*
+ * Batched form (not in the paper: many independent detectors -- cells, resource blocks -- of
+ * uneven antenna count, user count, dictionary size and data length).  One instance:
+ */
+typedef struct {
+    apsm_params p;             /* its parameters (M, K, window, dict_cap, kernel parameters)   */
+    int32_t P;                 /* pilots                                                       */
+    int32_t N;                 /* data vectors                                                 */
+    const float *rx_pilot;     /* device [P][M] complex                                        */
+    const float *sym_pilot;    /* device [P][K] complex                                        */
+    const float *rx;           /* device [N][M] complex                                        */
+    float *soft;               /* device [N][K] complex                                        */
+    uint8_t *hard;             /* device [N][K] or NULL                                        */
+    apsm_state st;             /* its state (apsm_dict_alloc(&p) slots)                        */
+    void *workspace;           /* device, apsm_train_workspace_bytes(&p, P) bytes              */
+    size_t workspace_bytes;
+} apsm_instance;
+
+typedef struct apsm_batch_s *apsm_batch;
+
+/*
+ * Record, into one CUDA graph, apsm_train (from f_0 = 0) followed by apsm_detect for every
+ * instance; instances are spread over `lanes` (1..64) parallel graph branches, longest first,
+ * each onto the currently least-loaded branch.  The descriptors (and the buffers they point to)
+ * are bound at creation: apsm_batch_launch replays the same work on new data in the same
+ * buffers.  Every instance is validated before anything is recorded.  The handle owns the graph.
+ */
+apsm_status apsm_batch_create(const apsm_instance *inst, int32_t n, int32_t lanes, apsm_batch *out);
+/* Launch the whole batch (one graph launch) on `stream`. */
+apsm_status apsm_batch_launch(apsm_batch b, void *stream);
+apsm_status apsm_batch_destroy(apsm_batch b);
+
 /* Synchronise `stream`, then copy meta[3] (the device status word) to *device_status and clear it.
  * Returns APSM_ERR_CUDA if the synchronisation fails. */
 apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream);

@@ -40,6 +40,13 @@ class _CState(ctypes.Structure):
                 ("clin", ctypes.c_void_p), ("meta", ctypes.c_void_p)]
 
 
+class _CInstance(ctypes.Structure):
+    _fields_ = [("p", _CParams), ("P", ctypes.c_int32), ("N", ctypes.c_int32), ("rx_pilot", ctypes.c_void_p),
+                ("sym_pilot", ctypes.c_void_p), ("rx", ctypes.c_void_p), ("soft", ctypes.c_void_p),
+                ("hard", ctypes.c_void_p), ("st", _CState), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -63,12 +70,19 @@ def load_library(path: str | None = None):
         lib.apsm_state_set.argtypes = [P, vp, vp, vp, ctypes.c_int32, S, vp]
         lib.apsm_detect_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_detect_backward.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        i32 = ctypes.c_int32
+        lib.apsm_tune_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
+        lib.apsm_tune_clear.argtypes = []
+        lib.apsm_batch_create.argtypes = [ctypes.POINTER(_CInstance), i32, i32, ctypes.POINTER(vp)]
+        lib.apsm_batch_launch.argtypes = [vp, vp]
+        lib.apsm_batch_destroy.argtypes = [vp]
         lib.apsm_status_string.argtypes = [ctypes.c_int]
         lib.apsm_status_string.restype = ctypes.c_char_p
         lib.apsm_launch_count.restype = ctypes.c_int64
         for f in ("apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_train", "apsm_detect",
                   "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
-                  "apsm_detect_backward"):
+                  "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
+                  "apsm_batch_launch", "apsm_batch_destroy"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -270,6 +284,80 @@ def detect_autograd(p: Params, state: State, rx: torch.Tensor, gamma: torch.Tens
                     sigma: torch.Tensor, w_L: torch.Tensor) -> torch.Tensor:
     """Differentiable detection: gradients flow to gamma, clin, sigma and w_L."""
     return DetectFunction.apply(gamma, clin, sigma, w_L, p, state, rx)
+
+
+ENGINES = {"tensor": 0, "ffma": 1}
+
+
+def tune_set(M: int, K: int, dtype: str, engine: str, threads: int = 64, split: int = 1, qpt: int = 1):
+    """apsm_tune_set: the detection launch choice for class (M, K, dtype)."""
+    _check(load_library().apsm_tune_set(M, K, _DTYPES[dtype], ENGINES[engine], threads, split, qpt),
+           "apsm_tune_set")
+
+
+def tune_clear():
+    _check(load_library().apsm_tune_clear(), "apsm_tune_clear")
+
+
+def load_tuning(path: str) -> int:
+    """Apply a table written by paper_2201_05024_gb300.autotune; returns the number of classes."""
+    import json
+    with open(path) as fh:
+        table = json.load(fh)
+    for e in table["classes"]:
+        tune_set(e["M"], e["K"], e["dtype"], e["engine"], e.get("threads", 64), e.get("split", 1), e.get("qpt", 1))
+    return len(table["classes"])
+
+
+class BatchInstance:
+    """Device buffers of one detector instance of a batch (apsm_instance)."""
+
+    def __init__(self, p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, rx: torch.Tensor,
+                 want_hard: bool = True):
+        P, N = int(rx_pilot.shape[0]), int(rx.shape[0])
+        _dev(rx_pilot, torch.complex64, (P, p.M), "rx_pilot")
+        _dev(sym_pilot, torch.complex64, (P, p.K), "sym_pilot")
+        _dev(rx, torch.complex64, (N, p.M), "rx")
+        dev = rx.device
+        self.p, self.P, self.N = p, P, N
+        self.rx_pilot, self.sym_pilot, self.rx = rx_pilot, sym_pilot, rx
+        self.soft = torch.empty((N, p.K), dtype=torch.complex64, device=dev)
+        self.hard = torch.empty((N, p.K), dtype=torch.uint8, device=dev) if want_hard else None
+        self.state = State(p, device=dev)
+        nb = train_workspace_bytes(p, P)
+        self.workspace = torch.empty((max(nb, 1),), dtype=torch.uint8, device=dev)
+
+    def c(self) -> _CInstance:
+        return _CInstance(self.p.c(), self.P, self.N, self.rx_pilot.data_ptr(), self.sym_pilot.data_ptr(),
+                          self.rx.data_ptr(), self.soft.data_ptr(),
+                          self.hard.data_ptr() if self.hard is not None else None, self.state.c(),
+                          self.workspace.data_ptr(), self.workspace.numel())
+
+
+class Batch:
+    """apsm_batch: train + detect of many uneven instances replayed as one CUDA graph."""
+
+    def __init__(self, instances, lanes: int = 16):
+        lib = load_library()
+        self.instances = list(instances)   # keeps every buffer alive while the graph exists
+        arr = (_CInstance * len(self.instances))(*[x.c() for x in self.instances])
+        h = ctypes.c_void_p()
+        _check(lib.apsm_batch_create(arr, len(self.instances), lanes, ctypes.byref(h)), "apsm_batch_create")
+        self._h = h
+
+    def launch(self):
+        _check(load_library().apsm_batch_launch(self._h, _stream()), "apsm_batch_launch")
+
+    def close(self):
+        if self._h:
+            _check(load_library().apsm_batch_destroy(self._h), "apsm_batch_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def read_status(state: State) -> int:

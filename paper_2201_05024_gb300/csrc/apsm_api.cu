@@ -100,8 +100,35 @@ inline apsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APSM_O
 
 float k2_of(float sigma) { return kLog2e / (2.f * sigma * sigma); }
 
+// ---- launch-choice table filled by the autotuner (apsm_tune_set) ----------------------------
+struct TuneEntry {
+    int set, engine, threads, split, qpt;
+};
+std::mutex g_tune_mu;
+TuneEntry g_tune[7][17][3];  // [log2 M][K][dtype]
+
+int m_slot(int M) {
+    switch (M) {
+        case 2: return 1;
+        case 4: return 2;
+        case 8: return 3;
+        case 16: return 4;
+        case 32: return 5;
+        case 64: return 6;
+        default: return 0;
+    }
+}
+
+TuneEntry tune_get(int M, int K, int dtype) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    if (m_slot(M) == 0 || K < 1 || K > 16 || dtype < 0 || dtype > 2) return TuneEntry{};
+    return g_tune[m_slot(M)][K][dtype];
+}
+
 // ---- detection launch shape -------------------------------------------------------------
-DetectShape detect_shape(int M, int N) {
+DetectShape detect_shape(int M, int K, int dtype) {
+    const TuneEntry te = tune_get(M, K, dtype);
+    if (te.set && te.engine == 1) return DetectShape{te.threads, te.split, te.qpt};
     DetectShape s;
     s.qpt = env_int("APSM_DETECT_QPT", 1);
     if (s.qpt != 1 && s.qpt != 2) s.qpt = 1;
@@ -109,7 +136,6 @@ DetectShape detect_shape(int M, int N) {
     if (s.threads < 32 || s.threads > 256 || s.threads % 32) s.threads = 64;
     s.split = env_int("APSM_DETECT_SPLIT", 2);
     if (s.split < 1 || s.split * s.threads > 256) s.split = 1;
-    (void)N;
     return s;
 }
 
@@ -342,7 +368,8 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     // Engine: the Gram on the tensor cores (TF32 x3 for FP32, BF16/FP16 as requested) where a
     // kernel exists for (M, K); FFMA otherwise (APSM_DETECT_ENGINE=ffma forces it for FP32).
     const char *eng = std::getenv("APSM_DETECT_ENGINE");
-    const bool force_ffma = eng && std::strcmp(eng, "ffma") == 0;
+    const TuneEntry te = tune_get(p->M, p->K, p->dtype);
+    const bool force_ffma = eng ? std::strcmp(eng, "ffma") == 0 : (te.set && te.engine == 1);
     if (p->dtype != APSM_FP32 || !force_ffma) {
         const int prec = p->dtype == APSM_FP32 ? kTF32x3 : kHalf;
         TcLauncher tc = detect_tc_launcher(p->M, p->K, prec);
@@ -389,7 +416,7 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     da.hard = hard;
     da.partial = nullptr;
     da.status = st->meta + 3;
-    const DetectShape sh = detect_shape(p->M, N);
+    const DetectShape sh = detect_shape(p->M, p->K, p->dtype);
     if (det(da, 1, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches++;
     return APSM_OK;
@@ -465,6 +492,24 @@ apsm_status apsm_detect_backward(const apsm_params *p, const apsm_state *st, con
     a.dscalars = dscalars;
     if (bwd(a, static_cast<cudaStream_t>(stream)) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches += N > 0 ? 4 : 2;
+    return APSM_OK;
+}
+
+apsm_status apsm_tune_set(int32_t M, int32_t K, int32_t dtype, int32_t engine, int32_t threads, int32_t split,
+                          int32_t qpt) {
+    if (m_slot(M) == 0 || K < 1 || K > 16 || dtype < 0 || dtype > 2 || (engine != 0 && engine != 1))
+        return APSM_ERR_INVALID_ARG;
+    if (engine == 1 && (threads < 32 || threads > 256 || threads % 32 || split < 1 || split * threads > 256 ||
+                        (qpt != 1 && qpt != 2)))
+        return APSM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[m_slot(M)][K][dtype] = TuneEntry{1, engine, threads, split, qpt};
+    return APSM_OK;
+}
+
+apsm_status apsm_tune_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    std::memset(g_tune, 0, sizeof(g_tune));
     return APSM_OK;
 }
 

@@ -129,3 +129,33 @@ def test_status_strings(lib):
     for c in range(7):
         assert apsm.status_string(c) not in ("", "unknown status")
     assert lib.apsm_launch_count() >= 0
+
+
+def test_tune_table_validation(lib):
+    from paper_2201_05024_gb300 import apsm
+    assert lib.apsm_tune_set(16, 6, 0, 1, 64, 2, 1) == 0
+    assert lib.apsm_tune_set(16, 6, 0, 0, 0, 0, 0) == 0          # tensor engine ignores the shape
+    assert lib.apsm_tune_set(3, 6, 0, 0, 0, 0, 0) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_tune_set(16, 17, 0, 0, 0, 0, 0) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_tune_set(16, 6, 0, 1, 48, 1, 1) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_tune_set(16, 6, 0, 1, 128, 4, 1) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_tune_set(16, 6, 0, 2, 64, 1, 1) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_tune_clear() == 0
+
+
+def test_batch_create_validates_every_instance_first(lib):
+    import ctypes as C
+    from paper_2201_05024_gb300 import apsm
+    p = params(dict_cap=64).c()
+    st = _cstate(256)
+    good = apsm._CInstance(p, 64, 10, 256, 256, 256, 256, None, st, 256, 1 << 30)
+    bad_ws = apsm._CInstance(p, 64, 10, 256, 256, 256, 256, None, st, 256, 16)
+    bad_rx = apsm._CInstance(p, 64, 10, 256, 256, None, 256, None, st, 256, 1 << 30)
+    h = C.c_void_p()
+    for bad, code in ((bad_ws, apsm.APSM_ERR_WORKSPACE), (bad_rx, apsm.APSM_ERR_INVALID_ARG)):
+        arr = (apsm._CInstance * 2)(good, bad)
+        assert lib.apsm_batch_create(arr, 2, 4, C.byref(h)) == code
+    arr = (apsm._CInstance * 1)(good)
+    assert lib.apsm_batch_create(arr, 0, 4, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_batch_create(arr, 1, 0, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_batch_launch(None, None) == apsm.APSM_ERR_INVALID_ARG

@@ -1,0 +1,90 @@
+"""Batched form: many uneven detector instances trained and detected by one CUDA graph, and the
+autotuner's launch table.  Each instance must give exactly what the single-instance calls give,
+and a small instance is also checked against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_05024_gb300 import apsm, autotune, synth
+
+from parity import assert_hard_match, assert_soft_close, gpu_params, load_state, oracle_state_fp32, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # M, K, P, D, N  (P > D: eviction; ragged sizes)
+    (8, 2, 300, 128, 1000),
+    (16, 6, 200, 512, 3000),
+    (32, 12, 150, 160, 2050),
+    (16, 5, 700, 333, 777),
+    (8, 11, 64, 900, 1500),
+    (32, 3, 257, 256, 4096),
+]
+
+
+def _instances():
+    out = []
+    for i, (M, K, P, D, N) in enumerate(SHAPES):
+        inst = synth.make_instance(M, K, P, N, 10.0, instance=500 + i)
+        p = apsm.Params(M=M, K=K, window=16, dict_cap=D)
+        out.append((p, inst))
+    return out
+
+
+def test_batch_graph_matches_single_instance_calls():
+    data = _instances()
+    bis = [apsm.BatchInstance(p, to_dev(x.rx_pilot), to_dev(x.sym_pilot), to_dev(x.rx_data)) for p, x in data]
+    batch = apsm.Batch(bis, lanes=4)
+    for rep in range(2):                       # replay: the same graph on the same buffers
+        for b in bis:
+            b.soft.zero_()
+        batch.launch()
+        torch.cuda.synchronize()
+        for (p, x), b in zip(data, bis):
+            st = apsm.State(p)
+            apsm.train(p, b.rx_pilot, b.sym_pilot, st)
+            soft, hard = apsm.detect(p, st, b.rx)
+            assert torch.equal(soft, b.soft), (p, rep)
+            assert torch.equal(hard, b.hard)
+            assert torch.equal(st.gamma, b.state.gamma) and torch.equal(st.clin, b.state.clin)
+            assert apsm.read_status(b.state) == 0
+    batch.close()
+
+
+def test_batch_small_instance_matches_oracle():
+    M, K, P, D, N = 8, 3, 120, 50, 400
+    x = synth.make_instance(M, K, P, N, 10.0, instance=600)
+    p = apsm.Params(M=M, K=K, window=8, dict_cap=D)
+    b = apsm.BatchInstance(p, to_dev(x.rx_pilot), to_dev(x.sym_pilot), to_dev(x.rx_data))
+    batch = apsm.Batch([b], lanes=2)
+    batch.launch()
+    torch.cuda.synchronize()
+    op = oracle.Params(M=M, K=K, W=8, D=D, sigma=p.sigma, mu=p.mu, eps=p.eps, w_L=p.w_L)
+    ref = oracle.detect(op, oracle.train(op, x.rx_pilot, x.sym_pilot), x.rx_data)
+    assert_soft_close(b.soft.cpu().numpy(), ref)
+    assert_hard_match(b.hard.cpu().numpy(), ref)
+    batch.close()
+
+
+def test_autotuned_table_keeps_parity():
+    M, K = 16, 5
+    entry = autotune.tune_class(M, K, "fp32", D=256, N=2048, reps=2)
+    assert entry["engine"] in ("tensor", "ffma") and entry["candidates"] > 1
+    try:
+        apsm.tune_set(M, K, "fp32", entry["engine"], entry.get("threads", 64), entry.get("split", 1),
+                      entry.get("qpt", 1))
+        ent, gam, clin = synth.random_state(M, K, 300, instance=9)
+        inst = synth.make_instance(M, K, 4, 777, 10.0, instance=10)
+        op = oracle.Params(M=M, K=K, W=1, D=300)
+        gp = gpu_params(op)
+        st = load_state(gp, ent, gam, clin)
+        soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+        ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
+        assert_soft_close(soft.cpu().numpy(), ref)
+        # every FFMA shape the tuner may pick is itself correct
+        for t, s, q in autotune.FFMA_SHAPES:
+            apsm.tune_set(M, K, "fp32", "ffma", t, s, q)
+            soft, _ = apsm.detect(gp, st, to_dev(inst.rx_data))
+            assert_soft_close(soft.cpu().numpy(), ref, what=f"ffma {t}x{s}x{q}")
+    finally:
+        apsm.tune_clear()
