@@ -200,6 +200,27 @@ apsm_status apsm_detect_backward(const apsm_params *p, const apsm_state *st, con
                                  const float *dsoft, float *dgamma, float *dclin, float *dscalars, void *workspace,
                                  size_t workspace_bytes, void *stream);
 
+/* Bytes of device workspace apsm_train_backward needs for P pilots. */
+apsm_status apsm_train_backward_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes);
+
+/*
+ * Adjoint of apsm_train (not in the paper: gradients through the unrolled recurrence of Eq. apsm
+ * with Eq. beta, Sec. II-D).  Given the gradient of a loss with respect to the trained state --
+ * dgamma [A][2][K] (ring layout of apsm_state.gamma, e.g. from apsm_detect_backward) and
+ * dclin [M][K] complex (dL/dRe c + i dL/dIm c) -- it returns
+ *   dscalars[4] = {dL/dsigma, dL/dmu, dL/deps, dL/dw_L} through the training only, and
+ *   dclin0 [M][K] complex = dL/d(initial linear filter c_0).
+ * The derivative of Eq. beta is taken piecewise: -1/kappa_jj with respect to the residual and
+ * -+1/kappa_jj with respect to eps outside the slab, 0 inside it (and at |e| = eps exactly).
+ * The forward recurrence is re-run from checkpoints taken every 32 pilots (64 steps).
+ *   rx_pilot, sym_pilot, P, clin0: as given to apsm_train (clin0 may be NULL for zero), P >= 1
+ *   workspace: apsm_train_backward_workspace_bytes(p, P) bytes, 256-byte aligned
+ * All pointers DEVICE.  Deterministic.  Errors as for apsm_train.
+ */
+apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                                const float *clin0, const float *dgamma, const float *dclin, float *dscalars,
+                                float *dclin0, void *workspace, size_t workspace_bytes, void *stream);
+
 /*
  * Load a given filter into a state (detection with fixed, externally trained coefficients):
  * entries [n][M] complex, gamma [n][2][K] and clin [M][K] complex, all DEVICE, in age order

@@ -71,6 +71,8 @@ def load_library(path: str | None = None):
         lib.apsm_detect_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_detect_backward.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         i32 = ctypes.c_int32
+        lib.apsm_train_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.apsm_train_backward.argtypes = [P, vp, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.apsm_tune_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
         lib.apsm_tune_clear.argtypes = []
         lib.apsm_batch_create.argtypes = [ctypes.POINTER(_CInstance), i32, i32, ctypes.POINTER(vp)]
@@ -82,6 +84,7 @@ def load_library(path: str | None = None):
         for f in ("apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_train", "apsm_detect",
                   "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
                   "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
+                  "apsm_train_backward_workspace_bytes", "apsm_train_backward",
                   "apsm_batch_launch", "apsm_batch_destroy"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -284,6 +287,62 @@ def detect_autograd(p: Params, state: State, rx: torch.Tensor, gamma: torch.Tens
                     sigma: torch.Tensor, w_L: torch.Tensor) -> torch.Tensor:
     """Differentiable detection: gradients flow to gamma, clin, sigma and w_L."""
     return DetectFunction.apply(gamma, clin, sigma, w_L, p, state, rx)
+
+
+def train_backward(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, dgamma: torch.Tensor,
+                   dclin: torch.Tensor, *, clin0: torch.Tensor | None = None, workspace: torch.Tensor | None = None):
+    """apsm_train_backward: given dL/dgamma [A][2][K] and dL/dclin [M][K] of the trained state, the
+    gradients through the training recurrence: ([4] float32 = d sigma, d mu, d eps, d w_L, and
+    dL/dclin0 [M][K] complex64)."""
+    lib = load_library()
+    P = int(rx_pilot.shape[0])
+    _dev(rx_pilot, torch.complex64, (P, p.M), "rx_pilot")
+    _dev(sym_pilot, torch.complex64, (P, p.K), "sym_pilot")
+    _dev(dgamma, torch.float32, (dict_alloc(p), 2, p.K), "dgamma")
+    _dev(dclin, torch.complex64, (p.M, p.K), "dclin")
+    nb = ctypes.c_size_t()
+    _check(lib.apsm_train_backward_workspace_bytes(ctypes.byref(p.c()), P, ctypes.byref(nb)),
+           "apsm_train_backward_workspace_bytes")
+    if workspace is None:
+        workspace = torch.empty((max(nb.value, 1),), dtype=torch.uint8, device=rx_pilot.device)
+    dscal = torch.empty((4,), dtype=torch.float32, device=rx_pilot.device)
+    dclin0 = torch.empty((p.M, p.K), dtype=torch.complex64, device=rx_pilot.device)
+    _check(lib.apsm_train_backward(ctypes.byref(p.c()), _ptr(rx_pilot), _ptr(sym_pilot), P, _ptr(clin0), _ptr(dgamma),
+                                   _ptr(dclin), _ptr(dscal), _ptr(dclin0), _ptr(workspace), workspace.numel(),
+                                   _stream()), "apsm_train_backward")
+    return dscal, dclin0
+
+
+class TrainDetectFunction(torch.autograd.Function):
+    """soft = detect(train(pilots; c_0, sigma, mu, eps, w_L), rx): the APSM recurrence unrolled over
+    the pilots and the detection of the data vectors, differentiable with respect to the initial
+    linear filter c_0 and the four scalars (0-d tensors)."""
+
+    @staticmethod
+    def forward(ctx, clin0, sigma, mu, eps, w_L, p: Params, rx_pilot, sym_pilot, rx):
+        q = Params(**{**p.__dict__, "sigma": float(sigma), "mu": float(mu), "eps": float(eps), "w_L": float(w_L)})
+        st = State(q, device=rx.device)
+        c0 = clin0.detach().contiguous()
+        train(q, rx_pilot, sym_pilot, st, clin0=c0)
+        soft, _ = detect(q, st, rx, want_hard=False)
+        ctx.q, ctx.st, ctx.c0, ctx.data = q, st, c0, (rx_pilot, sym_pilot, rx)
+        ctx.dtypes = (sigma.dtype, mu.dtype, eps.dtype, w_L.dtype)
+        return soft
+
+    @staticmethod
+    def backward(ctx, dsoft):
+        rx_pilot, sym_pilot, rx = ctx.data
+        dgamma, dclin, dsd = detect_backward(ctx.q, ctx.st, rx, dsoft.contiguous())
+        dst, dclin0 = train_backward(ctx.q, rx_pilot, sym_pilot, dgamma, dclin, clin0=ctx.c0)
+        dsd, dst = dsd.cpu().double(), dst.cpu().double()
+        ds, dm, de, dw = (dsd[0] + dst[0], dst[1], dst[2], dsd[1] + dst[3])
+        t = ctx.dtypes
+        return (dclin0, ds.to(t[0]), dm.to(t[1]), de.to(t[2]), dw.to(t[3]), None, None, None, None)
+
+
+def train_detect_autograd(p: Params, rx_pilot, sym_pilot, rx, clin0, sigma, mu, eps, w_L):
+    """Differentiable train + detect; gradients flow to clin0, sigma, mu, eps and w_L."""
+    return TrainDetectFunction.apply(clin0, sigma, mu, eps, w_L, p, rx_pilot, sym_pilot, rx)
 
 
 ENGINES = {"tensor": 0, "ffma": 1}

@@ -1,0 +1,86 @@
+"""Adjoint of the training recurrence: gradients of an MSE detection loss with respect to sigma,
+mu, eps, w_L and the initial linear filter, through training (checkpointed reverse sweep) and
+detection, against FP64 central finite differences of the oracle.  A finite difference is used
+only where no branch of Eq. beta flips between the two perturbed runs (the loss has kinks
+there); the number of usable checks is asserted."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2201_05024_gb300 import apsm, synth
+
+from parity import to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # M, K, P, W, D, N, sigma, mu, eps, w_L
+    (4, 2, 40, 4, 40, 150, 0.6, 0.5, 0.05, 0.5),     # no eviction, two checkpoint segments
+    (4, 2, 70, 6, 12, 150, 0.6, 0.7, 0.05, 0.4),     # FIFO eviction
+    (8, 3, 33, 3, 33, 120, 0.5, 0.9, 0.02, 0.6),     # (mu = 1 lands residuals exactly on the slab edge)
+]
+
+
+def _loss(op, inst, clin0):
+    w0 = np.concatenate([clin0.real.T, clin0.imag.T], axis=1)
+    fst, cases, _ = oracle.train(op, inst.rx_pilot, inst.sym_pilot, w0=w0, log_cases=True)
+    y = oracle.detect(op, fst, inst.rx_data)
+    return float(np.sum(np.abs(y - inst.sym_data) ** 2)), cases
+
+
+@pytest.mark.parametrize("M,K,P,W,D,N,sigma,mu,eps,wL", CASES)
+def test_train_and_detect_gradients_match_finite_differences(M, K, P, W, D, N, sigma, mu, eps, wL):
+    inst = synth.make_instance(M, K, P, N, 8.0, instance=900 + P)
+    rng = np.random.default_rng(P)
+    clin0 = ((rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K))) * 0.2).astype(np.complex64)
+    p = apsm.Params(M=M, K=K, window=W, dict_cap=D, sigma=sigma, mu=mu, eps=eps, w_L=wL)
+    c_t = to_dev(clin0).requires_grad_(True)
+    th = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True)
+          for k, v in dict(sigma=sigma, mu=mu, eps=eps, w_L=wL).items()}
+    soft = apsm.train_detect_autograd(p, to_dev(inst.rx_pilot), to_dev(inst.sym_pilot), to_dev(inst.rx_data), c_t,
+                                      th["sigma"], th["mu"], th["eps"], th["w_L"])
+    loss = (soft - to_dev(inst.sym_data)).abs().pow(2).sum()
+    loss.backward()
+
+    base = dict(sigma=sigma, mu=mu, eps=eps, w_L=wL)
+    c64 = clin0.astype(np.complex128)
+    scale = max(abs(float(loss.item())), 1.0)
+    checked = 0
+
+    def fd(name=None, comp=None):
+        h = 1e-6 if name is None else 1e-6 * max(abs(base[name]), 1e-2)
+        vals, logs = [], []
+        for sgn in (1, -1):
+            b = dict(base)
+            c = c64.copy()
+            if name is not None:
+                b[name] += sgn * h
+            else:
+                c[comp[0], comp[1]] += sgn * h * comp[2]
+            op = oracle.Params(M=M, K=K, W=W, D=D, sigma=b["sigma"], mu=b["mu"], eps=b["eps"], w_L=b["w_L"])
+            v, cs = _loss(op, inst, c)
+            vals.append(v)
+            logs.append(cs)
+        if not np.array_equal(logs[0], logs[1]):
+            return None  # a branch of Eq. beta flips inside the stencil
+        return (vals[0] - vals[1]) / (2 * h)
+
+    for name in ("sigma", "mu", "eps", "w_L"):
+        ref = fd(name)
+        if ref is None:
+            continue
+        got = th[name].grad.item()
+        assert got == pytest.approx(ref, rel=3e-3, abs=1e-5 * scale), name
+        checked += 1
+    for _ in range(4):
+        m, k = int(rng.integers(M)), int(rng.integers(K))
+        for unit in (1.0, 1j):
+            ref = fd(comp=(m, k, unit))
+            if ref is None:
+                continue
+            g = c_t.grad[m, k].item()
+            got = g.real if unit == 1.0 else g.imag
+            assert got == pytest.approx(ref, rel=3e-3, abs=1e-5 * scale), (m, k, unit)
+            checked += 1
+    assert checked >= 8
