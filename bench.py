@@ -273,6 +273,115 @@ def run_batched(args):
     print(json.dumps(out))
 
 
+def _time_events(fn, steps, warmup):
+    import torch
+    for _ in range(max(warmup, 3)):
+        fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def run_precision(args):
+    """Detection only, 64 antennas, 16 users, D = 4096 entries, 1,048,576 data vectors, Gram in
+    BF16 (and FP16) on the tensor cores with FP32 accumulation; coefficients trained by the FP32
+    GPU trainer on 4096 pilots (W = 16).  Errors against the FP64 oracle (sampled) and the FP32
+    GPU path."""
+    import torch
+    from paper_2201_05024_gb300 import apsm, build, synth
+    import oracle
+    torch.cuda.set_device(0)
+    build.build()
+    M, K, D, N = 64, 16, 4096, args.precision_n
+    x = synth.make_instance(M, K, D, N, 15.0, instance=4)
+    base = dict(M=M, K=K, window=16, dict_cap=D, sigma=0.5, mu=0.5, eps=0.01, w_L=0.5)
+    p32 = apsm.Params(**base)
+    st = apsm.State(p32)
+    rp, sp = torch.from_numpy(x.rx_pilot).cuda(), torch.from_numpy(x.sym_pilot).cuda()
+    apsm.train(p32, rp, sp, st)
+    rd = torch.from_numpy(x.rx_data).cuda()
+    out = {"metric": METRIC, "unit": "symbol-vectors/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic", "config": {"workload": f"detect-only M={M} K={K} D={D} N={N}, state trained "
+                                                       "by the FP32 GPU trainer on 4096 pilots (W=16)",
+                                           "l2": "inputs larger than L2 (%d MB of data vectors)" % (N * M * 8 >> 20)}}
+    soft = {}
+    for dt in ("fp32", "bf16", "fp16"):
+        q = apsm.Params(**base, dtype=dt)
+        s_ = torch.empty((N, K), dtype=torch.complex64, device="cuda")
+        h_ = torch.empty((N, K), dtype=torch.uint8, device="cuda")
+        ms = _time_events(lambda: apsm.detect(q, st, rd, soft=s_, hard=h_), args.steps, args.warmup)
+        soft[dt] = s_
+        pairs = N * D
+        out[dt] = {"value": N / (ms / 1e3), "ms": ms, "pairs_per_s": pairs / (ms / 1e3),
+                   "tensor_tflops": (1 if dt != "fp32" else 3) * 2 * (2 * M) * 2 * pairs / (ms / 1e3) / 1e12,
+                   "ser": float((h_.cpu().numpy() != x.idx_data).mean())}
+    out["value"], out["ms_per_step"], out["dtype"] = out["bf16"]["value"], out["bf16"]["ms"], "bf16"
+    sample = np.random.default_rng(0).choice(N, 512, replace=False)
+    ent, gam = st.entries()
+    op = oracle.Params(M=M, K=K, W=16, D=D, sigma=0.5, w_L=0.5)
+    ost = oracle.state_from_arrays(M, ent, gam, st.clin.cpu().numpy())
+    ref = oracle.detect(op, ost, x.rx_data[sample])
+    cr = np.stack([ref.real, ref.imag])
+    rms = np.sqrt(np.mean(cr ** 2))
+    for dt in ("fp32", "bf16", "fp16"):
+        y = soft[dt].cpu().numpy()[sample].astype(np.complex128)
+        cy = np.stack([y.real, y.imag])
+        out[dt]["err_vs_fp64_max_scaled"] = float((np.abs(cy - cr) / np.maximum(np.abs(cr), rms)).max())
+        if dt != "fp32":
+            y32 = soft["fp32"].cpu().numpy().astype(np.complex128)
+            yd = soft[dt].cpu().numpy().astype(np.complex128)
+            c32, cd = np.stack([y32.real, y32.imag]), np.stack([yd.real, yd.imag])
+            r32 = np.sqrt(np.mean(c32 ** 2))
+            out[dt]["err_vs_fp32_max_scaled"] = float((np.abs(cd - c32) / np.maximum(np.abs(c32), r32)).max())
+    print(json.dumps(out))
+
+
+def run_grad(args):
+    """Differentiation form: 256 instances of 16 antennas, 6 users, 256 pilots (W = 8, D = 256),
+    4096 data vectors each; loss = MSE of the soft outputs to the transmitted symbols; forward
+    (train + detect) and backward (detect adjoint + checkpointed training adjoint) timed over all
+    instances (one stream, instance after instance)."""
+    import torch
+    from paper_2201_05024_gb300 import apsm, build, synth
+    torch.cuda.set_device(0)
+    build.build()
+    n_inst, M, K, P, W, D, N = args.grad_instances, 16, 6, 256, 8, 256, 4096
+    p = apsm.Params(M=M, K=K, window=W, dict_cap=D, sigma=0.5, mu=0.5, eps=0.01, w_L=0.5)
+    data = []
+    for i in range(n_inst):
+        x = synth.make_instance(M, K, P, N, 10.0, instance=20000 + i)
+        data.append(tuple(torch.from_numpy(a).cuda() for a in (x.rx_pilot, x.sym_pilot, x.rx_data, x.sym_data)))
+    c0 = torch.zeros((M, K), dtype=torch.complex64, device="cuda", requires_grad=True)
+    th = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (0.5, 0.5, 0.01, 0.5)]
+
+    def step():
+        total = 0.0
+        for rp, sp, rd, sd in data:
+            soft = apsm.train_detect_autograd(p, rp, sp, rd, c0, *th)
+            loss = (soft - sd).abs().pow(2).sum()
+            loss.backward()
+            total = total + loss.detach()
+        return total
+
+    ms = _time_events(step, args.steps, args.warmup)
+    fwd = _time_events(lambda: [apsm.detect(p, apsm.train(p, rp, sp, apsm.State(p)), rd, want_hard=False)
+                                for rp, sp, rd, sd in data], args.steps, args.warmup)
+    print(json.dumps({"metric": METRIC, "value": n_inst * N / (ms / 1e3), "unit": "symbol-vectors/s (forward+backward)",
+                      "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+                      "forward_ms": fwd, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"{n_inst} instances x (M={M}, K={K}, P={P}, W={W}, D={D}, N={N}); "
+                                             "gradients wrt sigma, mu, eps, w_L, c_0; checkpoint every 32 pilots"},
+                      "grad_sample": [float(g.grad) for g in th]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -283,13 +392,21 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--flush-mb", type=int, default=L2_FLUSH_BYTES >> 20,
                     help="MiB written between timed steps to flush L2 (0: none, for profiler captures)")
-    ap.add_argument("--workload", default="paper16x6", choices=["paper16x6", "batched"])
+    ap.add_argument("--workload", default="paper16x6", choices=["paper16x6", "batched", "precision", "grad"])
+    ap.add_argument("--precision-n", type=int, default=1 << 20)
+    ap.add_argument("--grad-instances", type=int, default=256)
     ap.add_argument("--instances", type=int, default=1024)
     ap.add_argument("--lanes", type=int, default=32)
     ap.add_argument("--tuning", default=None, help="autotuner table (JSON) for the batched workload")
     args = ap.parse_args()
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "precision":
+        run_precision(args)
+        return
+    if args.workload == "grad":
+        run_grad(args)
         return
     w = dict(WORKLOAD)
     if args.impl == "reference":
