@@ -105,6 +105,8 @@ struct ChunkSmem {
     }
 };
 
+constexpr int kRingMax = 32;  // windows up to this padded size keep their kernel column in registers
+
 // Phase B of one chunk for one user (blockIdx.x = k).  Thread u owns live-range sample u
 // (RS = 32 S threads); a step is one CTA barrier: window threads publish their beta, then every
 // thread adds the window's contribution to its own prediction.  WP is the window rounded up to a
@@ -175,7 +177,9 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
 #pragma unroll
                 for (int j = 0; j < 8; ++j) gs[j] += src[(sl + j) * stride];
             }
-            for (int j = 0; sl + j < a.n_slices; ++j) gs[j] += src[(sl + j) * stride];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (sl + j < a.n_slices) gs[j] += src[(sl + j) * stride];
             p = a.wG * (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])));
         }
     }
@@ -204,38 +208,91 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     const bool log_cases = a.case_log != nullptr;
     const float muq_full = a.mu / (float)W;  // mu q with q = 1/W once the window is full
     const float *kcol = s_kmat + u;          // column u of the kernel table
-    for (int n = s0; n < s1; ++n) {
-        const int un = n - l0;
-        // a new pilot arrives at n = 2t: the oldest entry is dropped once D are held
-        if (evict && !(n & 1) && (n >> 1) >= D) {
-            const int e = (n >> 1) - t0;
-            p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u], s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
-        }
-        const int ujlo = max(0, n - W + 1) - l0;
-        const float muq = (n >= W - 1) ? muq_full : a.mu / (float)(n + 1);  // mu q, q = 1/|J_n|
-        float *bb = s_beta + (n & 1) * (WP + RS) + WP;
-        if (u >= ujlo && u <= un) {
-            const float e = p - b;  // <f_n, kappa(x_j,.)> - b_j
-            // Eq. beta without branches: (-e - eps) below the slab, (eps - e) above it, 0 inside
-            const float beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
-            gam = fmaf(muq, beta, gam);
-            bb[u] = beta;
-            if (log_cases)
-                a.case_log[((size_t)n * W + (m - n + W - 1)) * K + k] = (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
-        } else if (u < ujlo && u > un - WP) {
-            bb[u] = 0.f;
-        }
-        __syncthreads();
-        // p_u += mu q sum_{i in J_n} beta_i kappa(x_i, x_u)
-        const float *kp = kcol + (un - WP + 1) * RS;
-        const float *bp = bb + (un - WP + 1);
-        float acc0 = 0.f, acc1 = 0.f;
+    if constexpr (WP <= kRingMax) {
+        // Window ring: sample j sits in slot (j - s0) mod WP.  kc[r] holds kappa(x_j, x_u) of the
+        // sample j currently in slot r, the betas of the step sit in a ring of WP floats (two,
+        // alternating by step parity), so the window sum is WP register FMAs over broadcast
+        // vector loads.  Slots of samples that left the window (WP > W) hold beta = 0.
+        float kc[WP];
 #pragma unroll
-        for (int d = 0; d < WP; d += 2) {
-            acc0 = fmaf(bp[d], kp[d * RS], acc0);
-            acc1 = fmaf(bp[d + 1], kp[(d + 1) * RS], acc1);
+        for (int r = 0; r < WP; ++r) kc[r] = kcol[(s0 - WP + r - l0) * RS];  // rows >= -WP: zero rows
+        const int slot = valid ? (m - s0 + WP) % WP : 0;
+        for (int nb = s0; nb < s1; nb += WP) {
+#pragma unroll
+            for (int r = 0; r < WP; ++r) {
+                const int n = nb + r;
+                if (n >= s1) break;
+                const int un = n - l0;
+                kc[r] = kcol[un * RS];  // sample n enters slot r
+                if (evict && !(n & 1) && (n >> 1) >= D) {
+                    const int e = (n >> 1) - t0;
+                    p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u],
+                                     s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
+                }
+                float muq = muq_full;
+                if (n < W - 1) muq = a.mu / (float)(n + 1);  // mu q, q = 1/|J_n|
+                float *ring = s_beta + (r & 1) * WP;          // nb - s0 is a multiple of WP (even)
+                if (valid && m <= n && m > n - WP) {
+                    float beta = 0.f;
+                    if (m > n - W) {
+                        const float e = p - b;  // <f_n, kappa(x_j,.)> - b_j
+                        // Eq. beta without branches: (-e - eps) below the slab, (eps - e) above, 0 inside
+                        beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
+                        gam = fmaf(muq, beta, gam);
+                        if (log_cases)
+                            a.case_log[((size_t)n * W + (m - n + W - 1)) * K + k] =
+                                (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
+                    }
+                    ring[slot] = beta;
+                }
+                __syncthreads();
+                // p_u += mu q sum_{i in J_n} beta_i kappa(x_i, x_u)
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int q4 = 0; q4 < WP; q4 += 4) {
+                    const float4 bv = *reinterpret_cast<const float4 *>(ring + q4);
+                    acc[0] = fmaf(bv.x, kc[q4], acc[0]);
+                    acc[1] = fmaf(bv.y, kc[q4 + 1], acc[1]);
+                    acc[2] = fmaf(bv.z, kc[q4 + 2], acc[2]);
+                    acc[3] = fmaf(bv.w, kc[q4 + 3], acc[3]);
+                }
+                p = fmaf(muq, (acc[0] + acc[1]) + (acc[2] + acc[3]), p);
+            }
         }
-        p = fmaf(muq, acc0 + acc1, p);
+    } else {
+        for (int n = s0; n < s1; ++n) {
+            const int un = n - l0;
+            // a new pilot arrives at n = 2t: the oldest entry is dropped once D are held
+            if (evict && !(n & 1) && (n >> 1) >= D) {
+                const int e = (n >> 1) - t0;
+                p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u], s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
+            }
+            const int ujlo = max(0, n - W + 1) - l0;
+            const float muq = (n >= W - 1) ? muq_full : a.mu / (float)(n + 1);  // mu q, q = 1/|J_n|
+            float *bb = s_beta + (n & 1) * (WP + RS) + WP;
+            if (u >= ujlo && u <= un) {
+                const float e = p - b;  // <f_n, kappa(x_j,.)> - b_j
+                // Eq. beta without branches: (-e - eps) below the slab, (eps - e) above it, 0 inside
+                const float beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
+                gam = fmaf(muq, beta, gam);
+                bb[u] = beta;
+                if (log_cases)
+                    a.case_log[((size_t)n * W + (m - n + W - 1)) * K + k] = (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
+            } else if (u < ujlo && u > un - WP) {
+                bb[u] = 0.f;
+            }
+            __syncthreads();
+            // p_u += mu q sum_{i in J_n} beta_i kappa(x_i, x_u)
+            const float *kp = kcol + (un - WP + 1) * RS;
+            const float *bp = bb + (un - WP + 1);
+            float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+            for (int d = 0; d < WP; d += 2) {
+                acc0 = fmaf(bp[d], kp[d * RS], acc0);
+                acc1 = fmaf(bp[d + 1], kp[(d + 1) * RS], acc1);
+            }
+            p = fmaf(muq, acc0 + acc1, p);
+        }
     }
 
     // ---- write back: coefficients, carried predictions, linear filter ---------------------------
