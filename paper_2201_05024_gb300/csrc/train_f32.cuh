@@ -20,6 +20,8 @@
 //   train_chunk_kernel  phase B of one chunk.
 #pragma once
 
+#include <type_traits>
+
 #include "apsm_common.cuh"
 
 namespace apsm {
@@ -98,7 +100,7 @@ struct ChunkSmem {
         gev = kmat + (g.WP + RS) * RS * 4;
         egam = gev + (g.P > g.D ? g.T * 2 * RS * 4 : 0);   // dropped-entry table only when P > D
         beta = egam + round_up(g.T * 2 * 4, 16);
-        dg = beta + 2 * (RS + g.WP) * 4;
+        dg = beta + (4 * RS + 2 * g.WP + 128) * 4;  // beta ring, or p / gamma / b / 1/kappa + rings
         clin = dg + RS * 4;
         pil = clin + round_up(g.M * 8, 16);
         bytes = pil + npil * g.M * 8;
@@ -106,6 +108,7 @@ struct ChunkSmem {
 };
 
 constexpr int kRingMax = 32;  // windows up to this padded size keep their kernel column in registers
+constexpr int kBlockMin = 8;  // shortest step block of the blocked form (padded windows up to 24)
 
 // Phase B of one chunk for one user (blockIdx.x = k).  Thread u owns live-range sample u
 // (RS = 32 S threads); a step is one CTA barrier: window threads publish their beta, then every
@@ -167,19 +170,18 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
             p = a.carry[u * K + k];
             gam = a.gamma[((size_t)(pa % D) * 2 + l) * K + k];
         } else {
-            // Gaussian part of f_{s0}(x_m) from the phase-A slices: eight interleaved partial sums
-            // (loads in flight together), combined in a fixed order
+            // Gaussian part of f_{s0}(x_m) from the phase-A slices: 32 loads in flight at a time,
+            // summed into eight partial sums (slice i into sum i mod 8) combined in a fixed order
             const float *src = a.partial + (size_t)(pa - t0) * 2 * K + l * K + k;
             const size_t stride = (size_t)Tc * 2 * K;
             float gs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            int sl = 0;
-            for (; sl + 8 <= a.n_slices; sl += 8) {
+            for (int sl = 0; sl < a.n_slices; sl += 32) {
+                float v[32];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) gs[j] += src[(sl + j) * stride];
+                for (int j = 0; j < 32; ++j) v[j] = sl + j < a.n_slices ? src[(sl + j) * stride] : 0.f;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) gs[j & 7] += v[j];
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (sl + j < a.n_slices) gs[j] += src[(sl + j) * stride];
             p = a.wG * (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])));
         }
     }
@@ -208,7 +210,129 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     const bool log_cases = a.case_log != nullptr;
     const float muq_full = a.mu / (float)W;  // mu q with q = 1/W once the window is full
     const float *kcol = s_kmat + u;          // column u of the kernel table
-    if constexpr (WP <= kRingMax) {
+    if constexpr (WP + kBlockMin - 1 <= 32) {
+        // Blocked form.  Over a block of B = 32 - WP steps from n0, every sample that is in a
+        // window of the block lies in [n0 - WP + 1, n0 + B - 1]: 31 samples, one per lane of warp 0.
+        // That warp runs the B steps alone: the window lanes compute mu q beta (Eq. beta, written
+        // as beta = clamp(p, b - eps, b + eps) - p over kappa_jj), publish it in a 32-float ring and
+        // every lane adds the window sum to its own prediction with the kernel values held in
+        // registers; one warp barrier per step.  Since kappa(x_j, x_m) does not depend on the step,
+        // the block then moves every later sample m >= n0 + B by
+        //   sum_j kappa(x_j, x_m) sum_{n in block} mu q_n beta_j(n)
+        // at once: the lanes publish their summed updates and all threads apply them.
+        constexpr int B = 32 - WP;
+        constexpr int NL = WP + B - 1;
+        float *s_p = s_beta, *s_g = s_p + RS, *s_b = s_g + RS, *s_rk = s_b + RS, *s_agg = s_rk + RS;
+        float *s_w = s_agg + 32, *s_muq = s_w + 64;
+        if (valid) {
+            s_p[u] = p;
+            s_g[u] = gam;
+            s_b[u] = b;
+            s_rk[u] = rk;
+        }
+        if (u < 32) s_muq[u] = a.mu / (float)(u + 1);  // mu q while the window is filling (n < W - 1)
+        for (int i = u; i < 64; i += RS) s_w[i] = 0.f;
+        __syncthreads();
+        const int lane = u & 31;
+        for (int n0 = s0; n0 < s1; n0 += B) {
+            const int wl0 = n0 - WP + 1;  // sample of lane 0
+            if (u < 32) {
+                const int ms = wl0 + lane, lu = ms - l0;
+                const bool lv = lane < NL && ms >= l0 && ms < s1;
+                const int col = lv ? lu : 0;
+                float pl = 0.f, c1 = 0.f, c2 = 0.f, rkl = 0.f, agg = 0.f;
+                if (lv) {
+                    pl = s_p[lu];
+                    c1 = s_b[lu] - a.eps;  // the hyperslab [b - eps, b + eps]
+                    c2 = s_b[lu] + a.eps;
+                    rkl = s_rk[lu];
+                }
+                float kc[NL];  // kappa(x_{wl0+j}, x of this lane)
+#pragma unroll
+                for (int j = 0; j < NL; ++j) {
+                    const int row = wl0 + j - l0;  // >= -WP + 1: the zero rows
+                    kc[j] = row < R ? s_kmat[row * RS + col] : 0.f;
+                }
+                auto steps = [&](auto tail_c, auto evict_c) {
+                    constexpr bool kTail = decltype(tail_c)::value, kEvict = decltype(evict_c)::value;
+#pragma unroll
+                    for (int s = 0; s < B; ++s) {
+                        const int n = n0 + s;
+                        if (kTail && n >= s1) break;
+                        if (kEvict && !(n & 1) && (n >> 1) >= D) {
+                            const int e = (n >> 1) - t0;
+                            pl -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + col],
+                                              s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + col]);
+                        }
+                        const float muq = n < W - 1 ? s_muq[n] : muq_full;  // mu q, q = 1/|J_n|
+                        // window J_n = samples [n - W + 1, n] = lanes [s + WP - W, s + WP - 1]
+                        const bool inw = lv && lane >= s + WP - W && lane <= s + WP - 1;
+                        const float sc = inw ? muq * rkl : 0.f;
+                        const float mb = (fminf(fmaxf(pl, c1), c2) - pl) * sc;  // mu q beta_j
+                        agg += mb;
+                        if (log_cases && inw)
+                            a.case_log[((size_t)n * W + (ms - n + W - 1)) * K + k] =
+                                (int8_t)(pl < c1 ? -1 : (pl > c2 ? 1 : 0));
+                        float *ring = s_w + (s & 1) * 32;
+                        ring[lane] = mb;
+                        __syncwarp();
+                        float acc[4] = {pl, 0.f, 0.f, 0.f};
+                        const int b4 = s & ~3;
+#pragma unroll
+                        for (int q4 = 0; q4 < WP + 4; q4 += 4) {
+                            const float4 v = *reinterpret_cast<const float4 *>(ring + b4 + q4);
+                            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const int j = b4 + q4 + r;
+                                if (j >= s && j < s + WP) acc[(j - s) & 3] = fmaf(vv[r], kc[j], acc[(j - s) & 3]);
+                            }
+                        }
+                        pl = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+                    }
+                };
+                using T_ = std::true_type;
+                using F_ = std::false_type;
+                const bool tail = n0 + B > s1;
+                if (evict) {
+                    if (tail) steps(T_{}, T_{});
+                    else steps(F_{}, T_{});
+                } else {
+                    if (tail) steps(T_{}, F_{});
+                    else steps(F_{}, F_{});
+                }
+                if (lv) {
+                    s_p[lu] = pl;
+                    s_g[lu] += agg;
+                }
+                s_agg[lane] = lv ? agg : 0.f;
+            }
+            __syncthreads();
+            // the block's moves of every later sample, and its dropped entries
+            if (valid && m >= n0 + B) {
+                const int r0 = wl0 - l0;
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < NL; ++j)
+                    if (r0 + j < R) acc[j & 3] = fmaf(s_agg[j], kcol[(r0 + j) * RS], acc[j & 3]);
+                float pv = s_p[u] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+                if (evict) {
+                    for (int n = n0 + (n0 & 1); n < min(n0 + B, s1); n += 2) {
+                        if ((n >> 1) < D) continue;
+                        const int e = (n >> 1) - t0;
+                        pv -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u],
+                                          s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
+                    }
+                }
+                s_p[u] = pv;
+            }
+            __syncthreads();
+        }
+        if (valid) {
+            p = s_p[u];
+            gam = s_g[u];
+        }
+    } else if constexpr (WP <= kRingMax) {
         // Window ring: sample j sits in slot (j - s0) mod WP.  kc[r] holds kappa(x_j, x_u) of the
         // sample j currently in slot r, the betas of the step sit in a ring of WP floats (two,
         // alternating by step parity), so the window sum is WP register FMAs over broadcast
@@ -303,17 +427,44 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         if (m >= l0n) a.carry[(m - l0n) * K + k] = p;
     }
     __syncthreads();
-    // c_k += sum_u dgamma_u x~_u, with x~ = r(t) for r1(t) and -i r(t) for r2(t)
-    for (int mm = u; mm < M; mm += RS) {
-        float2 c = s_clin[mm];
-        for (int v = 0; v < R; ++v) {
-            const int mv = l0 + v;
-            const float d = s_dg[v];
-            const float2 x = s_pil[((mv >> 1) - pa0) * M + mm];
-            if (mv & 1) { c.x = fmaf(d, x.y, c.x); c.y = fmaf(-d, x.x, c.y); }
-            else        { c.x = fmaf(d, x.x, c.x); c.y = fmaf(d, x.y, c.y); }
+    // c_k += sum_u dgamma_u x~_u, with x~ = r(t) for r1(t) and -i r(t) for r2(t): the live range
+    // is split into np parts per antenna, partial sums combined in a fixed order
+    {
+        const int np = max(1, min(RS / M, 16));
+        float2 *s_part = reinterpret_cast<float2 *>(s_beta);  // free after the recurrence
+        for (int tid = u; tid < np * M; tid += RS) {
+            const int mm = tid % M, part = tid / M;
+            const int v0 = R * part / np, v1 = R * (part + 1) / np;
+            float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+            int v = v0;
+            for (; v + 1 < v1; v += 2) {
+                const int ma = l0 + v, mb = ma + 1;
+                const float da = s_dg[v], db = s_dg[v + 1];
+                const float2 xa = s_pil[((ma >> 1) - pa0) * M + mm], xb = s_pil[((mb >> 1) - pa0) * M + mm];
+                if (ma & 1) { c0.x = fmaf(da, xa.y, c0.x); c0.y = fmaf(-da, xa.x, c0.y); }
+                else        { c0.x = fmaf(da, xa.x, c0.x); c0.y = fmaf(da, xa.y, c0.y); }
+                if (mb & 1) { c1.x = fmaf(db, xb.y, c1.x); c1.y = fmaf(-db, xb.x, c1.y); }
+                else        { c1.x = fmaf(db, xb.x, c1.x); c1.y = fmaf(db, xb.y, c1.y); }
+            }
+            if (v < v1) {
+                const int ma = l0 + v;
+                const float da = s_dg[v];
+                const float2 xa = s_pil[((ma >> 1) - pa0) * M + mm];
+                if (ma & 1) { c0.x = fmaf(da, xa.y, c0.x); c0.y = fmaf(-da, xa.x, c0.y); }
+                else        { c0.x = fmaf(da, xa.x, c0.x); c0.y = fmaf(da, xa.y, c0.y); }
+            }
+            s_part[part * M + mm] = make_float2(c0.x + c1.x, c0.y + c1.y);
         }
-        a.clin[mm * K + k] = c;
+        __syncthreads();
+        for (int mm = u; mm < M; mm += RS) {
+            float2 c = s_clin[mm];
+            for (int part = 0; part < np; ++part) {
+                const float2 d = s_part[part * M + mm];
+                c.x += d.x;
+                c.y += d.y;
+            }
+            a.clin[mm * K + k] = c;
+        }
     }
 
     // ---- new dictionary entries of this chunk (slot t % D), their norms, bookkeeping -------
