@@ -116,6 +116,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     float2 *s_clin = reinterpret_cast<float2 *>(smem + S::kClinOffset);
     float *s_red = reinterpret_cast<float *>(smem + S::kReduceOffset);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
+    pdl_enter();
 
     int n_ent = a.n_entries;
     if (a.meta) n_ent = min(n_ent, max(__ldg(a.meta), 0));
@@ -373,15 +374,16 @@ cudaError_t launch_detect_f32(const DetectArgs &a, int grid_y, DetectShape sh, c
             auto fn = detect_f32_kernel<M, K, 2>;
             cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
-            fn<<<grid, block, smem, stream>>>(a);
-            return cudaGetLastError();
+            e = launch_pdl(fn, grid, block, smem, stream, a);
+            return e != cudaSuccess ? e : cudaGetLastError();
         }
     }
     {
         auto fn = detect_f32_kernel<M, K, 1>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
-        fn<<<grid, block, smem, stream>>>(a);
+        e = launch_pdl(fn, grid, block, smem, stream, a);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

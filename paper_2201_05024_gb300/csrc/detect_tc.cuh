@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc_kernel(const TcArgs a
     using Sh = TcShape<M, kPrec>;
     using L = TcSmem<M, KB, kPrec>;
     extern __shared__ __align__(1024) unsigned char smem[];
+    pdl_enter();
     unsigned char *sA = smem + L::kA;
     unsigned char *sB = smem + L::kB;
     float *sG = reinterpret_cast<float *>(smem + L::kG);
@@ -376,8 +377,8 @@ cudaError_t launch_detect_tc(const TcArgs &a, cudaStream_t stream) {
     auto fn = detect_tc_kernel<M, KB, kPrec>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
     if (e != cudaSuccess) return e;
-    fn<<<grid, kTcThreads, L::kBytes, stream>>>(a);
-    return cudaGetLastError();
+    e = launch_pdl(fn, dim3(grid), dim3(kTcThreads), L::kBytes, stream, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 using TcLauncher = cudaError_t (*)(const TcArgs &, cudaStream_t);

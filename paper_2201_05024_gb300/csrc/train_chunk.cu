@@ -6,6 +6,7 @@ namespace apsm {
 
 __global__ void train_gram_kernel(const float2 *__restrict__ rx, TrainGeom g, float k2, float wL, float wG,
                                   float *__restrict__ kmat, float *__restrict__ gev) {
+    pdl_enter();
     const int c = blockIdx.y;
     int t0, Tc, s0, s1, l0;
     chunk_range(g, c, t0, Tc, s0, s1, l0);
@@ -44,8 +45,8 @@ cudaError_t launch_train_gram(const float2 *rx, const TrainGeom &g, float k2, fl
                               float *gev, cudaStream_t stream) {
     const int per_chunk = g.RS * g.RS + g.T * 2 * g.RS;
     dim3 grid((per_chunk + 255) / 256, g.n_chunks);
-    train_gram_kernel<<<grid, 256, 0, stream>>>(rx, g, k2, wL, wG, kmat, gev);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(train_gram_kernel, grid, dim3(256), 0, stream, rx, g, k2, wL, wG, kmat, gev);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int S, int WP>
@@ -53,8 +54,8 @@ cudaError_t launch_chunk_sw(const ChunkArgs &a, int smem, cudaStream_t stream) {
     auto fn = train_chunk_kernel<S, WP>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    fn<<<a.g.K, 32 * S, smem, stream>>>(a);
-    return cudaGetLastError();
+    e = launch_pdl(fn, dim3(a.g.K), dim3(32 * S), smem, stream, a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);

@@ -118,6 +118,7 @@ template <int S, int WP>
 __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int RS = 32 * S;
+    pdl_enter();
     const TrainGeom &g = a.g;
     const ChunkSmem L(g);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
