@@ -151,14 +151,15 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         if (evict) bulk_g2s(s_gev, a.gev + (size_t)a.chunk * g.T * 2 * RS, gb, bar);
         bulk_g2s(s_pil, a.rx + (size_t)pa0 * M, pb, bar);
     }
-    for (int mm = u; mm < M; mm += RS) s_clin[mm] = a.clin[mm * K + k];
-    for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
-    for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
+    // every global load of the prologue is issued before the first use (one round trip)
+    float2 clin_r[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // M <= 64 <= 2 RS
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (u + i * RS < M) clin_r[i] = a.clin[(u + i * RS) * K + k];
     // coefficients of the entries dropped in this chunk (entry t0+e-D at step 2(t0+e))
-    if (evict && u < 2 * Tc) {
-        const int e = u >> 1, l = u & 1;
-        s_egam[u] = (t0 + e >= D) ? a.gamma[((size_t)((t0 + e - D) % D) * 2 + l) * K + k] : 0.f;
-    }
+    float egam_r = 0.f;
+    if (evict && u < 2 * Tc && t0 + (u >> 1) >= D)
+        egam_r = a.gamma[((size_t)((t0 + (u >> 1) - D) % D) * 2 + (u & 1)) * K + k];
 
     // ---- this thread's sample: target, coefficient, prediction at chunk start ---------------
     float p = 0.f, gam = 0.f, b = 0.f;
@@ -187,6 +188,12 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         }
     }
     const float gam0 = gam;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+        if (u + i * RS < M) s_clin[u + i * RS] = clin_r[i];
+    if (evict && u < 2 * Tc) s_egam[u] = egam_r;
+    for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
+    for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
     __syncthreads();
     if (!mbar_wait_bounded(bar, 0)) {
         if (u == 0) report(a.meta + 3, APSM_ERR_TIMEOUT);
@@ -197,13 +204,18 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         const float kjj = s_kmat[u * RS + u];
         rk = kjj != 0.f ? 1.f / kjj : 0.f;
         if (m >= s0) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
+            // each pilot starts at its own antenna so the lanes of a warp hit distinct banks
             const float2 *rv = s_pil + (pa - pa0) * M;
-            float lin = 0.f;
-            for (int mm = 0; mm < M; ++mm) {
-                const float2 c = s_clin[mm], x = rv[mm];
-                lin = l ? fmaf(c.x, x.y, fmaf(-c.y, x.x, lin)) : fmaf(c.x, x.x, fmaf(c.y, x.y, lin));
+            float lin0 = 0.f, lin1 = 0.f;
+            int mm = pa % M;
+            for (int i = 0; i < M; i += 2) {
+                const int mb = mm + 1 == M ? 0 : mm + 1;
+                const float2 c = s_clin[mm], x = rv[mm], cb = s_clin[mb], xb = rv[mb];
+                lin0 = l ? fmaf(c.x, x.y, fmaf(-c.y, x.x, lin0)) : fmaf(c.x, x.x, fmaf(c.y, x.y, lin0));
+                lin1 = l ? fmaf(cb.x, xb.y, fmaf(-cb.y, xb.x, lin1)) : fmaf(cb.x, xb.x, fmaf(cb.y, xb.y, lin1));
+                mm = mb + 1 == M ? 0 : mb + 1;
             }
-            p = fmaf(a.wL, lin, p);
+            p = fmaf(a.wL, lin0 + lin1, p);
         }
     }
 
@@ -254,24 +266,25 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                     const int row = wl0 + j - l0;  // >= -WP + 1: the zero rows
                     kc[j] = row < R ? s_kmat[row * RS + col] : 0.f;
                 }
-                auto steps = [&](auto tail_c, auto evict_c) {
-                    constexpr bool kTail = decltype(tail_c)::value, kEvict = decltype(evict_c)::value;
+                // kChecked: a partial last block, the filling window (n < W - 1) or case logging
+                auto steps = [&](auto checked_c, auto evict_c) {
+                    constexpr bool kChecked = decltype(checked_c)::value, kEvict = decltype(evict_c)::value;
 #pragma unroll
                     for (int s = 0; s < B; ++s) {
                         const int n = n0 + s;
-                        if (kTail && n >= s1) break;
+                        if (kChecked && n >= s1) break;
                         if (kEvict && !(n & 1) && (n >> 1) >= D) {
                             const int e = (n >> 1) - t0;
                             pl -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + col],
                                               s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + col]);
                         }
-                        const float muq = n < W - 1 ? s_muq[n] : muq_full;  // mu q, q = 1/|J_n|
+                        const float muq = kChecked && n < W - 1 ? s_muq[n] : muq_full;  // mu q, q = 1/|J_n|
                         // window J_n = samples [n - W + 1, n] = lanes [s + WP - W, s + WP - 1]
                         const bool inw = lv && lane >= s + WP - W && lane <= s + WP - 1;
                         const float sc = inw ? muq * rkl : 0.f;
                         const float mb = (fminf(fmaxf(pl, c1), c2) - pl) * sc;  // mu q beta_j
                         agg += mb;
-                        if (log_cases && inw)
+                        if (kChecked && log_cases && inw)
                             a.case_log[((size_t)n * W + (ms - n + W - 1)) * K + k] =
                                 (int8_t)(pl < c1 ? -1 : (pl > c2 ? 1 : 0));
                         float *ring = s_w + (s & 1) * 32;
@@ -294,12 +307,12 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 };
                 using T_ = std::true_type;
                 using F_ = std::false_type;
-                const bool tail = n0 + B > s1;
+                const bool checked = n0 + B > s1 || n0 < W - 1 || log_cases;
                 if (evict) {
-                    if (tail) steps(T_{}, T_{});
+                    if (checked) steps(T_{}, T_{});
                     else steps(F_{}, T_{});
                 } else {
-                    if (tail) steps(T_{}, F_{});
+                    if (checked) steps(T_{}, F_{});
                     else steps(F_{}, F_{});
                 }
                 if (lv) {
