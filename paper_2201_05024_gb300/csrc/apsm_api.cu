@@ -349,6 +349,7 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         ca.n_slices = n_slices;
         ca.carry = carry;
         ca.case_log = case_log;
+        ca.early = n_alive > 0 ? 1 : 0;  // the launch before this one is this chunk's phase A
         if (chunk(ca, layout.bytes, strm) != cudaSuccess) return APSM_ERR_CUDA;
         g_launches++;
     }

@@ -88,9 +88,13 @@ __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / 
 // predecessor in the stream is still running (its launch and shared-memory setup overlap the
 // predecessor); before touching any memory it waits for the predecessor to complete, then lets
 // its own successor begin launching.  Launched without the attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Since every kernel triggers its successor only after its own wait, a kernel that starts early
+// may already rely on everything two launches back having completed.
 __device__ __forceinline__ void pdl_enter() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();
+    pdl_trigger();
 }
 
 template <typename... KArgs, typename... Args>

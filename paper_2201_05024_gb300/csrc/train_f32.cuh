@@ -87,6 +87,7 @@ struct ChunkArgs {
     int n_slices;
     float *carry;           // [W][K]
     int8_t *case_log;       // [2P][W][K] nullable
+    int early;              // launched right after this chunk's phase A: stage before waiting
 };
 
 // Shared-memory layout of phase B (bytes; every region 16-byte aligned).
@@ -118,7 +119,7 @@ template <int S, int WP>
 __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int RS = 32 * S;
-    pdl_enter();
+    if (!a.early) pdl_wait();
     const TrainGeom &g = a.g;
     const ChunkSmem L(g);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
@@ -171,20 +172,6 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         if (m < s0) {
             p = a.carry[u * K + k];
             gam = a.gamma[((size_t)(pa % D) * 2 + l) * K + k];
-        } else {
-            // Gaussian part of f_{s0}(x_m) from the phase-A slices: 32 loads in flight at a time,
-            // summed into eight partial sums (slice i into sum i mod 8) combined in a fixed order
-            const float *src = a.partial + (size_t)(pa - t0) * 2 * K + l * K + k;
-            const size_t stride = (size_t)Tc * 2 * K;
-            float gs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int sl = 0; sl < a.n_slices; sl += 32) {
-                float v[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = sl + j < a.n_slices ? src[(sl + j) * stride] : 0.f;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) gs[j & 7] += v[j];
-            }
-            p = a.wG * (((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])));
         }
     }
     const float gam0 = gam;
@@ -215,8 +202,28 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 lin1 = l ? fmaf(cb.x, xb.y, fmaf(-cb.y, xb.x, lin1)) : fmaf(cb.x, xb.x, fmaf(cb.y, xb.y, lin1));
                 mm = mb + 1 == M ? 0 : mb + 1;
             }
-            p = fmaf(a.wL, lin0 + lin1, p);
+            p = a.wL * (lin0 + lin1);
         }
+    }
+    // Everything above reads only what the previous chunk's phase B (complete before this kernel
+    // could launch, when the launch directly follows this chunk's phase A) and the kernel tables
+    // wrote; the phase-A partial sums below need phase A itself to have completed.
+    if (a.early) pdl_wait();
+    pdl_trigger();
+    if (valid && m >= s0) {
+        // Gaussian part of f_{s0}(x_m) from the phase-A slices: 32 loads in flight at a time,
+        // summed into eight partial sums (slice i into sum i mod 8) combined in a fixed order
+        const float *src = a.partial + (size_t)(pa - t0) * 2 * K + l * K + k;
+        const size_t stride = (size_t)Tc * 2 * K;
+        float gs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int sl = 0; sl < a.n_slices; sl += 32) {
+            float v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = sl + j < a.n_slices ? src[(sl + j) * stride] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) gs[j & 7] += v[j];
+        }
+        p = fmaf(a.wG, ((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])), p);
     }
 
     // ---- the recurrence over the chunk's samples -----------------------------------------------
