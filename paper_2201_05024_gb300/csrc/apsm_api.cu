@@ -147,18 +147,24 @@ TrainGeom train_geom(const apsm_params *p, int P) {
     g.W = p->window;
     g.D = p->dict_cap;
     g.P = P;
-    // Entries dropped inside a chunk must be older than the chunk's live range: 2D > 2T + W - 2.
+    // Entries dropped inside a chunk must be older than the chunk's live range, whose first pilot
+    // is t0 - floor(W/2): D >= T + floor(W/2).  The same bound keeps a chunk's live range in the
+    // dictionary at the next chunk's start (needed by the tracked form).
     int T = env_int("APSM_TRAIN_CHUNK", 64);
     if (T < 1) T = 64;
-    T = std::min(T, (2 * g.D - g.W + 1) / 2);
-    T = std::min(T, (kMaxChunkThreads - g.W + 1) / 2);  // one thread per live-range sample
+    T = std::min(T, g.D - g.W / 2);
+    T = std::min(T, (kMaxChunkThreads - g.W) / 2);  // one thread per live-range sample
     T = std::max(T, 1);
     g.WP = padded_window(g.W);
     g.slice = kTileEntries;
+    const bool want_track = env_int("APSM_TRAIN_TRACK", 1) != 0;
     for (;; --T) {  // the largest chunk whose phase-B tables fit in shared memory
         g.T = T;
-        g.RMAX = 2 * T + g.W - 1;
+        g.RMAX = 2 * T + g.W;
         g.RS = round_up(g.RMAX, 32);
+        g.KXS = round_up(2 * T, 32);
+        // tracking needs the blocked form (padded window <= 24) and a warp besides the window warp
+        g.track = want_track && g.WP <= 24 && g.RS >= 64 && 2 * T <= 2 * (g.RS - 32) ? 1 : 0;
         if (T == 1 || ChunkSmem(g).bytes <= kMaxSmemBytes) break;
     }
     g.n_chunks = P > 0 ? (P + T - 1) / T : 0;
@@ -166,7 +172,8 @@ TrainGeom train_geom(const apsm_params *p, int P) {
 }
 
 struct TrainWs {
-    size_t kmat, gev, partial, carry, total;
+    size_t kmat, gev, kx, partial[2], track[2], carry, total;
+    int max_slices;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -178,9 +185,18 @@ TrainWs train_ws(const TrainGeom &g) {
     off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.RS * g.RS);
     w.gev = off;
     off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.T * 2 * g.RS);
-    w.partial = off;
-    const int max_slices = (g.D + g.slice - 1) / g.slice;
-    off = align256(off + sizeof(float) * (size_t)max_slices * g.T * 2 * g.K);
+    w.kx = off;
+    if (g.track) off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.RS * g.KXS);
+    // slot segments of the frozen entries start at a tile boundary: up to two extra slices
+    w.max_slices = (g.D + g.slice - 1) / g.slice + 2;
+    for (int i = 0; i < 2; ++i) {
+        w.partial[i] = off;
+        if (i == 0 || g.track) off = align256(off + sizeof(float) * (size_t)w.max_slices * g.T * 2 * g.K);
+    }
+    for (int i = 0; i < 2; ++i) {
+        w.track[i] = off;
+        if (g.track) off = align256(off + sizeof(float) * (size_t)g.KXS * g.K);
+    }
     w.carry = off;
     off = align256(off + sizeof(float) * (size_t)g.W * g.K);
     w.total = g.n_chunks > 0 ? off : 0;
@@ -287,14 +303,17 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
     unsigned char *wsb = static_cast<unsigned char *>(workspace);
     float *kmat = reinterpret_cast<float *>(wsb + ws.kmat);
     float *gev = reinterpret_cast<float *>(wsb + ws.gev);
-    float *partial = reinterpret_cast<float *>(wsb + ws.partial);
+    float *kx = reinterpret_cast<float *>(wsb + ws.kx);
+    float *partial[2] = {reinterpret_cast<float *>(wsb + ws.partial[0]), reinterpret_cast<float *>(wsb + ws.partial[1])};
+    float *track[2] = {reinterpret_cast<float *>(wsb + ws.track[0]), reinterpret_cast<float *>(wsb + ws.track[1])};
     float *carry = reinterpret_cast<float *>(wsb + ws.carry);
     const float k2 = k2_of(p->sigma);
     const float wL = p->w_L, wG = 1.f - p->w_L;
     const float2 *rx = reinterpret_cast<const float2 *>(rx_pilot);
 
-    {   // kernel values of every chunk's live range, and of dropped entries against it
-        if (launch_train_gram(rx, g, k2, wL, wG, kmat, gev, strm) != cudaSuccess) return APSM_ERR_CUDA;
+    {   // kernel values of every chunk's live range, of dropped entries against it, and against
+        // the next chunk's samples
+        if (launch_train_gram(rx, g, k2, wL, wG, kmat, gev, kx, strm) != cudaSuccess) return APSM_ERR_CUDA;
         g_launches++;
     }
 
@@ -303,31 +322,64 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
     const ChunkSmem layout(g);
     const ChunkLauncher chunk = chunk_launcher(g.RS / 32, g.WP);
     if (!chunk) return APSM_ERR_UNSUPPORTED;
+
+    // phase A: the partial Gaussian sums of f at the start of chunk cq, at cq's pilots, over the
+    // dictionary slots [lo, lo + n) (mod D) -- the whole dictionary, or its frozen entries
+    auto phase_a = [&](int cq, int lo, int n, float *dst, int &n_slices, bool late) -> bool {
+        int t0, Tc, s0, s1, l0;
+        chunk_range(g, cq, t0, Tc, s0, s1, l0);
+        DetectArgs da{};
+        da.rx = rx + (size_t)t0 * g.M;
+        da.N = Tc;
+        da.dict = reinterpret_cast<const float2 *>(st->dict);
+        da.dict_norm = st->dict_norm;
+        da.gamma = st->gamma;
+        da.clin = reinterpret_cast<const float2 *>(st->clin);
+        da.meta = nullptr;
+        da.n_entries = g.D;
+        da.slice_entries = g.slice;
+        da.k2 = k2;
+        da.wL = wL;
+        da.wG = wG;
+        da.partial = dst;
+        da.pdl_late = late ? 1 : 0;
+        da.status = st->meta + 3;
+        const int first = lo % g.D, hi0 = std::min(g.D, first + n), hi1 = first + n - g.D;
+        da.seg0_lo = first;
+        da.seg0_hi = hi0;
+        const int ns0 = (hi0 - first / g.slice * g.slice + g.slice - 1) / g.slice;
+        int ns1 = 0;
+        if (hi1 > 0) {
+            da.seg1_lo = 0;
+            da.seg1_hi = hi1;
+            ns1 = (hi1 + g.slice - 1) / g.slice;
+        }
+        da.seg_slices = ns0;
+        n_slices = ns0 + ns1;
+        const int thr = std::min(256, round_up(Tc, 32));
+        const DetectShape sh{thr, std::max(1, 256 / thr), 1};  // entry groups share each tile
+        if (det(da, n_slices, sh, strm) != cudaSuccess) return false;
+        g_launches++;
+        return true;
+    };
+
+    int slices_of[2] = {0, 0};  // phase-A slices waiting in partial[c & 1]
     for (int c = 0; c < g.n_chunks; ++c) {
         int t0, Tc, s0, s1, l0;
         chunk_range(g, c, t0, Tc, s0, s1, l0);
-        const int n_alive = std::min(t0, g.D);
-        const int n_slices = (n_alive + g.slice - 1) / g.slice;
-        if (n_alive > 0) {  // phase A: f at chunk start, evaluated at the chunk's pilots
-            DetectArgs da{};
-            da.rx = rx + (size_t)t0 * g.M;
-            da.N = Tc;
-            da.dict = reinterpret_cast<const float2 *>(st->dict);
-            da.dict_norm = st->dict_norm;
-            da.gamma = st->gamma;
-            da.clin = reinterpret_cast<const float2 *>(st->clin);
-            da.meta = nullptr;
-            da.n_entries = n_alive;
-            da.slice_entries = g.slice;
-            da.k2 = k2;
-            da.wL = wL;
-            da.wG = wG;
-            da.partial = partial;
-            da.status = st->meta + 3;
-            const int thr = std::min(256, round_up(Tc, 32));
-            const DetectShape sh{thr, std::max(1, 256 / thr), 1};  // entry groups share each tile
-            if (det(da, n_slices, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
-            g_launches++;
+        int mode = 0;
+        if (!g.track) {
+            // f at the chunk start over the whole dictionary, between the chunks
+            const int n_alive = std::min(t0, g.D);
+            slices_of[0] = 0;
+            if (n_alive > 0) {
+                if (!phase_a(c, t0 - n_alive, n_alive, partial[0], slices_of[0], false)) return APSM_ERR_CUDA;
+                mode = 2;
+            }
+        } else {
+            // the previous launch is the previous chunk's phase B or this chunk's frozen-entry
+            // phase A; either way the kernel tables are complete
+            mode = c > 0 ? 1 : 0;
         }
         ChunkArgs ca{};
         ca.g = g;
@@ -345,13 +397,31 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         ca.meta = st->meta;
         ca.kmat = kmat;
         ca.gev = gev;
-        ca.partial = partial;
-        ca.n_slices = n_slices;
+        const int pb = g.track ? (c & 1) : 0;  // the tracked form alternates two phase-A buffers
+        ca.partial = partial[pb];
+        ca.n_slices = slices_of[pb];
         ca.carry = carry;
         ca.case_log = case_log;
-        ca.early = n_alive > 0 ? 1 : 0;  // the launch before this one is this chunk's phase A
+        if (g.track) {
+            ca.kx = kx + (size_t)c * g.RS * g.KXS;
+            ca.track_in = c > 0 ? track[c & 1] : nullptr;
+            ca.track_out = c + 1 < g.n_chunks ? track[(c + 1) & 1] : nullptr;
+        }
+        ca.pdl_mode = mode;
         if (chunk(ca, layout.bytes, strm) != cudaSuccess) return APSM_ERR_CUDA;
         g_launches++;
+        if (g.track && c + 1 < g.n_chunks) {
+            // frozen part of the next chunk's starting filter: pilots older than this chunk's live
+            // range still held at the next chunk's start.  Their coefficients are final once the
+            // previous chunk's phase B completed, which this chunk's phase B waits for before it
+            // lets this launch start; it runs beside this chunk's phase B.
+            int t0n, Tcn, s0n, s1n, l0n;
+            chunk_range(g, c + 1, t0n, Tcn, s0n, s1n, l0n);
+            const int f0 = std::max(0, t0n - g.D), f1 = l0 / 2;
+            slices_of[(c + 1) & 1] = 0;
+            if (f1 > f0 && !phase_a(c + 1, f0, f1 - f0, partial[(c + 1) & 1], slices_of[(c + 1) & 1], true))
+                return APSM_ERR_CUDA;
+        }
     }
     return APSM_OK;
 }

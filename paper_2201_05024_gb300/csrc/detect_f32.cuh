@@ -63,6 +63,14 @@ struct DetectArgs {
     uint8_t *hard;             // [N][K] nullable
     float *partial;            // [gridDim.y][N][2K] partial mode (full mode: nullptr)
     int *status;               // device status word
+    // Optional slot segments (partial mode): when seg0_hi or seg1_hi is nonzero, grid.y slices
+    // [0, seg_slices) cover slots [seg0_lo, seg0_hi) and the rest cover [seg1_lo, seg1_hi), each
+    // segment sliced from its first 32-slot tile boundary; slots below a segment start are masked.
+    int seg_slices, seg0_lo, seg0_hi, seg1_lo, seg1_hi;
+    // Launched beside a training chunk whose own wait has already covered everything this launch
+    // reads: let the successor launch at once, skip the wait at the start, and wait for the
+    // predecessor (that chunk) only before exiting, so that completion still orders the stream.
+    int pdl_late;
 };
 
 template <int M, int K>
@@ -116,12 +124,23 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     float2 *s_clin = reinterpret_cast<float2 *>(smem + S::kClinOffset);
     float *s_red = reinterpret_cast<float *>(smem + S::kReduceOffset);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthreads = blockDim.x * blockDim.y;
-    pdl_enter();
+    if (a.pdl_late) pdl_trigger();
+    else pdl_enter();
 
     int n_ent = a.n_entries;
     if (a.meta) n_ent = min(n_ent, max(__ldg(a.meta), 0));
-    const int e_begin = blockIdx.y * a.slice_entries;
-    const int e_end = min(n_ent, e_begin + a.slice_entries);
+    int e_begin, e_end, e_lo = 0;
+    if (a.seg0_hi > 0 || a.seg1_hi > 0) {
+        const bool second = (int)blockIdx.y >= a.seg_slices;
+        const int lo = second ? a.seg1_lo : a.seg0_lo, hi = second ? a.seg1_hi : a.seg0_hi;
+        const int sl = second ? (int)blockIdx.y - a.seg_slices : (int)blockIdx.y;
+        e_begin = lo / kTileEntries * kTileEntries + sl * a.slice_entries;
+        e_end = min(hi, e_begin + a.slice_entries);
+        e_lo = lo;
+    } else {
+        e_begin = blockIdx.y * a.slice_entries;
+        e_end = min(n_ent, e_begin + a.slice_entries);
+    }
     const int n_tiles = e_end > e_begin ? (e_end - e_begin + kTileEntries - 1) / kTileEntries : 0;
 
     auto issue = [&](int tile) {
@@ -195,7 +214,8 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
         const float2 *sd = reinterpret_cast<const float2 *>(st);
         const float *sn = reinterpret_cast<const float *>(st + S::kDictBytes);
         const float *sg = reinterpret_cast<const float *>(st + S::kDictBytes + S::kNormBytes);
-        const int cnt = min(kTileEntries, e_end - (e_begin + tile * kTileEntries));
+        const int e0 = e_begin + tile * kTileEntries;
+        const int cnt = min(kTileEntries, e_end - e0);
         // fold the entry factor 2^(-k2 n_t) into the tile's coefficients
         if (tid == 0) *s_flag = 1;
         __syncthreads();
@@ -203,11 +223,12 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
             for (int i = tid; i < cnt * 2 * K; i += nthreads) {
                 const float ht = a.k2 * sn[i / (2 * K)];
                 if (ht > kFactorLimit) *s_flag = 0;
-                s_gs[i] = sg[i] * ex2(-ht);
+                s_gs[i] = e0 + i / (2 * K) >= e_lo ? sg[i] * ex2(-ht) : 0.f;  // masked below the segment
             }
         }
         if (!__syncthreads_and(ok)) {
             if (tid == 0) report(a.status, APSM_ERR_TIMEOUT);
+            if (a.pdl_late) pdl_wait();
             return;
         }
         if (cta_in_range && *s_flag) {
@@ -254,6 +275,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
             const float inv_g2 = 1.f / g2;
 #pragma unroll 1
             for (int t = threadIdx.y; t < cnt; t += blockDim.y) {
+                if (e0 + t < e_lo) continue;
                 float dA[QPT], dB[QPT], dC[QPT];
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) dA[i] = dB[i] = dC[i] = 0.f;
@@ -286,6 +308,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
         }
         if (!__syncthreads_and(ok)) {
             if (tid == 0) report(a.status, APSM_ERR_TIMEOUT);
+            if (a.pdl_late) pdl_wait();
             return;
         }
         if (tid == 0 && tile + 2 < n_tiles) issue(tile + 2);
@@ -352,6 +375,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
             for (int k = 0; k < K; ++k) a.hard[(size_t)q * K + k] = hbits[k];
         }
     }
+    if (a.pdl_late) pdl_wait();
 }
 
 // Host-side launcher for one (M, K) instantiation.

@@ -3,20 +3,28 @@
 //
 // The recurrence runs over the 2P real-split samples n = 2t + l, in chunks of T pilots.
 // For chunk c (pilots [t0, t0+Tc), samples [s0, s1)) every sample that can be touched in the
-// chunk lies in the live range L = [l0, s1), l0 = max(0, s0 - W + 1): the W-1 window samples
-// carried from the previous chunk plus the chunk's own.  Each sample m in L keeps a running
-// prediction p_m = f_n(x_m) of the current filter.  Because f is linear in its coefficients,
+// chunk lies in the live range L = [l0, s1), l0 = max(0, s0 - W + 1) rounded down to a pilot
+// boundary: the window samples carried from the previous chunk plus the chunk's own.  Each
+// sample m in L keeps a running prediction p_m = f_n(x_m) of the current filter.  Because f is
+// linear in its coefficients,
 //   f_{n+1}(x_m) = f_n(x_m) + mu q sum_{i in J_n} beta_i kappa(x_i, x_m)          (Eq. apsm)
 // exactly, so one step needs only the window's residuals, its betas (Eq. beta) and the
 // kernel values kappa(x_i, x_m) between samples of L; dropping a dictionary entry subtracts its
-// Gaussian terms.  The expensive part -- f at the start of the chunk evaluated at the chunk's
-// new samples against the whole dictionary -- is the detection kernel in partial mode, run on
-// all SMs between chunks (phase A).  The serial part (phase B) runs one CTA per user (users are
-// independent) with one thread per live-range sample, so a step is one CTA barrier.
+// Gaussian terms.
+//
+// The chunk's new samples enter with f at the chunk start.  Split the dictionary at the start of
+// chunk c+1 into the entries of chunk c's live range and the older ("frozen") ones, whose
+// coefficients no longer change after chunk c-1.  Phase B of chunk c tracks the first part for
+// the next chunk's samples as it goes (the same incremental identity, applied once per step
+// block from the block's summed coefficient changes); the frozen part is the detection kernel
+// in partial mode over those entries only (phase A), launched before chunk c's phase B and run
+// on other SMs at the same time.  When tracking is not available (single-warp live range, or
+// windows above 24) phase A covers the whole dictionary and runs between the chunks.
 //
 // Kernels:
-//   train_gram_kernel   kappa(x_u, x_v) for all u, v in L of every chunk (sum kernel, Fact 1)
-//                       and kappa_G between each entry dropped during a chunk and L.
+//   train_gram_kernel   kappa(x_u, x_v) for all u, v in L of every chunk (sum kernel, Fact 1),
+//                       kappa_G between each entry dropped during a chunk and L, and kappa
+//                       between L and the next chunk's samples.
 //   train_chunk_kernel  phase B of one chunk.
 #pragma once
 
@@ -30,11 +38,16 @@ struct TrainGeom {
     int M, K, W, D, P;
     int T;         // pilots per chunk
     int n_chunks;
-    int RMAX;      // 2T + W - 1: live-range capacity
+    int RMAX;      // 2T + W: live-range capacity
     int RS;        // row stride of the per-chunk kernel tables: RMAX rounded up to 32
     int WP;        // window W rounded up to a supported multiple of 4
     int slice;     // entries per phase-A slice
+    int KXS;       // row stride of the next-chunk table: 2T rounded up to 32
+    int track;     // phase B tracks the next chunk's samples (phase A then covers frozen entries)
 };
+
+// first sample of the live range of a chunk starting at sample s0 (a pilot boundary)
+__host__ __device__ inline int live_start(int s0, int W) { return max(0, s0 - W + 1) & ~1; }
 
 __host__ __device__ inline void chunk_range(const TrainGeom &g, int c, int &t0, int &Tc, int &s0, int &s1,
                                             int &l0) {
@@ -42,7 +55,7 @@ __host__ __device__ inline void chunk_range(const TrainGeom &g, int c, int &t0, 
     Tc = min(g.T, g.P - t0);
     s0 = 2 * t0;
     s1 = 2 * (t0 + Tc);
-    l0 = max(0, s0 - g.W + 1);
+    l0 = live_start(s0, g.W);
 }
 
 // Real-split inner product and squared distance between sample (a, la) and sample (b, lb),
@@ -63,12 +76,13 @@ __device__ inline void sample_pair(const float2 *ra, const float2 *rb, int M, in
     dist2 = fmaxf(na + nb - 2.f * dot, 0.f);
 }
 
-// Tables per chunk c (row stride RS, zero outside the live range):
-//   kmat[c][u][v] = kappa(x_{l0+u}, x_{l0+v})                       u, v < R
+// Tables per chunk c (zero outside the live range):
+//   kmat[c][u][v] = kappa(x_{l0+u}, x_{l0+v})                       u, v < R        (stride RS)
 //   gev[c][e][l][v] = kappa_G(x_{2(t0+e-D)+l}, x_{l0+v})            entry t0+e-D dropped at n = 2(t0+e)
-// (train_gram_kernel, defined in train_chunk.cu).
+//   kx[c][u][v] = kappa(x_{l0+u}, x_{s1+v})                         v < next chunk's 2Tc (stride KXS)
+// (train_gram_kernel, defined in train_chunk.cu; kx only when g.track).
 cudaError_t launch_train_gram(const float2 *rx, const TrainGeom &g, float k2, float wL, float wG, float *kmat,
-                              float *gev, cudaStream_t stream);
+                              float *gev, float *kx, cudaStream_t stream);
 
 struct ChunkArgs {
     TrainGeom g;
@@ -87,12 +101,20 @@ struct ChunkArgs {
     int n_slices;
     float *carry;           // [W][K]
     int8_t *case_log;       // [2P][W][K] nullable
-    int early;              // launched right after this chunk's phase A: stage before waiting
+    const float *kx;        // [RS][KXS] of this chunk (tracking)
+    const float *track_in;  // [2T][K]: tracked part of f at this chunk's start, at its samples
+    float *track_out;       // [2T][K]: the same for the next chunk (null: no tracking)
+    // When this launch waits for the previous one (programmatic dependent launch):
+    // 0: first thing; 1: after staging the kernel tables and pilots (tracked form: the previous
+    // launch is the frozen-entry phase A of this chunk, which completes after the previous chunk's
+    // phase B); 2: after staging everything but the phase-A sums (the previous launch is this
+    // chunk's whole-dictionary phase A, launched after the previous phase B had completed)
+    int pdl_mode;
 };
 
 // Shared-memory layout of phase B (bytes; every region 16-byte aligned).
 struct ChunkSmem {
-    int bar, kmat, gev, egam, beta, dg, clin, pil, bytes;
+    int bar, kmat, gev, egam, beta, dg, clin, pil, trk, bytes;
     __host__ __device__ ChunkSmem(const TrainGeom &g) {
         const int RS = g.RS;
         const int npil = g.T + (g.W + 1) / 2 + 1;
@@ -101,10 +123,11 @@ struct ChunkSmem {
         gev = kmat + (g.WP + RS) * RS * 4;
         egam = gev + (g.P > g.D ? g.T * 2 * RS * 4 : 0);   // dropped-entry table only when P > D
         beta = egam + round_up(g.T * 2 * 4, 16);
-        dg = beta + (4 * RS + 2 * g.WP + 128) * 4;  // beta ring, or p / gamma / b / 1/kappa + rings
+        dg = beta + (4 * RS + 2 * g.WP + 160) * 4;  // beta ring, or p / gamma / b / 1/kappa + rings
         clin = dg + RS * 4;
         pil = clin + round_up(g.M * 8, 16);
-        bytes = pil + npil * g.M * 8;
+        trk = pil + npil * g.M * 8;                   // carried coefficients [32], reduced filter [M]
+        bytes = trk + (g.track ? 32 * 4 + g.M * 8 : 0);
     }
 };
 
@@ -119,7 +142,10 @@ template <int S, int WP>
 __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int RS = 32 * S;
-    if (!a.early) pdl_wait();
+    if (a.pdl_mode == 0) {
+        pdl_wait();
+        pdl_trigger();
+    }
     const TrainGeom &g = a.g;
     const ChunkSmem L(g);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar);
@@ -130,6 +156,8 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     float *s_dg = reinterpret_cast<float *>(smem + L.dg);
     float2 *s_clin = reinterpret_cast<float2 *>(smem + L.clin);
     float2 *s_pil = reinterpret_cast<float2 *>(smem + L.pil);
+    float *s_gcar = reinterpret_cast<float *>(smem + L.trk);             // carried gamma at chunk start
+    float2 *s_clinw = reinterpret_cast<float2 *>(smem + L.trk + 32 * 4);  // filter minus carried terms
 
     const int M = g.M, K = g.K, W = g.W, D = g.D;
     int t0, Tc, s0, s1, l0;
@@ -152,6 +180,17 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         if (evict) bulk_g2s(s_gev, a.gev + (size_t)a.chunk * g.T * 2 * RS, gb, bar);
         bulk_g2s(s_pil, a.rx + (size_t)pa0 * M, pb, bar);
     }
+    const bool valid = u < R;
+    const int m = l0 + u, pa = m >> 1, l = m & 1;
+    float b = 0.f;
+    if (valid) {
+        const float2 sy = a.sym[(size_t)pa * K + k];
+        b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
+    }
+    if (a.pdl_mode == 1) {
+        pdl_wait();
+        pdl_trigger();
+    }
     // every global load of the prologue is issued before the first use (one round trip)
     float2 clin_r[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // M <= 64 <= 2 RS
 #pragma unroll
@@ -163,15 +202,13 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         egam_r = a.gamma[((size_t)((t0 + (u >> 1) - D) % D) * 2 + (u & 1)) * K + k];
 
     // ---- this thread's sample: target, coefficient, prediction at chunk start ---------------
-    float p = 0.f, gam = 0.f, b = 0.f;
-    const bool valid = u < R;
-    const int m = l0 + u, pa = m >> 1, l = m & 1;
+    float p = 0.f, gam = 0.f;
     if (valid) {
-        const float2 sy = a.sym[(size_t)pa * K + k];
-        b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
         if (m < s0) {
             p = a.carry[u * K + k];
             gam = a.gamma[((size_t)(pa % D) * 2 + l) * K + k];
+        } else if (a.track_in) {
+            p = a.track_in[(m - s0) * K + k];
         }
     }
     const float gam0 = gam;
@@ -190,7 +227,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     if (valid) {
         const float kjj = s_kmat[u * RS + u];
         rk = kjj != 0.f ? 1.f / kjj : 0.f;
-        if (m >= s0) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
+        if (m >= s0 && !a.track_in) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
             // each pilot starts at its own antenna so the lanes of a warp hit distinct banks
             const float2 *rv = s_pil + (pa - pa0) * M;
             float lin0 = 0.f, lin1 = 0.f;
@@ -205,11 +242,12 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
             p = a.wL * (lin0 + lin1);
         }
     }
-    // Everything above reads only what the previous chunk's phase B (complete before this kernel
-    // could launch, when the launch directly follows this chunk's phase A) and the kernel tables
-    // wrote; the phase-A partial sums below need phase A itself to have completed.
-    if (a.early) pdl_wait();
-    pdl_trigger();
+    // In mode 2 everything above reads only what the previous chunk's phase B (complete before
+    // this kernel could launch) and the kernel tables wrote; the phase-A sums need phase A itself.
+    if (a.pdl_mode == 2) {
+        pdl_wait();
+        pdl_trigger();
+    }
     if (valid && m >= s0) {
         // Gaussian part of f_{s0}(x_m) from the phase-A slices: 32 loads in flight at a time,
         // summed into eight partial sums (slice i into sum i mod 8) combined in a fixed order
@@ -224,6 +262,29 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
             for (int j = 0; j < 32; ++j) gs[j & 7] += v[j];
         }
         p = fmaf(a.wG, ((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])), p);
+    }
+
+    // ---- tracking of the next chunk's samples: starting value --------------------------------------
+    // At this chunk's start the entries of L hold gamma only at the carried samples (the new ones
+    // start at 0), so the tracked part of f_{s0} at a next-chunk sample x is
+    //   w_L <w, x> + w_G sum_{carried j} gamma_j kappa_G(x_j, x)
+    //     = w_L <w - sum_{carried j} gamma_j x_j, x> + sum_{carried j} gamma_j kappa(x_j, x),
+    // the second form using the tabulated sum kernel; the reduced filter is formed once here.
+    const int nc = s0 - l0;  // carried samples (rows 0 .. nc-1 of the tables)
+    const bool track = a.track_out != nullptr;
+    if (track) {
+        if (u < 32) s_gcar[u] = (valid && m < s0) ? gam : 0.f;
+        __syncthreads();
+        for (int mm = u; mm < M; mm += RS) {
+            float2 c = s_clin[mm];
+            for (int j = 0; j < nc; ++j) {
+                const float d = -s_gcar[j];
+                const float2 x = s_pil[(((l0 + j) >> 1) - pa0) * M + mm];
+                if ((l0 + j) & 1) { c.x = fmaf(d, x.y, c.x); c.y = fmaf(-d, x.x, c.y); }
+                else              { c.x = fmaf(d, x.x, c.x); c.y = fmaf(d, x.y, c.y); }
+            }
+            s_clinw[mm] = c;
+        }
     }
 
     // ---- the recurrence over the chunk's samples -----------------------------------------------
@@ -242,8 +303,8 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         // at once: the lanes publish their summed updates and all threads apply them.
         constexpr int B = 32 - WP;
         constexpr int NL = WP + B - 1;
-        float *s_p = s_beta, *s_g = s_p + RS, *s_b = s_g + RS, *s_rk = s_b + RS, *s_agg = s_rk + RS;
-        float *s_w = s_agg + 32, *s_muq = s_w + 64;
+        float *s_p = s_beta, *s_g = s_p + RS, *s_b = s_g + RS, *s_rk = s_b + RS, *s_agg = s_rk + RS;  // [2][32]
+        float *s_w = s_agg + 64, *s_muq = s_w + 64;
         if (valid) {
             s_p[u] = p;
             s_g[u] = gam;
@@ -254,8 +315,59 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         for (int i = u; i < 64; i += RS) s_w[i] = 0.f;
         __syncthreads();
         const int lane = u & 31;
-        for (int n0 = s0; n0 < s1; n0 += B) {
+        // Tracking threads (warps 1..S-1, idle while warp 0 runs a block) keep the next chunk's
+        // samples: starting value during the first block, then each block's summed coefficient
+        // changes (published by warp 0) applied during the following block, kernel values from
+        // the next-chunk table in global memory (off the recurrence's critical path).
+        const int n_next = track ? 2 * min(g.T, g.P - (t0 + Tc)) : 0;
+        const int tu = u - 32, ntr = RS - 32;
+        float tp[2] = {0.f, 0.f};
+        auto track_init = [&]() {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int v = tu + i * ntr;
+                if (v >= n_next) continue;
+                const int tv = t0 + Tc + (v >> 1), lvv = v & 1;
+                const float2 *rv = a.rx + (size_t)tv * M;
+                float l0s = 0.f, l1s = 0.f;
+                for (int mm = 0; mm < M; mm += 2) {
+                    const float4 x = __ldg(reinterpret_cast<const float4 *>(rv + mm));
+                    const float2 c = s_clinw[mm], cb = s_clinw[mm + 1];
+                    l0s = lvv ? fmaf(c.x, x.y, fmaf(-c.y, x.x, l0s)) : fmaf(c.x, x.x, fmaf(c.y, x.y, l0s));
+                    l1s = lvv ? fmaf(cb.x, x.w, fmaf(-cb.y, x.z, l1s)) : fmaf(cb.x, x.z, fmaf(cb.y, x.w, l1s));
+                }
+                // s_gcar is zero past the carried samples; rows clamped into the table
+                float acc4[4] = {a.wL * (l0s + l1s), 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    acc4[j & 3] = fmaf(s_gcar[j], __ldg(a.kx + (size_t)min(j, R - 1) * g.KXS + v), acc4[j & 3]);
+                tp[i] = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
+            }
+        };
+        auto track_apply = [&](const float *agg, int r0) {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int v = tu + i * ntr;
+                if (v >= n_next) continue;
+                // rows outside [0, R) belong to lanes whose summed change is zero: clamp, no branch,
+                // so that all NL loads are in flight together
+                float kv[NL];
+#pragma unroll
+                for (int j = 0; j < NL; ++j) kv[j] = __ldg(a.kx + (size_t)min(max(r0 + j, 0), R - 1) * g.KXS + v);
+                float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < NL; ++j) acc[j & 3] = fmaf(agg[j], kv[j], acc[j & 3]);
+                tp[i] += (acc[0] + acc[1]) + (acc[2] + acc[3]);
+            }
+        };
+        int blk = 0;
+        for (int n0 = s0; n0 < s1; n0 += B, ++blk) {
             const int wl0 = n0 - WP + 1;  // sample of lane 0
+            float *agg_cur = s_agg + (blk & 1) * 32;
+            if (S > 1 && track && u >= 32) {
+                if (blk == 0) track_init();
+                else track_apply(s_agg + ((blk - 1) & 1) * 32, wl0 - B - l0);
+            }
             if (u < 32) {
                 const int ms = wl0 + lane, lu = ms - l0;
                 const bool lv = lane < NL && ms >= l0 && ms < s1;
@@ -326,7 +438,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                     s_p[lu] = pl;
                     s_g[lu] += agg;
                 }
-                s_agg[lane] = lv ? agg : 0.f;
+                agg_cur[lane] = lv ? agg : 0.f;
             }
             __syncthreads();
             // the block's moves of every later sample, and its dropped entries
@@ -334,8 +446,8 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 const int r0 = wl0 - l0;
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int j = 0; j < NL; ++j)
-                    if (r0 + j < R) acc[j & 3] = fmaf(s_agg[j], kcol[(r0 + j) * RS], acc[j & 3]);
+                for (int j = 0; j < NL; ++j)  // rows past R: lanes with zero change (rows < 0: zero rows)
+                    acc[j & 3] = fmaf(agg_cur[j], kcol[min(r0 + j, R - 1) * RS], acc[j & 3]);
                 float pv = s_p[u] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
                 if (evict) {
                     for (int n = n0 + (n0 & 1); n < min(n0 + B, s1); n += 2) {
@@ -348,6 +460,15 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 s_p[u] = pv;
             }
             __syncthreads();
+        }
+        if (S > 1 && track && u >= 32) {  // the last block's changes, then hand over
+            if (blk == 0) track_init();
+            else track_apply(s_agg + ((blk - 1) & 1) * 32, s0 + (blk - 1) * B - WP + 1 - l0);
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int v = tu + i * ntr;
+                if (v < n_next) a.track_out[v * K + k] = tp[i];
+            }
         }
         if (valid) {
             p = s_p[u];
@@ -444,7 +565,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     if (valid) {
         a.gamma[((size_t)(pa % D) * 2 + l) * K + k] = gam;
         s_dg[u] = gam - gam0;
-        const int l0n = max(0, s1 - W + 1);
+        const int l0n = live_start(s1, W);
         if (m >= l0n) a.carry[(m - l0n) * K + k] = p;
     }
     __syncthreads();

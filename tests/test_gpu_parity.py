@@ -224,6 +224,7 @@ TRAIN_CASES = [
     (8, 16, 70, 16, 70, 0.5, 0.5, 0.01, 1.0, 100),      # linear-only kernel
     (8, 2, 70, 16, 70, 0.5, 0.5, 0.01, 0.0, 100),       # Gaussian-only kernel
     (64, 4, 60, 10, 60, 0.5, 0.5, 0.01, 0.5, 100),
+    (16, 6, 600, 16, 200, 0.5, 0.5, 0.01, 0.5, 300),    # many full chunks, eviction, ring wrap
 ]
 
 
@@ -233,6 +234,23 @@ def test_train_matches_oracle(M, K, P, W, D, sigma, mu, eps, wL, N):
     op = oracle.Params(M=M, K=K, W=W, D=D, sigma=sigma, mu=mu, eps=eps, w_L=wL)
     gp, st, cl, ref = _train_both(op, inst)
     _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
+
+
+@pytest.mark.parametrize("M,K,P,W,D", [(16, 6, 600, 16, 200), (8, 3, 333, 8, 1000), (4, 2, 100, 8, 20)])
+def test_tracked_and_sequential_training_agree(M, K, P, W, D, monkeypatch):
+    """The next-chunk tracking form (frozen-entry phase A beside phase B) and the sequential form
+    (whole-dictionary phase A between chunks) compute the same recurrence; both match the oracle."""
+    inst = synth.make_instance(M, K, P, 200, 10.0, instance=7 * P + D)
+    op = oracle.Params(M=M, K=K, W=W, D=D)
+    results = []
+    for track in ("1", "0"):
+        monkeypatch.setenv("APSM_TRAIN_TRACK", track)
+        gp, st, cl, ref = _train_both(op, inst)
+        _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
+        results.append((st.gamma.cpu().numpy(), st.clin.cpu().numpy()))
+    (g1, c1), (g0, c0) = results
+    assert np.abs(g1 - g0).max() <= 1e-4 * rms(g0)
+    assert np.abs(c1 - c0).max() <= 1e-4 * rms(np.abs(c0))
 
 
 def test_train_with_initial_linear_filter():
