@@ -180,6 +180,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         if (evict) bulk_g2s(s_gev, a.gev + (size_t)a.chunk * g.T * 2 * RS, gb, bar);
         bulk_g2s(s_pil, a.rx + (size_t)pa0 * M, pb, bar);
     }
+    __syncthreads();  // the barrier's initialisation is visible before any thread waits on it
     const bool valid = u < R;
     const int m = l0 + u, pa = m >> 1, l = m & 1;
     float b = 0.f;
@@ -187,7 +188,22 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         const float2 sy = a.sym[(size_t)pa * K + k];
         b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
     }
-    if (a.pdl_mode == 1) {
+    for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
+    for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
+    float rk = 0.f;  // 1 / kappa(x_j, x_j)
+    auto tables_ready = [&]() {
+        if (!mbar_wait_bounded(bar, 0)) {
+            if (u == 0) report(a.meta + 3, APSM_ERR_TIMEOUT);
+            return false;
+        }
+        if (valid) {
+            const float kjj = s_kmat[u * RS + u];
+            rk = kjj != 0.f ? 1.f / kjj : 0.f;
+        }
+        return true;
+    };
+    if (a.pdl_mode == 1) {  // the staged tables do not depend on the previous chunk
+        if (!tables_ready()) return;
         pdl_wait();
         pdl_trigger();
     }
@@ -216,31 +232,24 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     for (int i = 0; i < 2; ++i)
         if (u + i * RS < M) s_clin[u + i * RS] = clin_r[i];
     if (evict && u < 2 * Tc) s_egam[u] = egam_r;
-    for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
-    for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
+    // carried gamma at the chunk start (zero past the carried samples), for the tracking threads
+    const bool track = a.track_out != nullptr;  // (the region exists only in the tracked form)
+    if (track && u < 32) s_gcar[u] = (valid && m < s0) ? gam : 0.f;
     __syncthreads();
-    if (!mbar_wait_bounded(bar, 0)) {
-        if (u == 0) report(a.meta + 3, APSM_ERR_TIMEOUT);
-        return;
-    }
-    float rk = 0.f;  // 1 / kappa(x_j, x_j)
-    if (valid) {
-        const float kjj = s_kmat[u * RS + u];
-        rk = kjj != 0.f ? 1.f / kjj : 0.f;
-        if (m >= s0 && !a.track_in) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
-            // each pilot starts at its own antenna so the lanes of a warp hit distinct banks
-            const float2 *rv = s_pil + (pa - pa0) * M;
-            float lin0 = 0.f, lin1 = 0.f;
-            int mm = pa % M;
-            for (int i = 0; i < M; i += 2) {
-                const int mb = mm + 1 == M ? 0 : mm + 1;
-                const float2 c = s_clin[mm], x = rv[mm], cb = s_clin[mb], xb = rv[mb];
-                lin0 = l ? fmaf(c.x, x.y, fmaf(-c.y, x.x, lin0)) : fmaf(c.x, x.x, fmaf(c.y, x.y, lin0));
-                lin1 = l ? fmaf(cb.x, xb.y, fmaf(-cb.y, xb.x, lin1)) : fmaf(cb.x, xb.x, fmaf(cb.y, xb.y, lin1));
-                mm = mb + 1 == M ? 0 : mb + 1;
-            }
-            p = a.wL * (lin0 + lin1);
+    if (a.pdl_mode != 1 && !tables_ready()) return;
+    if (valid && m >= s0 && !a.track_in) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
+        // each pilot starts at its own antenna so the lanes of a warp hit distinct banks
+        const float2 *rv = s_pil + (pa - pa0) * M;
+        float lin0 = 0.f, lin1 = 0.f;
+        int mm = pa % M;
+        for (int i = 0; i < M; i += 2) {
+            const int mb = mm + 1 == M ? 0 : mm + 1;
+            const float2 c = s_clin[mm], x = rv[mm], cb = s_clin[mb], xb = rv[mb];
+            lin0 = l ? fmaf(c.x, x.y, fmaf(-c.y, x.x, lin0)) : fmaf(c.x, x.x, fmaf(c.y, x.y, lin0));
+            lin1 = l ? fmaf(cb.x, xb.y, fmaf(-cb.y, xb.x, lin1)) : fmaf(cb.x, xb.x, fmaf(cb.y, xb.y, lin1));
+            mm = mb + 1 == M ? 0 : mb + 1;
         }
+        p = a.wL * (lin0 + lin1);
     }
     // In mode 2 everything above reads only what the previous chunk's phase B (complete before
     // this kernel could launch) and the kernel tables wrote; the phase-A sums need phase A itself.
@@ -263,35 +272,20 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         }
         p = fmaf(a.wG, ((gs[0] + gs[1]) + (gs[2] + gs[3])) + ((gs[4] + gs[5]) + (gs[6] + gs[7])), p);
     }
-
-    // ---- tracking of the next chunk's samples: starting value --------------------------------------
-    // At this chunk's start the entries of L hold gamma only at the carried samples (the new ones
-    // start at 0), so the tracked part of f_{s0} at a next-chunk sample x is
-    //   w_L <w, x> + w_G sum_{carried j} gamma_j kappa_G(x_j, x)
-    //     = w_L <w - sum_{carried j} gamma_j x_j, x> + sum_{carried j} gamma_j kappa(x_j, x),
-    // the second form using the tabulated sum kernel; the reduced filter is formed once here.
     const int nc = s0 - l0;  // carried samples (rows 0 .. nc-1 of the tables)
-    const bool track = a.track_out != nullptr;
-    if (track) {
-        if (u < 32) s_gcar[u] = (valid && m < s0) ? gam : 0.f;
-        __syncthreads();
-        for (int mm = u; mm < M; mm += RS) {
-            float2 c = s_clin[mm];
-            for (int j = 0; j < nc; ++j) {
-                const float d = -s_gcar[j];
-                const float2 x = s_pil[(((l0 + j) >> 1) - pa0) * M + mm];
-                if ((l0 + j) & 1) { c.x = fmaf(d, x.y, c.x); c.y = fmaf(-d, x.x, c.y); }
-                else              { c.x = fmaf(d, x.x, c.x); c.y = fmaf(d, x.y, c.y); }
-            }
-            s_clinw[mm] = c;
-        }
-    }
 
     // ---- the recurrence over the chunk's samples -----------------------------------------------
+    // Blocked form with more than one warp: the idle warps also accumulate the filter change
+    // c_k += sum_j dgamma_j x~_j block by block (thread = antenna x part of the block's lanes).
+    constexpr bool kBlocked = WP + kBlockMin - 1 <= 32;
+    constexpr bool kDcInRegs = kBlocked && S > 1;
+    const int ntr = RS - 32, tu = u - 32;
+    const int dc_parts = max(1, ntr / M);
+    float dcx[2] = {0.f, 0.f}, dcy[2] = {0.f, 0.f};
     const bool log_cases = a.case_log != nullptr;
     const float muq_full = a.mu / (float)W;  // mu q with q = 1/W once the window is full
     const float *kcol = s_kmat + u;          // column u of the kernel table
-    if constexpr (WP + kBlockMin - 1 <= 32) {
+    if constexpr (kBlocked) {
         // Blocked form.  Over a block of B = 32 - WP steps from n0, every sample that is in a
         // window of the block lies in [n0 - WP + 1, n0 + B - 1]: 31 samples, one per lane of warp 0.
         // That warp runs the B steps alone: the window lanes compute mu q beta (Eq. beta, written
@@ -320,9 +314,43 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         // changes (published by warp 0) applied during the following block, kernel values from
         // the next-chunk table in global memory (off the recurrence's critical path).
         const int n_next = track ? 2 * min(g.T, g.P - (t0 + Tc)) : 0;
-        const int tu = u - 32, ntr = RS - 32;
         float tp[2] = {0.f, 0.f};
+        // x~ = r(t) for r1(t) and -i r(t) for r2(t); lanes outside L carry a zero change
+        auto dc_apply = [&](const float *agg, int wl0b) {
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int idx = tu + it * ntr;
+                if (idx >= dc_parts * M) continue;
+                const int mm = idx % M, part = idx / M;
+                const int j0 = part * NL / dc_parts, j1 = (part + 1) * NL / dc_parts;
+                for (int j = j0; j < j1; ++j) {
+                    const float d = agg[j];
+                    const int ms = wl0b + j;
+                    const int pi = min(max((ms >> 1) - pa0, 0), npil - 1);
+                    const float2 x = s_pil[pi * M + mm];
+                    if (ms & 1) { dcx[it] = fmaf(d, x.y, dcx[it]); dcy[it] = fmaf(-d, x.x, dcy[it]); }
+                    else        { dcx[it] = fmaf(d, x.x, dcx[it]); dcy[it] = fmaf(d, x.y, dcy[it]); }
+                }
+            }
+        };
+        // At this chunk's start the entries of L hold gamma only at the carried samples (the new
+        // ones start at 0), so the tracked part of f_{s0} at a next-chunk sample x is
+        //   w_L <w, x> + w_G sum_{carried j} gamma_j kappa_G(x_j, x)
+        //     = w_L <w - sum_{carried j} gamma_j x_j, x> + sum_{carried j} gamma_j kappa(x_j, x),
+        // the second form using the tabulated sum kernel; the tracking threads form the reduced
+        // filter, meet at a named barrier of their own, then evaluate their samples.
         auto track_init = [&]() {
+            for (int mm = tu; mm < M; mm += ntr) {
+                float2 c = s_clin[mm];
+                for (int j = 0; j < nc; ++j) {
+                    const float d = -s_gcar[j];
+                    const float2 x = s_pil[(((l0 + j) >> 1) - pa0) * M + mm];
+                    if ((l0 + j) & 1) { c.x = fmaf(d, x.y, c.x); c.y = fmaf(-d, x.x, c.y); }
+                    else              { c.x = fmaf(d, x.x, c.x); c.y = fmaf(d, x.y, c.y); }
+                }
+                s_clinw[mm] = c;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(ntr) : "memory");
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int v = tu + i * ntr;
@@ -364,6 +392,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         for (int n0 = s0; n0 < s1; n0 += B, ++blk) {
             const int wl0 = n0 - WP + 1;  // sample of lane 0
             float *agg_cur = s_agg + (blk & 1) * 32;
+            if (S > 1 && u >= 32 && blk > 0) dc_apply(s_agg + ((blk - 1) & 1) * 32, wl0 - B);
             if (S > 1 && track && u >= 32) {
                 if (blk == 0) track_init();
                 else track_apply(s_agg + ((blk - 1) & 1) * 32, wl0 - B - l0);
@@ -382,8 +411,9 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 float kc[NL];  // kappa(x_{wl0+j}, x of this lane)
 #pragma unroll
                 for (int j = 0; j < NL; ++j) {
-                    const int row = wl0 + j - l0;  // >= -WP + 1: the zero rows
-                    kc[j] = row < R ? s_kmat[row * RS + col] : 0.f;
+                    // rows >= -WP + 1 (the zero rows); rows past R belong to invalid lanes, whose
+                    // beta is 0: clamp instead of branching so that the loads issue together
+                    kc[j] = s_kmat[min(wl0 + j - l0, R - 1) * RS + col];
                 }
                 // kChecked: a partial last block, the filling window (n < W - 1) or case logging
                 auto steps = [&](auto checked_c, auto evict_c) {
@@ -461,6 +491,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
             }
             __syncthreads();
         }
+        if (S > 1 && u >= 32 && blk > 0) dc_apply(s_agg + ((blk - 1) & 1) * 32, s0 + (blk - 1) * B - WP + 1);
         if (S > 1 && track && u >= 32) {  // the last block's changes, then hand over
             if (blk == 0) track_init();
             else track_apply(s_agg + ((blk - 1) & 1) * 32, s0 + (blk - 1) * B - WP + 1 - l0);
@@ -572,9 +603,16 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     // c_k += sum_u dgamma_u x~_u, with x~ = r(t) for r1(t) and -i r(t) for r2(t): the live range
     // is split into np parts per antenna, partial sums combined in a fixed order
     {
-        const int np = max(1, min(RS / M, 16));
+        const int np = kDcInRegs ? dc_parts : max(1, min(RS / M, 16));
         float2 *s_part = reinterpret_cast<float2 *>(s_beta);  // free after the recurrence
-        for (int tid = u; tid < np * M; tid += RS) {
+        if (kDcInRegs && u >= 32) {
+#pragma unroll
+            for (int it = 0; it < 2; ++it) {
+                const int idx = tu + it * ntr;
+                if (idx < dc_parts * M) s_part[(idx / M) * M + idx % M] = make_float2(dcx[it], dcy[it]);
+            }
+        }
+        for (int tid = u; !kDcInRegs && tid < np * M; tid += RS) {
             const int mm = tid % M, part = tid / M;
             const int v0 = R * part / np, v1 = R * (part + 1) / np;
             float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
