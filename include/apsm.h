@@ -155,7 +155,7 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
  *     training writes every scratch word before reading it).  Calls whose GPU work overlaps --
  *     on different streams, or from different threads -- race on it: serialise them.
  */
-#define APSM_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define APSM_NOALLOC_SCRATCH_BYTES (8u << 20)
 apsm_status apsm_train_noalloc(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
                                const float *clin0, const apsm_state *st, int8_t *case_log, void *stream);
 
