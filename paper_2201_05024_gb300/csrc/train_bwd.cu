@@ -18,7 +18,9 @@
 // Checkpointing: a first forward pass stores (w, every gamma) at the start of every segment of
 // 32 pilots (64 steps); the reverse sweep restores each segment, re-runs its forward recording a
 // per-step tape (beta, branch, kappa, <w, x_j>, gauss_j, its sigma weight), then walks it back.
-// Kernel values between samples come from tables built once per call.  One warp per user.
+// Kernel values between samples come from tables built once per call.  One CTA of 8 warps per
+// user: a warp per window slot for the inner products, a thread per centre for the state
+// adjoint's update, a thread per slot for the scalar terms (summed in slot order at the end).
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -82,45 +84,58 @@ struct Tape {  // one window slot of one step
     float beta, s, kappa, dotw, gauss, gd2;
 };
 
-// smem: gamma [2P], gbar [2P], w [2M], wbar [2M], abar [W], tape [kBwdSeg][W]
-__global__ void __launch_bounds__(32) train_bwd_kernel(const TrainBwdArgs a) {
+constexpr int kBwdThreads = 256;  // 8 warps per user: one window slot per warp
+
+// smem: gamma [2P], gbar [2P], norms [2P], w [2M], wbar [2M], abar [W], cw [W], cg [W],
+//       tape [kBwdSeg][W]
+__global__ void __launch_bounds__(kBwdThreads) train_bwd_kernel(const TrainBwdArgs a) {
     extern __shared__ __align__(16) float sm[];
-    const int k = blockIdx.x, lane = threadIdx.x;
+    const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kBwdThreads / 32;
     const int M = a.M, K = a.K, W = a.W, D = a.D, P = a.P, S = 2 * P, L2 = 2 * M;
-    float *gam = sm, *gbar = gam + S, *w = gbar + S, *wbar = w + L2, *abar = wbar + L2;
-    Tape *tape = reinterpret_cast<Tape *>(abar + W);
+    float *gam = sm, *gbar = gam + S, *nrm = gbar + S, *w = nrm + S, *wbar = w + L2, *abar = wbar + L2;
+    float *cw = abar + W, *cg = cw + W;
+    Tape *tape = reinterpret_cast<Tape *>(cg + W);
     const float inv_s3 = 1.f / (a.sigma * a.sigma * a.sigma);
 
     auto target = [&](int j) {
         const float2 b = __ldg(a.sym + (size_t)(j >> 1) * K + k);
         return (j & 1) ? b.y : b.x;
     };
-    auto norm2 = [&](int j) { return a.ltab[(size_t)j * S + j]; };  // ||x_j||^2
     auto first_centre = [&](int n) { return 2 * max(0, (n >> 1) - D + 1); };
+    for (int i = tid; i < S; i += kBwdThreads) nrm[i] = a.ltab[(size_t)i * S + i];  // ||x_i||^2
 
-    // ---- forward over one segment; record the tape when asked ------------------------------------
+    // ---- forward over one segment (warp o takes window slots o, o + 8, ...); records the tape --
     auto forward = [&](int n0, int n1) {
         for (int n = n0; n < n1; ++n) {
             const int c_lo = first_centre(n), c_hi = 2 * (n >> 1) + 2;
             const int jlo = max(0, n - W + 1), nJ = n - jlo + 1;
-            const float q = 1.f / (float)nJ;
-            // all projections of the step from the same f_n (Eq. apsm): compute, then apply
-            for (int o = 0; o < nJ; ++o) {
+            for (int o = warp; o < nJ; o += NW) {
                 const int j = jlo + o;
                 float dw = 0.f;
                 for (int m = lane; m < L2; m += 32) dw = fmaf(w[m], xcomp(a.rx, M, j, m), dw);
-                dw = warp_sum(dw);
-                float gs = 0.f, gd = 0.f;
-                const float nj = norm2(j);
-                for (int i = c_lo + lane; i < c_hi; i += 32) {
-                    const float g = a.gtab[(size_t)j * S + i], gi = gam[i];
-                    const float d2 = fmaxf(norm2(i) + nj - 2.f * a.ltab[(size_t)j * S + i], 0.f);
-                    gs = fmaf(gi, g, gs);
-                    gd = fmaf(gi * g, d2, gd);
+                const float nj = nrm[j];
+                const float *grow = a.gtab + (size_t)j * S, *lrow = a.ltab + (size_t)j * S;
+                float gs[4] = {0.f, 0.f, 0.f, 0.f}, gd[4] = {0.f, 0.f, 0.f, 0.f};
+                int i = c_lo + lane;
+                for (; i + 96 < c_hi; i += 128) {  // four centres per lane in flight
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int ii = i + 32 * q;
+                        const float g = __ldg(grow + ii), lt = __ldg(lrow + ii), gi = gam[ii];
+                        gs[q] = fmaf(gi, g, gs[q]);
+                        gd[q] = fmaf(gi * g, fmaxf(nrm[ii] + nj - 2.f * lt, 0.f), gd[q]);
+                    }
                 }
-                gs = warp_sum(gs);
-                gd = warp_sum(gd);
-                const float y = fmaf(a.wL, dw, a.wG * gs);
+                for (; i < c_hi; i += 32) {
+                    const float g = __ldg(grow + i), lt = __ldg(lrow + i), gi = gam[i];
+                    gs[0] = fmaf(gi, g, gs[0]);
+                    gd[0] = fmaf(gi * g, fmaxf(nrm[i] + nj - 2.f * lt, 0.f), gd[0]);
+                }
+                dw = warp_sum(dw);
+                const float gsum = warp_sum((gs[0] + gs[1]) + (gs[2] + gs[3]));
+                const float gdsum = warp_sum((gd[0] + gd[1]) + (gd[2] + gd[3]));
+                const float y = fmaf(a.wL, dw, a.wG * gsum);
                 const float e = y - target(j);
                 const float kap = fmaf(a.wL, nj, a.wG);
                 float beta = 0.f, s = 0.f;
@@ -128,98 +143,123 @@ __global__ void __launch_bounds__(32) train_bwd_kernel(const TrainBwdArgs a) {
                     if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
                     else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
                 }
-                if (lane == 0) tape[(n - n0) * W + o] = Tape{beta, s, kap, dw, gs, gd};
+                if (lane == 0) tape[(n - n0) * W + o] = Tape{beta, s, kap, dw, gsum, gdsum};
             }
-            __syncwarp();
-            for (int o = 0; o < nJ; ++o) {
-                const int j = jlo + o;
-                const float amt = a.mu * q * tape[(n - n0) * W + o].beta;
-                if (lane == 0) gam[j] += amt;
-                for (int m = lane; m < L2; m += 32) w[m] = fmaf(amt, xcomp(a.rx, M, j, m), w[m]);
-                __syncwarp();
+            __syncthreads();
+            // all projections of the step from the same f_n (Eq. apsm), then applied together
+            const float mq = a.mu / (float)nJ;
+            if (tid < nJ) gam[jlo + tid] += mq * tape[(n - n0) * W + tid].beta;
+            for (int m = tid; m < L2; m += kBwdThreads) {
+                float acc = w[m];
+                for (int o = 0; o < nJ; ++o) acc = fmaf(mq * tape[(n - n0) * W + o].beta, xcomp(a.rx, M, jlo + o, m), acc);
+                w[m] = acc;
             }
+            __syncthreads();
         }
     };
 
     // ---- pass 1: forward, checkpoint at every segment start ------------------------------------------
-    for (int i = lane; i < S; i += 32) gam[i] = 0.f;
-    for (int m = lane; m < M; m += 32) {
+    for (int i = tid; i < S; i += kBwdThreads) gam[i] = 0.f;
+    for (int m = tid; m < M; m += kBwdThreads) {
         const float2 c = a.clin0 ? a.clin0[m * K + k] : make_float2(0.f, 0.f);
         w[m] = c.x;      // w = [Re c; Im c]
         w[M + m] = c.y;
     }
-    __syncwarp();
+    __syncthreads();
     float *ck = a.ckpt + (size_t)k * a.n_seg * (L2 + S);
     for (int sg = 0; sg < a.n_seg; ++sg) {
         float *dst = ck + (size_t)sg * (L2 + S);
-        for (int m = lane; m < L2; m += 32) dst[m] = w[m];
-        for (int i = lane; i < S; i += 32) dst[L2 + i] = gam[i];
-        __syncwarp();
+        for (int m = tid; m < L2; m += kBwdThreads) dst[m] = w[m];
+        for (int i = tid; i < S; i += kBwdThreads) dst[L2 + i] = gam[i];
         forward(sg * kBwdSeg, min(S, (sg + 1) * kBwdSeg));
     }
 
     // ---- initial adjoint: the final coefficients and linear filter --------------------------------
-    for (int i = lane; i < S; i += 32) {
+    for (int i = tid; i < S; i += kBwdThreads) {
         const int t = i >> 1;
         const bool alive = P > 0 && t >= max(0, P - D);
         gbar[i] = alive ? a.dgamma[((size_t)(t % D) * 2 + (i & 1)) * K + k] : 0.f;
     }
-    for (int m = lane; m < M; m += 32) {
+    for (int m = tid; m < M; m += kBwdThreads) {
         const float2 d = a.dclin[m * K + k];
         wbar[m] = d.x;
         wbar[M + m] = d.y;
     }
-    __syncwarp();
-    float sig_bar = 0.f, mu_bar = 0.f, eps_bar = 0.f, wl_bar = 0.f;  // lane 0 holds the sums
+    __syncthreads();
+    // scalar adjoints: thread o sums the terms of window slot o over all steps (fixed order)
+    float sig_bar = 0.f, mu_bar = 0.f, eps_bar = 0.f, wl_bar = 0.f;
 
     // ---- reverse sweep, one segment at a time -------------------------------------------------------
     for (int sg = a.n_seg - 1; sg >= 0; --sg) {
         const int n0 = sg * kBwdSeg, n1 = min(S, (sg + 1) * kBwdSeg);
         const float *src = ck + (size_t)sg * (L2 + S);
-        for (int m = lane; m < L2; m += 32) w[m] = src[m];
-        for (int i = lane; i < S; i += 32) gam[i] = src[L2 + i];
-        __syncwarp();
+        for (int m = tid; m < L2; m += kBwdThreads) w[m] = src[m];
+        for (int i = tid; i < S; i += kBwdThreads) gam[i] = src[L2 + i];
+        __syncthreads();
         forward(n0, n1);
         for (int n = n1 - 1; n >= n0; --n) {
             const int c_lo = first_centre(n), c_hi = 2 * (n >> 1) + 2;
             const int jlo = max(0, n - W + 1), nJ = n - jlo + 1;
             const float q = 1.f / (float)nJ;
             // abar_j from the adjoint of S_{n+1}, for every j, before any update
-            for (int o = 0; o < nJ; ++o) {
+            for (int o = warp; o < nJ; o += NW) {
                 const int j = jlo + o;
                 float d = 0.f;
                 for (int m = lane; m < L2; m += 32) d = fmaf(wbar[m], xcomp(a.rx, M, j, m), d);
                 d = warp_sum(d) + gbar[j];
                 if (lane == 0) abar[o] = d;
             }
-            __syncwarp();
-            for (int o = 0; o < nJ; ++o) {
-                const int j = jlo + o;
+            __syncthreads();
+            if (tid < nJ) {  // slot tid: its scalar terms and its coefficients for the state adjoint
+                const int o = tid, j = jlo + o;
                 const float ab = abar[o];
                 const Tape tp = tape[(n - n0) * W + o];
                 mu_bar += q * tp.beta * ab;
                 const float bbar = a.mu * q * ab;
-                if (tp.s == 0.f) continue;  // inside the slab: beta does not depend on the state
-                const float ybar = -bbar / tp.kappa;
-                eps_bar += -tp.s * bbar / tp.kappa;
-                wl_bar += (-bbar * tp.beta / tp.kappa) * (norm2(j) - 1.f);
-                wl_bar += ybar * (tp.dotw - tp.gauss);
-                sig_bar += ybar * a.wG * tp.gd2 * inv_s3;
-                const float cw = ybar * a.wL, cg = ybar * a.wG;
-                for (int m = lane; m < L2; m += 32) wbar[m] = fmaf(cw, xcomp(a.rx, M, j, m), wbar[m]);
-                for (int i = c_lo + lane; i < c_hi; i += 32) gbar[i] = fmaf(cg, a.gtab[(size_t)j * S + i], gbar[i]);
+                float cwo = 0.f, cgo = 0.f;
+                if (tp.s != 0.f) {  // inside the slab beta does not depend on the state
+                    const float ybar = -bbar / tp.kappa;
+                    eps_bar += -tp.s * bbar / tp.kappa;
+                    wl_bar += (-bbar * tp.beta / tp.kappa) * (nrm[j] - 1.f);
+                    wl_bar += ybar * (tp.dotw - tp.gauss);
+                    sig_bar += ybar * a.wG * tp.gd2 * inv_s3;
+                    cwo = ybar * a.wL;
+                    cgo = ybar * a.wG;
+                }
+                cw[o] = cwo;
+                cg[o] = cgo;
             }
-            __syncwarp();
+            __syncthreads();
+            for (int m = tid; m < L2; m += kBwdThreads) {
+                float acc = wbar[m];
+                for (int o = 0; o < nJ; ++o) acc = fmaf(cw[o], xcomp(a.rx, M, jlo + o, m), acc);
+                wbar[m] = acc;
+            }
+            for (int i = c_lo + tid; i < c_hi; i += kBwdThreads) {
+                float acc = gbar[i];
+                for (int o = 0; o < nJ; ++o) acc = fmaf(cg[o], __ldg(a.gtab + (size_t)(jlo + o) * S + i), acc);
+                gbar[i] = acc;
+            }
+            __syncthreads();
         }
     }
 
     // ---- results -------------------------------------------------------------------------------------
-    for (int m = lane; m < M; m += 32) a.dclin0[m * K + k] = make_float2(wbar[m], wbar[M + m]);
-    if (lane == 0) {
-        a.scal[k * 4 + 0] = sig_bar;
-        a.scal[k * 4 + 1] = mu_bar;
-        a.scal[k * 4 + 2] = eps_bar;
-        a.scal[k * 4 + 3] = wl_bar;
+    for (int m = tid; m < M; m += kBwdThreads) a.dclin0[m * K + k] = make_float2(wbar[m], wbar[M + m]);
+    // per-slot partial sums, combined in slot order
+    __syncthreads();
+    float *red = reinterpret_cast<float *>(tape);  // free now (kBwdSeg * W tapes >= 4 W floats)
+    if (tid < W) {
+        red[4 * tid + 0] = sig_bar;
+        red[4 * tid + 1] = mu_bar;
+        red[4 * tid + 2] = eps_bar;
+        red[4 * tid + 3] = wl_bar;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        float s = 0.f;
+        for (int o = 0; o < W; ++o) s += red[4 * o + tid];
+        a.scal[k * 4 + tid] = s;
     }
 }
 
@@ -232,7 +272,7 @@ __global__ void train_bwd_sum_kernel(const TrainBwdArgs a) {
 }
 
 size_t train_bwd_smem(int M, int W, int P) {
-    return sizeof(float) * (size_t)(2 * 2 * P + 2 * 2 * M + W) + sizeof(Tape) * (size_t)kBwdSeg * W;
+    return sizeof(float) * (size_t)(3 * 2 * P + 2 * 2 * M + 3 * W) + sizeof(Tape) * (size_t)kBwdSeg * W;
 }
 
 }  // namespace apsm
@@ -330,7 +370,7 @@ apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, con
     train_bwd_tables_kernel<<<blocks, 256, 0, strm>>>(a);
     if (cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return APSM_ERR_CUDA;
-    train_bwd_kernel<<<p->K, 32, smem, strm>>>(a);
+    train_bwd_kernel<<<p->K, kBwdThreads, smem, strm>>>(a);
     train_bwd_sum_kernel<<<1, 32, 0, strm>>>(a);
     g_launches += 3;
     return cudaGetLastError() == cudaSuccess ? APSM_OK : APSM_ERR_CUDA;
