@@ -240,14 +240,14 @@ BwdGeom bwd_geom(const apsm_params *p, int N) {
     b.n_qslices = N > 0 ? std::min(want, (N + kBwdQueryTile - 1) / kBwdQueryTile) : 0;
     b.q_per_slice = b.n_qslices ? round_up((N + b.n_qslices - 1) / b.n_qslices, kBwdQueryTile) : 0;
     if (b.q_per_slice) b.n_qslices = (N + b.q_per_slice - 1) / b.q_per_slice;
-    b.n_cslices = N > 0 ? std::min(256, (N + 255) / 256) : 0;
+    b.n_cslices = N > 0 ? std::min(256, (N + 127) / 128) : 0;
     size_t off = 0;
     b.gh = off;
     off = align256(off + sizeof(float) * (size_t)b.n_qslices * b.A * 4 * p->K);
     b.cpart = off;
     off = align256(off + sizeof(float) * 2 * (size_t)b.n_cslices * p->M * p->K);
     b.scal = off;
-    off = align256(off + sizeof(float) * 2 * (size_t)b.A);
+    off = align256(off + sizeof(float) * 2 * (size_t)b.A * 2 * p->K);
     b.total = off;
     return b;
 }

@@ -19,8 +19,8 @@
 //                             shared memory; writes per-slice sums G (coefficient gradient) and
 //                             H (sigma weights) -- no atomics.
 //   detect_bwd_clin_kernel    per query slice, sum_s conj(dy) r for every (m, k).
-//   detect_bwd_finalize_kernel  fixed-order sums over slices per entry -> dgamma and per-entry
-//                             scalar terms.
+//   detect_bwd_finalize_kernel  one thread per (entry, coefficient): fixed-order sums over the
+//                             slices -> dgamma and its scalar terms.
 //   detect_bwd_scalars_kernel one CTA: fixed-order sums -> dclin, dsigma, dw_L.
 #pragma once
 
@@ -48,7 +48,7 @@ struct DetectBwdArgs {
     float k2, wL, wG, sigma;
     float *gh;                // workspace [n_qslices][A][4K]: G1, G2, H1, H2
     float2 *cpart;            // workspace [n_cslices][M][K]
-    float *scal;              // workspace [A][2]: per-entry sigma and Gaussian terms
+    float *scal;              // workspace [A][2K][2]: per-coefficient sigma and Gaussian terms
     float *dgamma;            // out [A][2][K]
     float2 *dclin;            // out [M][K]
     float *dscalars;          // out [2]: dL/dsigma, dL/dw_L
@@ -132,6 +132,7 @@ __global__ void detect_bwd_clin_kernel(const DetectBwdArgs a) {
     const int per = (a.N + a.n_cslices - 1) / a.n_cslices;
     const int q0 = blockIdx.x * per, q1 = min(a.N, q0 + per);
     float re = 0.f, im = 0.f;
+#pragma unroll 8
     for (int s = q0; s < q1; ++s) {
         const float2 r = __ldg(a.rx + (size_t)s * M + m), g = __ldg(a.dsoft + (size_t)s * K + k);
         re = fmaf(g.x, r.x, fmaf(g.y, r.y, re));   // Re(conj(g) r)
@@ -142,25 +143,33 @@ __global__ void detect_bwd_clin_kernel(const DetectBwdArgs a) {
 
 template <int K>
 __global__ void detect_bwd_finalize_kernel(const DetectBwdArgs a) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.A) return;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.A * 2 * K) return;
+    const int t = idx / (2 * K), j = idx % (2 * K);
     const int n_ent = min(a.n_entries, max(__ldg(a.meta), 0));
-    float sig = 0.f, gau = 0.f;
-    for (int j = 0; j < 2 * K; ++j) {
-        float G = 0.f, H = 0.f;
-        if (t < n_ent)
-            for (int sl = 0; sl < a.n_qslices; ++sl) {
-                const float *src = a.gh + ((size_t)sl * a.A + t) * 4 * K;
-                G += src[j];
-                H += src[2 * K + j];
+    float G = 0.f, H = 0.f;
+    if (t < n_ent) {
+        const float *src = a.gh + (size_t)t * 4 * K + j;
+        const size_t stride = (size_t)a.A * 4 * K;
+        for (int sl0 = 0; sl0 < a.n_qslices; sl0 += 8) {  // eight slices' loads in flight, summed in order
+            float g[8], h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const bool in = sl0 + q < a.n_qslices;
+                g[q] = in ? src[(sl0 + q) * stride] : 0.f;
+                h[q] = in ? src[(sl0 + q) * stride + 2 * K] : 0.f;
             }
-        const float g = t < n_ent ? a.gamma[(size_t)t * 2 * K + j] : 0.f;
-        a.dgamma[(size_t)t * 2 * K + j] = a.wG * G;
-        sig = fmaf(g, H, sig);
-        gau = fmaf(g, G, gau);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                G += g[q];
+                H += h[q];
+            }
+        }
     }
-    a.scal[2 * t] = sig;
-    a.scal[2 * t + 1] = gau;
+    const float g = t < n_ent ? a.gamma[(size_t)t * 2 * K + j] : 0.f;
+    a.dgamma[(size_t)t * 2 * K + j] = a.wG * G;
+    a.scal[2 * (size_t)idx] = g * H;
+    a.scal[2 * (size_t)idx + 1] = g * G;
 }
 
 // One CTA of 256 threads: fixed-order reductions for dclin, dsigma, dw_L.
@@ -168,7 +177,7 @@ template <int M, int K>
 __global__ void __launch_bounds__(256) detect_bwd_scalars_kernel(const DetectBwdArgs a) {
     __shared__ float s_sig[256], s_gau[256], s_lin[256];
     float sig = 0.f, gau = 0.f, lin = 0.f;
-    for (int t = threadIdx.x; t < a.A; t += blockDim.x) {
+    for (int t = threadIdx.x; t < a.A * 2 * K; t += blockDim.x) {
         sig += a.scal[2 * t];
         gau += a.scal[2 * t + 1];
     }
@@ -209,7 +218,7 @@ cudaError_t launch_detect_bwd(const DetectBwdArgs &a, cudaStream_t stream) {
         detect_bwd_entry_kernel<M, K><<<grid, kBwdEntriesPerCta, 0, stream>>>(a);
         detect_bwd_clin_kernel<M, K><<<a.n_cslices, round_up(M * K, 32), 0, stream>>>(a);
     }
-    detect_bwd_finalize_kernel<K><<<(a.A + 127) / 128, 128, 0, stream>>>(a);
+    detect_bwd_finalize_kernel<K><<<(a.A * 2 * K + 127) / 128, 128, 0, stream>>>(a);
     detect_bwd_scalars_kernel<M, K><<<1, 256, 0, stream>>>(a);
     return cudaGetLastError();
 }
