@@ -140,6 +140,21 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_max(dist, values, device):
+    """Max over ranks of each value: the slowest rank sets the job's time (one rank: unchanged)."""
+    if dist is None:
+        return list(values)
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(world, units_per_rank, ms_per_step):
+    """Whole-job throughput: every rank processes its own units in the (max-over-ranks) step time."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 def run_oracle(w, inst, sample, threads=None):
     """Time the FP64 oracle: full training, detection of `sample` queries."""
     import oracle
@@ -486,12 +501,9 @@ def main():
     t_step = sum(t_train) + sum(t_detect)  # ms over K steps
     mean_train = sum(t_train) / len(t_train)
     mean_detect = sum(t_detect) / len(t_detect)
-    if dist is not None:
-        t = torch.tensor([t_step, mean_train, mean_detect], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step, mean_train, mean_detect = t.tolist()
+    t_step, mean_train, mean_detect = reduce_max(dist, [t_step, mean_train, mean_detect], dev)
     ms_per_step = t_step / args.steps
-    value = world * w["N"] / (ms_per_step / 1e3)
+    value = job_rate(world, w["N"], ms_per_step)
     assert apsm.read_status(st) == 0, "device status word set during the benchmark"
 
     # ---- end to end through the public API on host buffers (pinned), copies inside the timing
@@ -511,10 +523,7 @@ def main():
             soft_h, hard_h = apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
             e2e_times.append(time.perf_counter() - t0)
         e2e_step = sum(e2e_times) / len(e2e_times)
-        if dist is not None:
-            t = torch.tensor([e2e_step], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_step = t.item()
+        e2e_step = reduce_max(dist, [e2e_step], dev)[0]
         h2d = hp.numel() * 8 + hs.numel() * 8 + hd.numel() * 8
         d2h = soft_h.numel() * 8 + hard_h.numel()
         e2e = {"value": world * w["N"] / e2e_step, "unit": "symbol-vectors/s", "h2d_bytes_per_step": int(h2d),
