@@ -13,6 +13,7 @@
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "detect_tc.cuh"
+#include "detect_tc2.cuh"
 #include "train_f32.cuh"
 
 namespace apsm {
@@ -438,12 +439,16 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     // Engine: the Gram on the tensor cores (TF32 x3 for FP32, BF16/FP16 as requested) where a
     // kernel exists for (M, K); FFMA otherwise (APSM_DETECT_ENGINE=ffma forces it for FP32).
+    // APSM_DETECT_TC_COEF=1 also moves the FP32 coefficient sums onto the tensor cores
+    // (detect_tc2.cuh; correct, not yet faster than the FMA epilogue, so not the default).
     const char *eng = std::getenv("APSM_DETECT_ENGINE");
     const TuneEntry te = tune_get(p->M, p->K, p->dtype);
     const bool force_ffma = eng ? std::strcmp(eng, "ffma") == 0 : (te.set && te.engine == 1);
     if (p->dtype != APSM_FP32 || !force_ffma) {
-        const int prec = p->dtype == APSM_FP32 ? kTF32x3 : kHalf;
+        const bool coef_tc = env_int("APSM_DETECT_TC_COEF", 0) != 0;
+        const int prec = p->dtype == APSM_FP32 ? (coef_tc ? kTF32x3Coef : kTF32x3) : kHalf;
         TcLauncher tc = detect_tc_launcher(p->M, p->K, prec);
+        if (!tc && prec == kTF32x3Coef) tc = detect_tc_launcher(p->M, p->K, kTF32x3);
         if (tc) {
             TcArgs ta{};
             ta.rx = reinterpret_cast<const float2 *>(rx);

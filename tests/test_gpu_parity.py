@@ -253,6 +253,23 @@ def test_tracked_and_sequential_training_agree(M, K, P, W, D, monkeypatch):
     assert np.abs(c1 - c0).max() <= 1e-4 * rms(np.abs(c0))
 
 
+@pytest.mark.parametrize("M,K,D,N", [(16, 6, 1024, 3000), (4, 2, 37, 500), (32, 12, 200, 700), (8, 16, 65, 300)])
+def test_detect_coefficient_sums_on_tensor_cores(M, K, D, N, monkeypatch):
+    """The opt-in FP32 path with both contractions on the tensor cores (E x G with E read from
+    tensor memory) against the oracle, including ragged tiles and the 12- and 16-user buckets."""
+    monkeypatch.setenv("APSM_DETECT_TC_COEF", "1")
+    ent, gam, clin = synth.random_state(M, K, D, instance=M * K + D)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=N + K)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.5, w_L=0.5)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
+    assert_soft_close(soft.cpu().numpy(), ref, what="tensor-core coefficient sums")
+    assert_hard_match(hard.cpu().numpy(), ref)
+    assert apsm.read_status(st) == 0
+
+
 def test_train_with_initial_linear_filter():
     M, K, P = 8, 3, 60
     inst = synth.make_instance(M, K, P, 200, 10.0, instance=41)
