@@ -12,13 +12,15 @@
 //
 // Tile = 32 entries (Gram N = 64), four coefficient sub-chunks of 8 entries per tile.  Tensor
 // memory (256 columns): Gram accumulators 2 x 64, two E buffers of 24 (hi) + 24 (lo), y NY (16
-// or 32).  Roles (256 threads): warps 0-3 epilogue (query row = thread; thread 0 issues the
-// coefficient MMAs of each sub-chunk once the four warps have stored its E), warps 4-7
-// converters (entry rows of the Gram operand, the tile's G operand; thread 128 issues the Gram
-// MMAs).  Barriers:
-//   mma_done[st]  converters' stage st written + Gram MMA of the tile committed
-//   epi_done[st]  epilogue done with the Gram buffer and with the G operand of stage st
-//   e_free[b]     the coefficient MMAs that read E buffer b have completed
+// or 32).  Roles (288 threads): warps 0-3 epilogue (query row = thread), warps 4-7 converters
+// (entry rows of the Gram operand, the tile's G operand), warp 8 issues every MMA (one thread),
+// so the epilogue never waits on an MMA it could overlap.  Barriers:
+//   conv_ready[st]  converters' stage written             mma_done[st]  Gram MMA of the tile done
+//   gram_free[st]   epilogue read Gram buffer st          g_free[gs]    G stage gs (and its norms)
+//   e_ready[b]      epilogue stored E buffer b            e_free[b]     its coefficient MMAs done
+// The entry operand has two stages (reused once the Gram MMA two tiles back is done), the G
+// operand and norms three (reused once the coefficient MMAs three tiles back are done), so the
+// converters run well ahead of the epilogue.
 // All waits are bounded.
 #pragma once
 
@@ -31,6 +33,8 @@ constexpr int kT2Entries = 32;  // entries per Gram tile (MMA N = 64)
 constexpr int kT2Sub = 8;       // entries per coefficient sub-chunk
 constexpr int kT2KG = 3 * kT2Sub;  // contraction length of a sub-chunk's coefficient MMAs (24)
 constexpr int kT2Subs = kT2Entries / kT2Sub;  // sub-chunks per tile
+constexpr int kT2Threads = 288;                // 4 epilogue + 4 converter warps + the MMA warp
+constexpr int kT2GStages = 3;                  // stages of the G operand and the entry norms
 
 template <int M, int KB>
 struct Tc2Smem {
@@ -42,11 +46,10 @@ struct Tc2Smem {
     static constexpr int kBytesG = NY / 8 * kSboG;      // G operand of one sub-chunk, one copy
     static constexpr int kA = 0;
     static constexpr int kB = kA + 2 * Sh::kBytesA;                 // 2 stages x 2 copies
-    static constexpr int kG = kB + 2 * 2 * kBytesB;                 // 2 stages x sub-chunks x 2 copies
-    static constexpr int kN = kG + 2 * kT2Subs * 2 * kBytesG;       // 2 stages x [32] -k2 n_t
-    static constexpr int kGam = round_up(kN + 2 * kT2Entries * 4, 16);  // the tile's raw coefficients
-    static constexpr int kBar = round_up(kGam + kT2Entries * 2 * KB * 4, 16);
-    static constexpr int kTmem = kBar + 64;
+    static constexpr int kG = kB + 2 * 2 * kBytesB;                 // G stages x sub-chunks x 2 copies
+    static constexpr int kN = kG + kT2GStages * kT2Subs * 2 * kBytesG;  // G stages x [32] -k2 n_t
+    static constexpr int kBar = round_up(kN + kT2GStages * kT2Entries * 4, 16);
+    static constexpr int kTmem = kBar + 112;  // 13 mbarriers
     static constexpr int kBytes = kTmem + 16;
     __device__ static constexpr int offG(int r, int k) {
         return (r / 8) * kSboG + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4;
@@ -69,7 +72,7 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
 }
 
 template <int M, int KB>
-__global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs a) {
+__global__ void __launch_bounds__(kT2Threads, 2) detect_tc2_kernel(const TcArgs a) {
     using Sh = TcShape<M, kTF32x3>;
     using L = Tc2Smem<M, KB>;
     constexpr int NB = L::NB, NY = L::NY, E = kT2Entries;
@@ -79,10 +82,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
     unsigned char *sB = smem + L::kB;
     unsigned char *sG = smem + L::kG;
     float *sH = reinterpret_cast<float *>(smem + L::kN);
-    float *sGam = reinterpret_cast<float *>(smem + L::kGam);  // [32][2][K] of the tile being converted
-    uint64_t *mma_done = reinterpret_cast<uint64_t *>(smem + L::kBar);  // [2]: commit + 128 converters
-    uint64_t *epi_done = mma_done + 2;                                   // [2]: 128 epilogue threads
-    uint64_t *e_free = mma_done + 4;                                     // [2]: commit
+    uint64_t *mma_done = reinterpret_cast<uint64_t *>(smem + L::kBar);  // [2]: Gram commit
+    uint64_t *gram_free = mma_done + 2;                                  // [2]: 128 epilogue threads
+    uint64_t *e_free = mma_done + 4;                                     // [2]: coefficient commit
+    uint64_t *conv_ready = mma_done + 6;                                 // [2]: 128 converters
+    uint64_t *e_ready = mma_done + 8;                                    // [2]: 128 epilogue threads
+    uint64_t *g_free = mma_done + 10;                                    // [3]: 128 epilogue threads
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + L::kTmem);
     // E buffer b: hi at kColE + 2 b kT2KG, lo kT2KG columns after it
     constexpr uint32_t kCols = 256, kColE = 2 * NB, kColY = kColE + 4 * kT2KG;
@@ -103,12 +108,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&mma_done[0], 1 + 128);
-        mbar_init(&mma_done[1], 1 + 128);
-        mbar_init(&epi_done[0], kTcRows);
-        mbar_init(&epi_done[1], kTcRows);
-        mbar_init(&e_free[0], 1);
-        mbar_init(&e_free[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&mma_done[i], 1);
+            mbar_init(&gram_free[i], kTcRows);
+            mbar_init(&e_free[i], 1);
+            mbar_init(&conv_ready[i], 128);
+            mbar_init(&e_ready[i], kTcRows);
+        }
+        for (int i = 0; i < kT2GStages; ++i) mbar_init(&g_free[i], kTcRows);
         fence_mbar_init();
     }
     float nq = 0.f;  // squared norm of this epilogue thread's query
@@ -123,6 +130,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
         }
         for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kTF32x3>(sA, Sh::kBytesA, Sh::off(tid, k), 0.f, 0);
     }
+    // G operands start at zero: only the structural positions of the coefficients are ever written
+    for (int i = tid; i < kT2GStages * kT2Subs * 2 * L::kBytesG / 4; i += kT2Threads)
+        reinterpret_cast<uint32_t *>(sG)[i] = 0u;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     const bool cta_in_range = __syncthreads_and(warp >= 4 || a.k2 * nq <= kFactorLimit);
@@ -132,68 +142,48 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
     const uint32_t ifmt = (1u << 4) | (2u << 7) | (2u << 10);  // F32 accumulate, TF32 A and B, K-major
     const uint32_t idesc_g = ifmt | ((uint32_t)(NB >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
     const uint32_t idesc_y = ifmt | ((uint32_t)(NY >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-    auto g_base = [&](int st, int h) { return sG + ((st * kT2Subs + h) * 2) * L::kBytesG; };  // hi; lo follows
+    auto g_base = [&](int gs, int h) { return sG + ((gs * kT2Subs + h) * 2) * L::kBytesG; };  // hi; lo follows
 
     bool ok = true;
-    if (warp >= 4) {
-        // ================= converters + MMA issue =================
-        const int ct = tid - 128;
-        for (int tile = 0; tile < n_tiles; ++tile) {
-            const int st = tile & 1;
-            // the epilogue has released stage st (Gram buffer read, y MMAs of tile-2 done)
-            bool w = true;
-            if (tile >= 2) w = mbar_wait_bounded(&epi_done[st], ((tile - 2) >> 1) & 1);
-            if (!converters_and(w)) {
-                ok = false;
-                break;
-            }
-            const int e0 = tile * E;
-            unsigned char *bst = sB + st * 2 * L::kBytesB;
-            // the tile's coefficients [32][2][K] are contiguous: coalesced loads, all in flight
-            const int n_gam = min(E, max(n_ent - e0, 0)) * 2 * a.K;
-            for (int i = ct; i < E * 2 * a.K; i += 128)
-                sGam[i] = i < n_gam ? __ldg(a.gamma + (size_t)e0 * 2 * a.K + i) : 0.f;
-            if (ct < NB) {
-                const int t = e0 + (ct >> 1), h = ct & 1;
-                // the entry's vector with 128-bit loads issued together, then converted
-                float2 r[M];
-                const float4 *rt = reinterpret_cast<const float4 *>(a.dict + (size_t)t * M);
+    if (warp == 8) {
+        // ================= MMA issue (one thread) =================
+        // Gram of tile t as soon as its operand is converted, then the coefficient MMAs of
+        // tile t-1's sub-chunks as the epilogue stores their E.
+        if ((tid & 31) == 0) {
+            int ysub = 0;
+            auto issue_y = [&](int tile) {
+                const int gs = tile % kT2GStages;
+                for (int h = 0; h < kT2Subs; ++h, ++ysub) {
+                    const int b = ysub & 1;
+                    if (!mbar_wait_bounded(&e_ready[b], (ysub >> 1) & 1)) return false;
+                    tc_fence_after();
+                    const uint32_t gb = smem_u32(g_base(gs, h));
+                    const uint32_t ce = kColE + 2 * kT2KG * b;
 #pragma unroll
-                for (int m = 0; m < M / 2; ++m) {
-                    const float4 v = t < n_ent ? __ldg(rt + m) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    r[2 * m] = make_float2(v.x, v.y);
-                    r[2 * m + 1] = make_float2(v.z, v.w);
+                    for (int s = 0; s < kT2KG / 8; ++s) {
+                        const uint64_t bh = umma_sdesc(gb + s * 256, L::kSboG);
+                        const uint64_t bl = umma_sdesc(gb + L::kBytesG + s * 256, L::kSboG);
+                        umma_tf32_ta(tmem + kColY, tmem + ce + kT2KG + 8 * s, bh, idesc_y, (ysub > 0 || s > 0) ? 1u : 0u);
+                        umma_tf32_ta(tmem + kColY, tmem + ce + 8 * s, bl, idesc_y, 1);
+                        umma_tf32_ta(tmem + kColY, tmem + ce + 8 * s, bh, idesc_y, 1);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&e_free[b]))
+                                 : "memory");
                 }
-                // row 2e: [Re r_t; Im r_t] gives Re z;  row 2e+1: [-Im r_t; Re r_t] gives Im z
-#pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    put_elem<kTF32x3>(bst, L::kBytesB, Sh::off(ct, m), h ? -r[m].y : r[m].x, 0);
-                    put_elem<kTF32x3>(bst, L::kBytesB, Sh::off(ct, M + m), h ? r[m].x : r[m].y, 0);
+                return true;
+            };
+            for (int tile = 0; tile < n_tiles && ok; ++tile) {
+                const int st = tile & 1;
+                // the tile's operands are converted and the epilogue has read Gram buffer st (tile-2)
+                if (!mbar_wait_bounded(&conv_ready[st], (tile >> 1) & 1) ||
+                    (tile >= 2 && !mbar_wait_bounded(&gram_free[st], ((tile - 2) >> 1) & 1))) {
+                    ok = false;
+                    break;
                 }
-                for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kTF32x3>(bst, L::kBytesB, Sh::off(ct, k), 0.f, 0);
-            }
-            named_sync(1, 128);  // sGam complete
-            // G operand of the tile's sub-chunks: rows = y columns, k = v * kT2Sub + e
-            for (int idx = ct; idx < kT2Subs * NY * kT2KG; idx += 128) {
-                const int h = idx / (NY * kT2KG), r = (idx / kT2KG) % NY, k = idx % kT2KG;
-                const int v = k / kT2Sub, e = h * kT2Sub + k % kT2Sub;
-                int l = -1, kk = r;  // coefficient g_l of user kk at this (row, k), or none
-                if (r < KB) l = v == 0 ? 0 : (v == 2 ? 1 : -1);
-                else if (r < 2 * KB) { kk = r - KB; l = v == 1 ? 0 : (v == 0 ? 1 : -1); }
-                const float x = (l >= 0 && kk < a.K) ? sGam[(e * 2 + l) * a.K + kk] : 0.f;
-                put_elem<kTF32x3>(g_base(st, h), L::kBytesG, L::offG(r, k), x, 0);
-            }
-            if (ct < E) {
-                const int t = e0 + ct;
-                sH[st * E + ct] = t < n_ent ? -a.k2 * __ldg(a.dict_norm + t) : 0.f;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            named_sync(1, 128);
-            mbar_arrive(&mma_done[st]);  // releases this thread's sH writes
-            if (ct == 0) {
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(st * NB);
-                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(bst);
+                const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + st * 2 * L::kBytesB);
 #pragma unroll
                 for (int s = 0; s < Sh::kSteps; ++s) {
                     const uint64_t ah = umma_sdesc(a0 + s * 256, Sh::SBO), bh = umma_sdesc(b0 + s * 256, Sh::SBO);
@@ -206,7 +196,78 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(&mma_done[st]))
                              : "memory");
+                if (tile >= 1 && !issue_y(tile - 1)) ok = false;
             }
+            if (ok && n_tiles > 0 && !issue_y(n_tiles - 1)) ok = false;
+        }
+    } else if (warp >= 4) {
+        // ================= converters =================
+        // Software-pipelined: the global loads of tile t+1 (entry vectors, coefficients, norms) go
+        // into registers right after tile t is converted, so their latency overlaps the wait for
+        // the stage.  Thread ct converts half (antennas [mh M/2, (mh+1) M/2)) of operand row ct/2.
+        const int ct = tid - 128;
+        const int row = ct >> 1, mh = ct & 1, hrow = row & 1;
+        constexpr int MH = (M + 1) / 2;                         // antennas per half row
+        constexpr int kGPer = (kT2Entries * 2 * KB + 127) / 128;  // coefficients per thread
+        float2 rp[MH];
+        float gp[kGPer], np = 0.f;
+        auto prefetch = [&](int tile) {
+            const int e0 = tile * E, te = e0 + (row >> 1);
+            const float2 *rt = a.dict + (size_t)te * M + mh * MH;
+#pragma unroll
+            for (int m = 0; m < MH; ++m)
+                rp[m] = (te < n_ent && mh * MH + m < M) ? __ldg(rt + m) : make_float2(0.f, 0.f);
+            const int n_gam = min(E, max(n_ent - e0, 0)) * 2 * a.K;
+#pragma unroll
+            for (int j = 0; j < kGPer; ++j) {
+                const int i = ct + 128 * j;
+                gp[j] = i < n_gam ? __ldg(a.gamma + (size_t)e0 * 2 * a.K + i) : 0.f;
+            }
+            np = (ct < E && e0 + ct < n_ent) ? -a.k2 * __ldg(a.dict_norm + e0 + ct) : 0.f;
+        };
+        if (n_tiles > 0) prefetch(0);
+        for (int tile = 0; tile < n_tiles; ++tile) {
+            const int st = tile & 1;
+            // entry stage st: the Gram MMA of tile-2 is done; G stage gs: the coefficient MMAs of
+            // tile-3 are done (which the epilogue reports)
+            const int gs = tile % kT2GStages;
+            bool w = true;
+            if (tile >= 2) w = mbar_wait_bounded(&mma_done[st], ((tile - 2) >> 1) & 1);
+            if (tile >= kT2GStages) w = w && mbar_wait_bounded(&g_free[gs], ((tile - kT2GStages) / kT2GStages) & 1);
+            if (!converters_and(w)) {
+                ok = false;
+                break;
+            }
+            unsigned char *bst = sB + st * 2 * L::kBytesB;
+            // row 2e: [Re r_t; Im r_t] gives Re z;  row 2e+1: [-Im r_t; Re r_t] gives Im z
+#pragma unroll
+            for (int m0 = 0; m0 < MH; ++m0) {
+                const int m = mh * MH + m0;
+                if (m < M) {
+                    put_elem<kTF32x3>(bst, L::kBytesB, Sh::off(row, m), hrow ? -rp[m0].y : rp[m0].x, 0);
+                    put_elem<kTF32x3>(bst, L::kBytesB, Sh::off(row, M + m), hrow ? rp[m0].x : rp[m0].y, 0);
+                }
+            }
+            if (mh == 0)
+                for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kTF32x3>(bst, L::kBytesB, Sh::off(row, k), 0.f, 0);
+            // coefficient g_l^k of entry e (index (2e + l) K + k of the tile's block) goes to its two
+            // positions of sub-chunk e / 8:  g1: (row k, E_A), (row KB + k, E_B);
+            //                                g2: (row k, E_C), (row KB + k, E_A)
+#pragma unroll
+            for (int j = 0; j < kGPer; ++j) {
+                const int i = ct + 128 * j;
+                if (i < E * 2 * a.K) {
+                    const int k = i % a.K, l = (i / a.K) & 1, e = i / (2 * a.K);
+                    const int el = e % kT2Sub;
+                    unsigned char *gb = g_base(gs, e / kT2Sub);
+                    put_elem<kTF32x3>(gb, L::kBytesG, L::offG(k, (l ? 2 : 0) * kT2Sub + el), gp[j], 0);
+                    put_elem<kTF32x3>(gb, L::kBytesG, L::offG(KB + k, (l ? 0 : 1) * kT2Sub + el), gp[j], 0);
+                }
+            }
+            if (ct < E) sH[gs * E + ct] = np;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&conv_ready[st]);  // releases this thread's operand and sH writes
+            if (tile + 1 < n_tiles) prefetch(tile + 1);
         }
     } else {
         // ================= epilogue: exponentials to tensor memory =================
@@ -216,16 +277,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
         for (int tile = 0; tile < n_tiles && ok; ++tile) {
             const int st = tile & 1;
             // warp-uniform decisions: tcgen05.ld / st below are executed by whole warps only
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&mma_done[st], (tile >> 1) & 1))) {
+            // the Gram MMA of the tile, and the converters' sH writes (acquired from their barrier)
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&mma_done[st], (tile >> 1) & 1) &&
+                                             mbar_wait_bounded(&conv_ready[st], (tile >> 1) & 1))) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const float *hh = sH + st * E;
+            const float *hh = sH + (tile % kT2GStages) * E;
             for (int h = 0; h < kT2Subs; ++h, ++sub) {
                 const int b = sub & 1;
                 float v[16], ex[kT2KG];
                 tmem_ld16(tmem + lane_base + (uint32_t)(st * NB + 16 * h), v);
+                if (h == kT2Subs - 1) {  // Gram buffer st read: the MMA warp may reuse it
+                    tc_fence_before();
+                    mbar_arrive(&gram_free[st]);
+                }
 #pragma unroll
                 for (int e = 0; e < kT2Sub; ++e) {
                     const float hv = hh[h * kT2Sub + e] + hq;
@@ -239,10 +306,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
                     break;
                 }
                 tc_fence_after();
-                if (h == 1 && tile >= 1) {  // tile-1: Gram read, its last sub-chunk's MMAs done -> stage free
-                    tc_fence_before();
-                    mbar_arrive(&epi_done[(tile - 1) & 1]);
-                }
+                if (h == 1 && tile >= 1)  // tile-1: its last sub-chunk's coefficient MMAs done -> G stage free
+                    mbar_arrive(&g_free[(tile - 1) % kT2GStages]);
                 const uint32_t ce = kColE + 2 * kT2KG * b;
 #pragma unroll
                 for (int p = 0; p < 3; ++p) {
@@ -251,30 +316,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
                     for (int j = 0; j < 8; ++j) {
                         const float x = ex[p * 8 + j];
                         hi[j] = tf32_rna(x);
-                        lo[j] = tf32_rna(x - __uint_as_float(hi[j]));
+                        lo[j] = __float_as_uint(x - __uint_as_float(hi[j]));  // exact; read as TF32
                     }
                     tmem_st8(tmem + lane_base + ce + 8 * p, hi);
                     tmem_st8(tmem + lane_base + ce + kT2KG + 8 * p, lo);
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
-                named_sync(2, kTcRows);  // the four epilogue warps have stored this sub-chunk's E
-                if (tid == 0) {
-                    tc_fence_after();
-                    const uint32_t gb = smem_u32(g_base(st, h));
-#pragma unroll
-                    for (int s = 0; s < kT2KG / 8; ++s) {
-                        const uint64_t bh = umma_sdesc(gb + s * 256, L::kSboG);
-                        const uint64_t bl = umma_sdesc(gb + L::kBytesG + s * 256, L::kSboG);
-                        umma_tf32_ta(tmem + kColY, tmem + ce + kT2KG + 8 * s, bh, idesc_y, (sub > 0 || s > 0) ? 1u : 0u);
-                        umma_tf32_ta(tmem + kColY, tmem + ce + 8 * s, bl, idesc_y, 1);
-                        umma_tf32_ta(tmem + kColY, tmem + ce + 8 * s, bh, idesc_y, 1);
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                     smem_u32(&e_free[b]))
-                                 : "memory");
-                }
-                __syncwarp();
+                mbar_arrive(&e_ready[b]);  // the MMA warp issues this sub-chunk's coefficient MMAs
             }
         }
         // y: wait for the last sub-chunk's MMAs, read the accumulator row
@@ -319,7 +368,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) detect_tc2_kernel(const TcArgs 
             }
         }
     }
-    if (!ok && (tid == 0 || tid == 128)) report(a.status, APSM_ERR_TIMEOUT);
+    if (!ok && (tid == 0 || tid == 128 || tid == 256)) report(a.status, APSM_ERR_TIMEOUT);
 
     // ---- teardown: every MMA has been waited for by the epilogue (or timed out) ----------------
     tc_fence_before();
@@ -337,7 +386,7 @@ cudaError_t launch_detect_tc2(const TcArgs &a, cudaStream_t stream) {
     auto fn = detect_tc2_kernel<M, KB>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(fn, dim3(grid), dim3(kTcThreads), L::kBytes, stream, a);
+    e = launch_pdl(fn, dim3(grid), dim3(kT2Threads), L::kBytes, stream, a);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
