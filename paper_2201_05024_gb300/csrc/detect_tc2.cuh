@@ -71,8 +71,12 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8])
                  : "memory");
 }
 
+// two CTAs per SM where the shared memory allows it (registers are then capped accordingly)
 template <int M, int KB>
-__global__ void __launch_bounds__(kT2Threads, 2) detect_tc2_kernel(const TcArgs a) {
+constexpr int tc2_min_blocks() { return Tc2Smem<M, KB>::kBytes <= 113 * 1024 ? 2 : 1; }
+
+template <int M, int KB>
+__global__ void __launch_bounds__(kT2Threads, tc2_min_blocks<M, KB>()) detect_tc2_kernel(const TcArgs a) {
     using Sh = TcShape<M, kTF32x3>;
     using L = Tc2Smem<M, KB>;
     constexpr int NB = L::NB, NY = L::NY, E = kT2Entries;
