@@ -40,7 +40,7 @@ ORACLE_DETECT_SAMPLE = 4096
 
 # DRAM bytes per launch of the detection kernel from one ncu capture, valid only for the kernel
 # source with this digest (a changed kernel reports null until it is re-captured).
-DETECT_TRAFFIC = {"digest": "53754cfdca7ff4d9", "bytes_per_launch": 8.610048e6}
+DETECT_TRAFFIC = {"digest": "7e9f0d9337aff70a", "bytes_per_launch": 8.610048e6}
 
 
 def workload_name(w):
@@ -57,21 +57,25 @@ def measured_peaks():
         return {}
 
 
-def detect_roofline(w, n_entries, seconds):
-    """Roofline of the tensor-core detection launch: algorithmic work per (query, entry) pair is
-    the complex Gram (2M x 2 MACs, issued as three TF32 products for FP32 accuracy) on the tensor
-    pipe, the three exponentials on MUFU, and the exponent arguments plus the coefficient
-    accumulation (4K + 3 FMA) on the FP32 pipe.  The bound is the resource with the largest
-    minimum time; `frac` = that minimum time / measured time."""
+def detect_roofline(w, n_entries, seconds, engine="tf32x3"):
+    """Roofline of one detection launch.  Algorithmic work per (query, entry) pair: the complex
+    Gram (2M x 2 MACs) -- on the tensor pipe as three TF32 products for FP32 accuracy
+    (engine "tf32x3") or one BF16/FP16 product ("half"), or on the FP32 pipe as 4M FMA ("ffma");
+    the three exponentials on MUFU; the exponent arguments and the coefficient accumulation
+    (4K + 3 FMA) on the FP32 pipe.  The bound is the resource with the largest minimum time; `frac` = that minimum time /
+    measured time."""
     pairs = w["N"] * n_entries
     peaks = measured_peaks()
     bf16 = peaks.get("bf16_tflops", 1900.0)
-    tf32_peak = bf16 * (1.1 / 2.25) * 1e12
-    res = {
-        "tensor": (3 * 2 * (2 * w["M"]) * 2 * pairs, tf32_peak, "TFLOP/s"),
-        "alu": (2 * (4 * w["K"] + 3) * pairs, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s"),
-        "mufu": (3 * pairs, MUFU_PEAK_PER_S, "Gex2/s"),
-    }
+    gram = 2 * (2 * w["M"]) * 2 * pairs
+    if engine == "ffma":
+        res = {"alu": (2 * (4 * w["M"] + 4 * w["K"] + 3) * pairs, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s")}
+    else:
+        tensor = ((3 * gram, bf16 * (1.1 / 2.25) * 1e12, "TFLOP/s") if engine == "tf32x3" else
+                  (gram, bf16 * 1e12, "TFLOP/s"))
+        res = {"tensor": tensor,
+               "alu": (2 * (4 * w["K"] + 3) * pairs, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s")}
+    res["mufu"] = (3 * pairs, MUFU_PEAK_PER_S, "Gex2/s")
     tmin = {k: v[0] / v[1] for k, v in res.items()}
     bound = max(tmin, key=tmin.get)
     work, peak, unit = res[bound]
@@ -81,7 +85,8 @@ def detect_roofline(w, n_entries, seconds):
             "frac": tmin[bound] / seconds, "frac_by_resource": others,
             "peak_kind": ("FP32 pipe derived (152 SM x 128 FMA x 2070 MHz)" if bound == "alu" else
                           "MUFU derived (152 SM x 32 ex2 x 2070 MHz)" if bound == "mufu" else
-                          "TF32 = measured BF16 x nominal 1.1/2.25")}
+                          "TF32 = measured BF16 x nominal 1.1/2.25" if engine == "tf32x3" else
+                          "measured BF16 (FP16 taken equal)")}
 
 
 def kernel_digest():
@@ -334,10 +339,15 @@ def run_precision(args):
         ms = _time_events(lambda: apsm.detect(q, st, rd, soft=s_, hard=h_), args.steps, args.warmup)
         soft[dt] = s_
         pairs = N * D
-        out[dt] = {"value": N / (ms / 1e3), "ms": ms, "pairs_per_s": pairs / (ms / 1e3),
-                   "tensor_tflops": (1 if dt != "fp32" else 3) * 2 * (2 * M) * 2 * pairs / (ms / 1e3) / 1e12,
+        # FP32 has no tensor-core kernel above 32 antennas (its TF32 hi/lo operands would not fit
+        # shared memory), so it runs on the FMA engine here; BF16/FP16 take one tensor product.
+        engine = "half" if dt != "fp32" else ("ffma" if M > 32 else "tf32x3")
+        out[dt] = {"value": N / (ms / 1e3), "ms": ms, "pairs_per_s": pairs / (ms / 1e3), "engine": engine,
+                   "roofline": detect_roofline(dict(M=M, K=K, N=N), D, ms / 1e3, engine),
                    "ser": float((h_.cpu().numpy() != x.idx_data).mean())}
     out["value"], out["ms_per_step"], out["dtype"] = out["bf16"]["value"], out["bf16"]["ms"], "bf16"
+    out["roofline"] = {"kernel": "detect_tc_kernel<64,16,half> (BF16)", **out["bf16"]["roofline"],
+                       "traffic": None}
     sample = np.random.default_rng(0).choice(N, 512, replace=False)
     ent, gam = st.entries()
     op = oracle.Params(M=M, K=K, W=16, D=D, sigma=0.5, w_L=0.5)

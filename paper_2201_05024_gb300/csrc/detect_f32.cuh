@@ -113,8 +113,41 @@ __device__ __forceinline__ void load_coef(const float *src, float (&g1)[K], floa
     }
 }
 
+// Lanes per query vector: from 64 antennas on, the query (2M floats) would not fit the register
+// file beside the accumulators, so two adjacent lanes share a query, each holding half of its
+// antennas and accumulating half of the users; their partial inner products meet by one shuffle.
+template <int M>
+constexpr int query_lanes() { return M >= 64 ? 2 : 1; }
+
+// The KH coefficients (both halves) of the users part * KH + j that a lane of a shared query
+// accumulates; a user index past K (odd K, second lane) reads a duplicate that is never stored.
+template <int K, int KH>
+__device__ __forceinline__ void load_coef_part(const float *src, int part, float (&g1)[KH], float (&g2)[KH]) {
+    if constexpr (KH == K) {
+        load_coef<K>(src, g1, g2);
+    } else if constexpr (KH % 4 == 0 && K % 4 == 0) {
+        const float *s1 = src + part * KH, *s2 = src + K + part * KH;
+#pragma unroll
+        for (int j = 0; j < KH; j += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(s1 + j);
+            const float4 y = *reinterpret_cast<const float4 *>(s2 + j);
+            g1[j] = x.x; g1[j + 1] = x.y; g1[j + 2] = x.z; g1[j + 3] = x.w;
+            g2[j] = y.x; g2[j + 1] = y.y; g2[j + 2] = y.z; g2[j + 3] = y.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < KH; ++j) {
+            const int k = min(part * KH + j, K - 1);
+            g1[j] = src[k];
+            g2[j] = src[K + k];
+        }
+    }
+}
+
 template <int M, int K, int QPT>
 __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
+    constexpr int QS = query_lanes<M>();               // lanes per query
+    constexpr int MH = M / QS, KH = (K + QS - 1) / QS;  // antennas and users per lane
     using S = DetectSmem<M, K>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -168,32 +201,35 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     // Queries of this thread, in registers, pre-scaled by g2 = 2 k2 so that the inner product
     // directly gives the exponent 2 k2 z of the factored form.
     const float g2 = 2.f * a.k2;
-    const int q_base = blockIdx.x * blockDim.x * QPT + threadIdx.x;
-    float2 r[QPT][M];
+    const int part = QS > 1 ? (int)threadIdx.x % QS : 0;  // which half of the antennas / users
+    const int qlanes = blockDim.x / QS;                    // queries per entry group and QPT step
+    const int q_base = blockIdx.x * qlanes * QPT + threadIdx.x / QS;
+    float2 r[QPT][MH];
     float hq[QPT];  // -k2 * n_s
     bool q_in_range = true;
 #pragma unroll
     for (int i = 0; i < QPT; ++i) {
-        const int q = q_base + i * blockDim.x;
+        const int q = q_base + i * qlanes;
         float n = 0.f;
         if (q < a.N) {
-            const float4 *src = reinterpret_cast<const float4 *>(a.rx + (size_t)q * M);
+            const float4 *src = reinterpret_cast<const float4 *>(a.rx + (size_t)q * M + part * MH);
 #pragma unroll
-            for (int m = 0; m < M / 2; ++m) {
+            for (int m = 0; m < MH / 2; ++m) {
                 const float4 v = __ldg(src + m);
                 r[i][2 * m] = make_float2(v.x, v.y);
                 r[i][2 * m + 1] = make_float2(v.z, v.w);
             }
         } else {
 #pragma unroll
-            for (int m = 0; m < M; ++m) r[i][m] = make_float2(0.f, 0.f);
+            for (int m = 0; m < MH; ++m) r[i][m] = make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int m = 0; m < M; ++m) n = fmaf(r[i][m].x, r[i][m].x, fmaf(r[i][m].y, r[i][m].y, n));
+        for (int m = 0; m < MH; ++m) n = fmaf(r[i][m].x, r[i][m].x, fmaf(r[i][m].y, r[i][m].y, n));
+        if constexpr (QS > 1) n += __shfl_xor_sync(0xffffffffu, n, 1);
         hq[i] = -a.k2 * n;
         q_in_range = q_in_range && (a.k2 * n <= kFactorLimit);
 #pragma unroll
-        for (int m = 0; m < M; ++m) r[i][m] = make_float2(g2 * r[i][m].x, g2 * r[i][m].y);
+        for (int m = 0; m < MH; ++m) r[i][m] = make_float2(g2 * r[i][m].x, g2 * r[i][m].y);
     }
     const bool cta_in_range = __syncthreads_and(q_in_range);
     // The query factor 2^(-k2 n_s) multiplies the sum at the end when the CTA is in range; the
@@ -202,11 +238,11 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 #pragma unroll
     for (int i = 0; i < QPT; ++i) qs[i] = cta_in_range ? ex2(-hq[i]) : 1.f;
 
-    float acc1[QPT][K], acc2[QPT][K];
+    float acc1[QPT][KH], acc2[QPT][KH];
 #pragma unroll
     for (int i = 0; i < QPT; ++i)
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc1[i][k] = acc2[i][k] = 0.f;
+        for (int k = 0; k < KH; ++k) acc1[i][k] = acc2[i][k] = 0.f;
 
     for (int tile = 0; tile < n_tiles; ++tile) {
         const bool ok = mbar_wait_bounded(&bar[tile & 1], (tile >> 1) & 1);
@@ -238,9 +274,9 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
                 float zr[QPT], zi[QPT];
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) zr[i] = zi[i] = 0.f;
-                const float4 *d4 = reinterpret_cast<const float4 *>(sd + t * M);
+                const float4 *d4 = reinterpret_cast<const float4 *>(sd + t * M + part * MH);
 #pragma unroll
-                for (int m = 0; m < M / 2; ++m) {
+                for (int m = 0; m < MH / 2; ++m) {
                     const float4 d = d4[m];
 #pragma unroll
                     for (int i = 0; i < QPT; ++i) {
@@ -255,13 +291,20 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
                         zi[i] = fmaf(-d.w, x1.x, zi[i]);
                     }
                 }
-                float gm1[K], gm2[K];
-                load_coef<K>(s_gs + t * 2 * K, gm1, gm2);
+                if constexpr (QS > 1) {
+#pragma unroll
+                    for (int i = 0; i < QPT; ++i) {
+                        zr[i] += __shfl_xor_sync(0xffffffffu, zr[i], 1);
+                        zi[i] += __shfl_xor_sync(0xffffffffu, zi[i], 1);
+                    }
+                }
+                float gm1[KH], gm2[KH];
+                load_coef_part<K, KH>(s_gs + t * 2 * K, part, gm1, gm2);
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) {
                     const float eA = ex2(zr[i]), eB = ex2(zi[i]), eC = ex2(-zi[i]);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
+                    for (int k = 0; k < KH; ++k) {
                         acc1[i][k] = fmaf(gm1[k], eA, fmaf(gm2[k], eC, acc1[i][k]));
                         acc2[i][k] = fmaf(gm1[k], eB, fmaf(gm2[k], eA, acc2[i][k]));
                     }
@@ -280,8 +323,8 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) dA[i] = dB[i] = dC[i] = 0.f;
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    const float2 d = sd[t * M + m];
+                for (int m = 0; m < MH; ++m) {
+                    const float2 d = sd[t * M + part * MH + m];
 #pragma unroll
                     for (int i = 0; i < QPT; ++i) {
                         const float sx = r[i][m].x * inv_g2, sy = r[i][m].y * inv_g2;
@@ -293,13 +336,21 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
                         dC[i] = fmaf(cx, cx, fmaf(cy, cy, dC[i]));
                     }
                 }
-                float gm1[K], gm2[K];
-                load_coef<K>(sg + t * 2 * K, gm1, gm2);
+                if constexpr (QS > 1) {
+#pragma unroll
+                    for (int i = 0; i < QPT; ++i) {
+                        dA[i] += __shfl_xor_sync(0xffffffffu, dA[i], 1);
+                        dB[i] += __shfl_xor_sync(0xffffffffu, dB[i], 1);
+                        dC[i] += __shfl_xor_sync(0xffffffffu, dC[i], 1);
+                    }
+                }
+                float gm1[KH], gm2[KH];
+                load_coef_part<K, KH>(sg + t * 2 * K, part, gm1, gm2);
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) {
                     const float eA = ex2(-a.k2 * dA[i]), eB = ex2(-a.k2 * dB[i]), eC = ex2(-a.k2 * dC[i]);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) {
+                    for (int k = 0; k < KH; ++k) {
                         acc1[i][k] = fmaf(gm1[k] * qs[i], eA, fmaf(gm2[k] * qs[i], eC, acc1[i][k]));
                         acc2[i][k] = fmaf(gm1[k] * qs[i], eB, fmaf(gm2[k] * qs[i], eA, acc2[i][k]));
                     }
@@ -317,25 +368,25 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     // merge the entry groups' partial sums in group order (group 0 keeps and finishes them)
     if (blockDim.y > 1) {
         if (threadIdx.y > 0) {
-            float *dst = s_red + ((size_t)(threadIdx.y - 1) * blockDim.x + threadIdx.x) * QPT * 2 * K;
+            float *dst = s_red + ((size_t)(threadIdx.y - 1) * blockDim.x + threadIdx.x) * QPT * 2 * KH;
 #pragma unroll
             for (int i = 0; i < QPT; ++i)
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    dst[(i * 2 + 0) * K + k] = acc1[i][k];
-                    dst[(i * 2 + 1) * K + k] = acc2[i][k];
+                for (int k = 0; k < KH; ++k) {
+                    dst[(i * 2 + 0) * KH + k] = acc1[i][k];
+                    dst[(i * 2 + 1) * KH + k] = acc2[i][k];
                 }
         }
         __syncthreads();
         if (threadIdx.y > 0) return;
         for (int y = 1; y < (int)blockDim.y; ++y) {
-            const float *src = s_red + ((size_t)(y - 1) * blockDim.x + threadIdx.x) * QPT * 2 * K;
+            const float *src = s_red + ((size_t)(y - 1) * blockDim.x + threadIdx.x) * QPT * 2 * KH;
 #pragma unroll
             for (int i = 0; i < QPT; ++i)
 #pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    acc1[i][k] += src[(i * 2 + 0) * K + k];
-                    acc2[i][k] += src[(i * 2 + 1) * K + k];
+                for (int k = 0; k < KH; ++k) {
+                    acc1[i][k] += src[(i * 2 + 0) * KH + k];
+                    acc2[i][k] += src[(i * 2 + 1) * KH + k];
                 }
         }
     }
@@ -343,36 +394,58 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     const float inv_g2 = 1.f / g2;
 #pragma unroll
     for (int i = 0; i < QPT; ++i) {
-        const int q = q_base + i * blockDim.x;
-        if (q >= a.N) continue;
+        const int q = q_base + i * qlanes;
+        const bool live = q < a.N;  // the same for both lanes of a shared query
+        if (QS == 1 && !live) continue;  // (a shared query's lanes still meet at the shuffles)
         const float fq = cta_in_range ? ex2(hq[i]) : 1.f;  // query factor 2^(-k2 n_s)
         if (a.partial != nullptr) {
+            if (!live) continue;
             float *dst = a.partial + ((size_t)blockIdx.y * a.N + q) * 2 * K;
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                dst[k] = fq * acc1[i][k];
-                dst[K + k] = fq * acc2[i][k];
+            for (int j = 0; j < KH; ++j) {
+                const int k = part * KH + j;
+                if (QS == 1 || k < K) {
+                    dst[k] = fq * acc1[i][j];
+                    dst[K + k] = fq * acc2[i][j];
+                }
             }
             continue;
         }
-        unsigned char hbits[K];
+        unsigned char hbits[KH];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            float l1 = 0.f, l2 = 0.f;  // c_k^H r = sum_m conj(c[m][k]) r[m]  (r held as g2 r)
+        for (int j = 0; j < KH; ++j) {
+            // c_k^H r = sum_m conj(c[m][k]) r[m]  (r held as g2 r); with a shared query each lane
+            // sums its own antennas for its own user and for the partner's user of the same j,
+            // and the partner's sum for this lane's user arrives by shuffle (all lanes take part).
+            const int k = min(part * KH + j, K - 1);
+            float l1 = 0.f, l2 = 0.f;
 #pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const float2 c = s_clin[m * K + k];
+            for (int m = 0; m < MH; ++m) {
+                const float2 c = s_clin[(part * MH + m) * K + k];
                 l1 = fmaf(c.x, r[i][m].x, fmaf(c.y, r[i][m].y, l1));
                 l2 = fmaf(c.x, r[i][m].y, fmaf(-c.y, r[i][m].x, l2));
             }
-            const float y1 = fmaf(a.wL * inv_g2, l1, a.wG * fq * acc1[i][k]);
-            const float y2 = fmaf(a.wL * inv_g2, l2, a.wG * fq * acc2[i][k]);
-            a.soft[(size_t)q * K + k] = make_float2(y1, y2);
-            hbits[k] = (unsigned char)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
-        }
-        if (a.hard) {
+            if constexpr (QS > 1) {
+                const int ko = min((1 - part) * KH + j, K - 1);
+                float o1 = 0.f, o2 = 0.f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) a.hard[(size_t)q * K + k] = hbits[k];
+                for (int m = 0; m < MH; ++m) {
+                    const float2 c = s_clin[(part * MH + m) * K + ko];
+                    o1 = fmaf(c.x, r[i][m].x, fmaf(c.y, r[i][m].y, o1));
+                    o2 = fmaf(c.x, r[i][m].y, fmaf(-c.y, r[i][m].x, o2));
+                }
+                l1 += __shfl_xor_sync(0xffffffffu, o1, 1);
+                l2 += __shfl_xor_sync(0xffffffffu, o2, 1);
+            }
+            const float y1 = fmaf(a.wL * inv_g2, l1, a.wG * fq * acc1[i][j]);
+            const float y2 = fmaf(a.wL * inv_g2, l2, a.wG * fq * acc2[i][j]);
+            if (live && (QS == 1 || part * KH + j < K)) a.soft[(size_t)q * K + k] = make_float2(y1, y2);
+            hbits[j] = (unsigned char)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
+        }
+        if (a.hard && live) {
+#pragma unroll
+            for (int j = 0; j < KH; ++j)
+                if (QS == 1 || part * KH + j < K) a.hard[(size_t)q * K + part * KH + j] = hbits[j];
         }
     }
     if (a.pdl_late) pdl_wait();
@@ -388,7 +461,7 @@ template <int M, int K>
 cudaError_t launch_detect_f32(const DetectArgs &a, int grid_y, DetectShape sh, cudaStream_t stream) {
     using S = DetectSmem<M, K>;
     if constexpr (M > 16) sh.qpt = 1;
-    const int per_cta = sh.threads * sh.qpt;
+    const int per_cta = sh.threads / query_lanes<M>() * sh.qpt;
     const int gx = (a.N + per_cta - 1) / per_cta;
     if (gx == 0 || grid_y == 0) return cudaSuccess;
     const dim3 grid(gx, grid_y), block(sh.threads, sh.split);

@@ -172,8 +172,12 @@ __device__ __forceinline__ bool converters_and(bool v) {
     return r != 0;
 }
 
+// two CTAs per SM where the shared memory allows it (registers are then capped accordingly)
 template <int M, int KB, int kPrec>
-__global__ void __launch_bounds__(kTcThreads, 2) detect_tc_kernel(const TcArgs a) {
+constexpr int tc_min_blocks() { return TcSmem<M, KB, kPrec>::kBytes <= 113 * 1024 ? 2 : 1; }
+
+template <int M, int KB, int kPrec>
+__global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) detect_tc_kernel(const TcArgs a) {
     using Sh = TcShape<M, kPrec>;
     using L = TcSmem<M, KB, kPrec>;
     extern __shared__ __align__(1024) unsigned char smem[];

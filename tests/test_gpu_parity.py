@@ -34,6 +34,7 @@ DETECT_CASES = [
     (8, 3, 100, 257, 0.4, 0.8),
     (32, 12, 300, 513, 0.6, 0.5),
     (64, 16, 130, 300, 0.5, 0.5),
+    (64, 7, 70, 131, 0.5, 0.5),         # two lanes per query, odd user count, ragged tail
     (16, 16, 64, 70, 0.3, 0.0),         # Gaussian part only
     (8, 5, 40, 129, 0.5, 1.0),          # linear part only
     (16, 6, 1, 31, 0.5, 0.5),           # a single entry
@@ -65,12 +66,13 @@ def test_detect_matches_oracle(M, K, D, N, sigma, wL, engine):
     assert apsm.read_status(st) == 0
 
 
+@pytest.mark.parametrize("M,K", [(16, 6), (64, 5)])
 @pytest.mark.parametrize("case", ["offset", "mixed_entries", "mixed_queries"])
-def test_detect_unnormalised_inputs(case, engine):
+def test_detect_unnormalised_inputs(case, M, K, engine):
     """Inputs outside the range where the factored exponentials are used: a large common offset
     (||r||^2 >> ||r - r_t||^2, where a norm expansion would cancel), a dictionary whose tiles are
     partly out of range, and query blocks that are partly out of range."""
-    M, K, D, N = 16, 6, 200, 700
+    D, N = 200, 700
     rng = np.random.default_rng(11)
     ent, gam, clin = synth.random_state(M, K, D, instance=5)
     inst = synth.make_instance(M, K, 4, N, 10.0, instance=6)
@@ -224,6 +226,7 @@ TRAIN_CASES = [
     (8, 16, 70, 16, 70, 0.5, 0.5, 0.01, 1.0, 100),      # linear-only kernel
     (8, 2, 70, 16, 70, 0.5, 0.5, 0.01, 0.0, 100),       # Gaussian-only kernel
     (64, 4, 60, 10, 60, 0.5, 0.5, 0.01, 0.5, 100),
+    (64, 5, 200, 8, 100, 0.5, 0.5, 0.01, 0.5, 150),     # 64 antennas over several chunks, eviction
     (16, 6, 600, 16, 200, 0.5, 0.5, 0.01, 0.5, 300),    # many full chunks, eviction, ring wrap
 ]
 
