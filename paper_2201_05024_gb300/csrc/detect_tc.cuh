@@ -160,6 +160,88 @@ __device__ __forceinline__ void put_elem(unsigned char *base, int copy_bytes, in
     }
 }
 
+// Writes one 16-byte core row (TcShape::kCoreK consecutive elements x[]) at byte offset `off` of
+// every operand copy: packed BF16/FP16 pairs, or TF32 hi and lo words.
+template <int kPrec, int C>
+__device__ __forceinline__ void put_core(unsigned char *base, int copy_bytes, int off, const float (&x)[C],
+                                         int half_fmt) {
+    if constexpr (kPrec == kTF32x3) {
+        static_assert(C == 4, "a TF32 core row holds four elements");
+        uint4 hi, lo;
+        uint32_t *h = &hi.x, *l = &lo.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            h[c] = tf32_rna(x[c]);
+            l[c] = tf32_rna(x[c] - __uint_as_float(h[c]));
+        }
+        *reinterpret_cast<uint4 *>(base + off) = hi;
+        *reinterpret_cast<uint4 *>(base + copy_bytes + off) = lo;
+    } else {
+        static_assert(C == 8, "a 16-bit core row holds eight elements");
+        uint4 v;
+        uint32_t *p = &v.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (half_fmt) {
+                const __nv_bfloat162 b = __floats2bfloat162_rn(x[2 * c], x[2 * c + 1]);
+                p[c] = *reinterpret_cast<const uint32_t *>(&b);
+            } else {
+                const __half2 b = __floats2half2_rn(x[2 * c], x[2 * c + 1]);
+                p[c] = *reinterpret_cast<const uint32_t *>(&b);
+            }
+        }
+        *reinterpret_cast<uint4 *>(base + off) = v;
+    }
+}
+
+// Whole core rows can be written when a core row never straddles the real and imaginary halves
+// and the contraction needs no padding (M a multiple of the elements per core row).
+template <int M, int kPrec>
+constexpr bool tc_core_rows() {
+    using Sh = TcShape<M, kPrec>;
+    return M % Sh::kCoreK == 0 && Sh::KD == 2 * M;
+}
+
+// The entry operand of one tile by whole core rows.  Task = (entry e, half h, piece p): B row
+// 2e+h at k = p C.. and k = M + p C.. from the C complex values r_t[p C .. p C + C), i.e.
+//   row 2e: [Re | Im],  row 2e+1: [-Im | Re].
+// The eight lanes of a quarter-warp take the same piece of four consecutive entries (both
+// halves), i.e. eight consecutive B rows, so their 16-byte stores hit all 32 banks once.
+template <int M, int kPrec>
+__device__ __forceinline__ void put_entry_rows(unsigned char *bst, const float2 *__restrict__ dict, int e0,
+                                               int n_ent, int ct, int half_fmt) {
+    using Sh = TcShape<M, kPrec>;
+    constexpr int C = Sh::kCoreK, P = M / C;
+    const int lane = ct & 31, w = ct >> 5;
+    const int h = lane & 1, j = (lane >> 1) & 3;
+#pragma unroll 2
+    for (int i = 0; i < P; ++i) {  // 64 entries x 2 halves x P pieces over 128 threads
+        const int R = (lane >> 3) + 4 * (w + 4 * i);  // [0, 16 P): (entry group of 4, piece)
+        const int p = R % P, e = 4 * (R / P) + j, t = e0 + e;
+        float re[C], im[C];
+        if (t < n_ent) {
+            const float4 *src = reinterpret_cast<const float4 *>(dict + (size_t)t * M + p * C);
+#pragma unroll
+            for (int q = 0; q < C / 2; ++q) {
+                const float4 v = __ldg(src + q);
+                re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; ++c) re[c] = im[c] = 0.f;
+        }
+        float x0[C], x1[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            x0[c] = h ? -im[c] : re[c];
+            x1[c] = h ? re[c] : im[c];
+        }
+        const int r = 2 * e + h;
+        put_core<kPrec, C>(bst, Sh::kBytesB, Sh::off(r, p * C), x0, half_fmt);
+        put_core<kPrec, C>(bst, Sh::kBytesB, Sh::off(r, M + p * C), x1, half_fmt);
+    }
+}
+
 __device__ __forceinline__ bool converters_and(bool v) {
     // AND over the 128 converter threads (named barrier 1)
     uint32_t r;
@@ -217,13 +299,42 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
     if (warp < 4) {
         const int s = q0 + tid;
         const float2 *rq = a.rx + (size_t)s * M;
-        for (int m = 0; m < M; ++m) {
-            const float2 v = s < a.N ? __ldg(rq + m) : make_float2(0.f, 0.f);
-            nq = fmaf(v.x, v.x, fmaf(v.y, v.y, nq));
-            put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, m), g2 * v.x, a.half_fmt);
-            put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, M + m), g2 * v.y, a.half_fmt);
+        if constexpr (tc_core_rows<M, kPrec>()) {
+            // this thread's query row by whole core rows: [Re | Im] x 2 k2 (a quarter-warp writes
+            // eight consecutive rows of one core column: conflict-free 16-byte stores)
+            constexpr int C = Sh::kCoreK;
+#pragma unroll 2
+            for (int p = 0; p < M / C; ++p) {
+                float re[C], im[C];
+                if (s < a.N) {
+                    const float4 *src = reinterpret_cast<const float4 *>(rq + p * C);
+#pragma unroll
+                    for (int q = 0; q < C / 2; ++q) {
+                        const float4 v = __ldg(src + q);
+                        re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < C; ++c) re[c] = im[c] = 0.f;
+                }
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    nq = fmaf(re[c], re[c], fmaf(im[c], im[c], nq));
+                    re[c] *= g2;
+                    im[c] *= g2;
+                }
+                put_core<kPrec, C>(sA, Sh::kBytesA, Sh::off(tid, p * C), re, a.half_fmt);
+                put_core<kPrec, C>(sA, Sh::kBytesA, Sh::off(tid, M + p * C), im, a.half_fmt);
+            }
+        } else {
+            for (int m = 0; m < M; ++m) {
+                const float2 v = s < a.N ? __ldg(rq + m) : make_float2(0.f, 0.f);
+                nq = fmaf(v.x, v.x, fmaf(v.y, v.y, nq));
+                put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, m), g2 * v.x, a.half_fmt);
+                put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, M + m), g2 * v.y, a.half_fmt);
+            }
+            for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, k), 0.f, a.half_fmt);
         }
-        for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, k), 0.f, a.half_fmt);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -260,7 +371,9 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
             }
             const int e0 = tile * E;
             unsigned char *bst = sB + st * Sh::kCopies * Sh::kBytesB;
-            {
+            if constexpr (tc_core_rows<M, kPrec>()) {
+                put_entry_rows<M, kPrec>(bst, a.dict, e0, n_ent, ct, a.half_fmt);
+            } else {
                 const int t = e0 + (ct >> 1), h = ct & 1;
                 const float2 *rt = a.dict + (size_t)t * M;
                 // row 2e: [Re r_t; Im r_t] gives Re z;  row 2e+1: [-Im r_t; Re r_t] gives Im z
@@ -271,7 +384,16 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                 }
                 for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kPrec>(bst, Sh::kBytesB, Sh::off(ct, k), 0.f, a.half_fmt);
             }
-            if (ct < E) {  // the tile's coefficients (zero past the last entry) and -k2 n_t
+            if ((2 * KB) % 4 == 0 && a.K == KB) {
+                // the tile's coefficients row by row as float4 (global [2][K] = shared [2 KB])
+                constexpr int kQ = 2 * KB / 4;
+                for (int idx = ct; idx < E * kQ; idx += 128) {
+                    const int e = idx / kQ, q = idx % kQ, t = e0 + e;
+                    const float4 v = t < n_ent ? __ldg(reinterpret_cast<const float4 *>(a.gamma + (size_t)t * 2 * KB) + q)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    *reinterpret_cast<float4 *>(sG + (st * E + e) * 2 * KB + 4 * q) = v;
+                }
+            } else if (ct < E) {  // the tile's coefficients (zero past the last entry and user)
                 const int t = e0 + ct;
                 float *g = sG + (st * E + ct) * 2 * KB;
 #pragma unroll
@@ -279,8 +401,8 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                     const int l = j / KB, k = j % KB;
                     g[j] = (t < n_ent && k < a.K) ? __ldg(a.gamma + ((size_t)t * 2 + l) * a.K + k) : 0.f;
                 }
-                sH[st * E + ct] = t < n_ent ? -a.k2 * __ldg(a.dict_norm + t) : 0.f;
             }
+            if (ct < E) sH[st * E + ct] = e0 + ct < n_ent ? -a.k2 * __ldg(a.dict_norm + e0 + ct) : 0.f;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             named_sync(1, 128);
             mbar_arrive(&mma_done[st]);  // releases this thread's coefficient and norm writes

@@ -104,6 +104,8 @@ HALF_CASES = [
     (16, 6, 200, 700, "bf16"),
     (8, 3, 65, 129, "fp16"),
     (2, 1, 5, 40, "bf16"),
+    (4, 2, 70, 200, "bf16"),        # operands element by element (a core row spans Re and Im)
+    (32, 12, 130, 300, "bf16"),     # operands by whole core rows, coefficients as float4
 ]
 TOL_HALF = 2e-2
 
