@@ -217,40 +217,76 @@ constexpr bool tc_core_rows() {
 //   row 2e: [Re | Im],  row 2e+1: [-Im | Re].
 // The eight lanes of a quarter-warp take the same piece of four consecutive entries (both
 // halves), i.e. eight consecutive B rows, so their 16-byte stores hit all 32 banks once.
+// The first PF tasks' global loads can be issued ahead (prefetch), before the converters wait
+// for the stage they will write, so that their L2 latency overlaps the wait.
 template <int M, int kPrec>
-__device__ __forceinline__ void put_entry_rows(unsigned char *bst, const float2 *__restrict__ dict, int e0,
-                                               int n_ent, int ct, int half_fmt) {
+struct EntryRows {
     using Sh = TcShape<M, kPrec>;
-    constexpr int C = Sh::kCoreK, P = M / C;
-    const int lane = ct & 31, w = ct >> 5;
-    const int h = lane & 1, j = (lane >> 1) & 3;
-#pragma unroll 2
-    for (int i = 0; i < P; ++i) {  // 64 entries x 2 halves x P pieces over 128 threads
+    // (instantiated for every M; used only where tc_core_rows<M, kPrec>() holds, so that P >= 1)
+    static constexpr int C = Sh::kCoreK, P = M / C > 0 ? M / C : 1, V = C / 2;  // float4 loads per task
+    static constexpr int PF = P * V <= 8 ? P : 8 / V;                          // prefetched tasks (<= 8 float4)
+    float4 pf[PF][V];
+
+    // task i of thread ct: 64 entries x 2 halves x P pieces over 128 threads
+    __device__ __forceinline__ static void task(int ct, int i, int &e, int &h, int &p) {
+        const int lane = ct & 31, w = ct >> 5;
         const int R = (lane >> 3) + 4 * (w + 4 * i);  // [0, 16 P): (entry group of 4, piece)
-        const int p = R % P, e = 4 * (R / P) + j, t = e0 + e;
-        float re[C], im[C];
+        h = lane & 1;
+        p = R % P;
+        e = 4 * (R / P) + ((lane >> 1) & 3);
+    }
+    __device__ __forceinline__ static void load(const float2 *__restrict__ dict, int t, int n_ent, int p,
+                                                float4 (&v)[V]) {
         if (t < n_ent) {
             const float4 *src = reinterpret_cast<const float4 *>(dict + (size_t)t * M + p * C);
 #pragma unroll
-            for (int q = 0; q < C / 2; ++q) {
-                const float4 v = __ldg(src + q);
-                re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
-            }
+            for (int q = 0; q < V; ++q) v[q] = __ldg(src + q);
         } else {
 #pragma unroll
-            for (int c = 0; c < C; ++c) re[c] = im[c] = 0.f;
+            for (int q = 0; q < V; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+    }
+    __device__ __forceinline__ void prefetch(const float2 *__restrict__ dict, int e0, int n_ent, int ct) {
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            int e, h, p;
+            task(ct, i, e, h, p);
+            load(dict, e0 + e, n_ent, p, pf[i]);
+        }
+    }
+    __device__ __forceinline__ static void put(unsigned char *bst, int e, int h, int p, const float4 (&v)[V],
+                                               int half_fmt) {
         float x0[C], x1[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            x0[c] = h ? -im[c] : re[c];
-            x1[c] = h ? re[c] : im[c];
+        for (int q = 0; q < V; ++q) {
+            // v[q] = (Re, Im) of two consecutive antennas
+            x0[2 * q] = h ? -v[q].y : v[q].x;
+            x0[2 * q + 1] = h ? -v[q].w : v[q].z;
+            x1[2 * q] = h ? v[q].x : v[q].y;
+            x1[2 * q + 1] = h ? v[q].z : v[q].w;
         }
         const int r = 2 * e + h;
         put_core<kPrec, C>(bst, Sh::kBytesB, Sh::off(r, p * C), x0, half_fmt);
         put_core<kPrec, C>(bst, Sh::kBytesB, Sh::off(r, M + p * C), x1, half_fmt);
     }
-}
+    __device__ __forceinline__ void write(unsigned char *bst, const float2 *__restrict__ dict, int e0, int n_ent,
+                                          int ct, int half_fmt) const {
+#pragma unroll
+        for (int i = 0; i < PF; ++i) {
+            int e, h, p;
+            task(ct, i, e, h, p);
+            put(bst, e, h, p, pf[i], half_fmt);
+        }
+#pragma unroll 1
+        for (int i = PF; i < P; ++i) {
+            int e, h, p;
+            task(ct, i, e, h, p);
+            float4 v[V];
+            load(dict, e0 + e, n_ent, p, v);
+            put(bst, e, h, p, v, half_fmt);
+        }
+    }
+};
 
 __device__ __forceinline__ bool converters_and(bool v) {
     // AND over the 128 converter threads (named barrier 1)
@@ -370,6 +406,28 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
     if (warp >= 4) {
         // ================= converters + MMA issue =================
         const int ct = tid - 128;  // B row of this thread: entry ct/2, half ct%2
+        // global loads of a tile issued ahead of the wait for its stage (whole-core-row form)
+        constexpr bool kVecG = (2 * KB) % 4 == 0;
+        constexpr int kQ = 2 * KB / 4, kGQ = (E * kQ + 127) / 128;
+        const bool vec_g = kVecG && a.K == KB;
+        EntryRows<M, kPrec> rows;
+        float4 gpf[kGQ];
+        float hpf = 0.f;
+        auto prefetch = [&](int tile) {
+            const int e0 = tile * E;
+            if constexpr (tc_core_rows<M, kPrec>()) rows.prefetch(a.dict, e0, n_ent, ct);
+            if (vec_g) {
+#pragma unroll
+                for (int j = 0; j < kGQ; ++j) {
+                    const int idx = ct + 128 * j, e = idx / kQ, q = idx % kQ, t = e0 + e;
+                    gpf[j] = (idx < E * kQ && t < n_ent)
+                                 ? __ldg(reinterpret_cast<const float4 *>(a.gamma + (size_t)t * 2 * KB) + q)
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            hpf = (ct < E && e0 + ct < n_ent) ? -a.k2 * __ldg(a.dict_norm + e0 + ct) : 0.f;
+        };
+        if (n_tiles > 0) prefetch(0);
         for (int tile = 0; tile < n_tiles; ++tile) {
             const int st = tile & 1;
             // the epilogue of tile-2 has released stage st (TMEM accumulator, coefficients), and
@@ -383,7 +441,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
             const int e0 = tile * E;
             unsigned char *bst = sB + st * Sh::kCopies * Sh::kBytesB;
             if constexpr (tc_core_rows<M, kPrec>()) {
-                put_entry_rows<M, kPrec>(bst, a.dict, e0, n_ent, ct, a.half_fmt);
+                rows.write(bst, a.dict, e0, n_ent, ct, a.half_fmt);
             } else {
                 const int t = e0 + (ct >> 1), h = ct & 1;
                 const float2 *rt = a.dict + (size_t)t * M;
@@ -395,14 +453,12 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                 }
                 for (int k = 2 * M; k < Sh::KD; ++k) put_elem<kPrec>(bst, Sh::kBytesB, Sh::off(ct, k), 0.f, a.half_fmt);
             }
-            if ((2 * KB) % 4 == 0 && a.K == KB) {
+            if (vec_g) {
                 // the tile's coefficients row by row as float4 (global [2][K] = shared [2 KB])
-                constexpr int kQ = 2 * KB / 4;
-                for (int idx = ct; idx < E * kQ; idx += 128) {
-                    const int e = idx / kQ, q = idx % kQ, t = e0 + e;
-                    const float4 v = t < n_ent ? __ldg(reinterpret_cast<const float4 *>(a.gamma + (size_t)t * 2 * KB) + q)
-                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-                    *reinterpret_cast<float4 *>(sG + (st * E + e) * 2 * KB + 4 * q) = v;
+#pragma unroll
+                for (int j = 0; j < kGQ; ++j) {
+                    const int idx = ct + 128 * j, e = idx / kQ, q = idx % kQ;
+                    if (idx < E * kQ) *reinterpret_cast<float4 *>(sG + (st * E + e) * 2 * KB + 4 * q) = gpf[j];
                 }
             } else if (ct < E) {  // the tile's coefficients (zero past the last entry and user)
                 const int t = e0 + ct;
@@ -413,7 +469,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                     g[j] = (t < n_ent && k < a.K) ? __ldg(a.gamma + ((size_t)t * 2 + l) * a.K + k) : 0.f;
                 }
             }
-            if (ct < E) sH[st * E + ct] = e0 + ct < n_ent ? -a.k2 * __ldg(a.dict_norm + e0 + ct) : 0.f;
+            if (ct < E) sH[st * E + ct] = hpf;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             named_sync(1, 128);
             mbar_arrive(&mma_done[st]);  // releases this thread's coefficient and norm writes
@@ -438,6 +494,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                                  smem_u32(&mma_done[st]))
                              : "memory");
             }
+            if (tile + 1 < n_tiles) prefetch(tile + 1);
         }
     } else {
         // ================= epilogue: exponentials and coefficient sums =================
