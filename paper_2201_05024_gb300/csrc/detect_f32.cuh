@@ -113,6 +113,16 @@ __device__ __forceinline__ void load_coef(const float *src, float (&g1)[K], floa
     }
 }
 
+// Packed FP32 pair FMA (Blackwell): (d0, d1) = (a0 * b + d0, a1 * b + d1), each lane an IEEE
+// fma with one rounding, so results equal two fmaf calls bit for bit in half the instructions.
+__device__ __forceinline__ void fma2_pair(float &d0, float &d1, float a0, float a1, float b) {
+    asm("{\n\t.reg .b64 d, a, b;\n\t"
+        "mov.b64 d, {%0, %1};\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %4};\n\t"
+        "fma.rn.f32x2 d, a, b, d;\n\tmov.b64 {%0, %1}, d;\n\t}"
+        : "+f"(d0), "+f"(d1)
+        : "f"(a0), "f"(a1), "f"(b));
+}
+
 // Lanes per query vector: from 64 antennas on, the query (2M floats) would not fit the register
 // file beside the accumulators, so two adjacent lanes share a query, each holding half of its
 // antennas and accumulating half of the users; their partial inner products meet by one shuffle.
@@ -303,10 +313,17 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
 #pragma unroll
                 for (int i = 0; i < QPT; ++i) {
                     const float eA = ex2(zr[i]), eB = ex2(zi[i]), eC = ex2(-zi[i]);
+                    // users in pairs with packed FMAs (same operations and order as the scalar tail)
 #pragma unroll
-                    for (int k = 0; k < KH; ++k) {
-                        acc1[i][k] = fmaf(gm1[k], eA, fmaf(gm2[k], eC, acc1[i][k]));
-                        acc2[i][k] = fmaf(gm1[k], eB, fmaf(gm2[k], eA, acc2[i][k]));
+                    for (int k = 0; k + 1 < KH; k += 2) {
+                        fma2_pair(acc1[i][k], acc1[i][k + 1], gm2[k], gm2[k + 1], eC);
+                        fma2_pair(acc1[i][k], acc1[i][k + 1], gm1[k], gm1[k + 1], eA);
+                        fma2_pair(acc2[i][k], acc2[i][k + 1], gm2[k], gm2[k + 1], eA);
+                        fma2_pair(acc2[i][k], acc2[i][k + 1], gm1[k], gm1[k + 1], eB);
+                    }
+                    if constexpr (KH % 2) {
+                        acc1[i][KH - 1] = fmaf(gm1[KH - 1], eA, fmaf(gm2[KH - 1], eC, acc1[i][KH - 1]));
+                        acc2[i][KH - 1] = fmaf(gm1[KH - 1], eB, fmaf(gm2[KH - 1], eA, acc2[i][KH - 1]));
                     }
                 }
             }

@@ -131,14 +131,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Packed FP32 pair FMA (Blackwell): (d0, d1) = (a0 * b + d0, a1 * b + d1), each lane an IEEE
-// fma with one rounding, so results equal two fmaf calls bit for bit in half the instructions.
-__device__ __forceinline__ void fma2_bcast(float &d0, float &d1, float a0, float a1, float b) {
-    asm("{\n\t.reg .b64 d, a, b;\n\t"
-        "mov.b64 d, {%0, %1};\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %4};\n\t"
-        "fma.rn.f32x2 d, a, b, d;\n\tmov.b64 {%0, %1}, d;\n\t}"
-        : "+f"(d0), "+f"(d1)
-        : "f"(a0), "f"(a1), "f"(b));
+// Packed FP32 pair add: (x0, x1) += b, each lane one IEEE add.
+__device__ __forceinline__ void add2_bcast(float &x0, float &x1, float b) {
+    asm("{\n\t.reg .b64 x, b;\n\t"
+        "mov.b64 x, {%0, %1};\n\tmov.b64 b, {%2, %2};\n\t"
+        "add.rn.f32x2 x, x, b;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(x0), "+f"(x1)
+        : "f"(b));
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -512,22 +511,26 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
             const float *hh = sH + st * E;
 #pragma unroll 1
             for (int c = 0; c < NB / 16; ++c) {
-                float v[16];
+                float v[16], hv[8];
                 tmem_ld16(tmem + lane_base + (uint32_t)(st * NB + 16 * c), v);
+                *reinterpret_cast<float4 *>(hv) = *reinterpret_cast<const float4 *>(hh + 8 * c);
+                *reinterpret_cast<float4 *>(hv + 4) = *reinterpret_cast<const float4 *>(hh + 8 * c + 4);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const int e = 8 * c + j;
-                    const float h = hh[e] + hq;
-                    const float eA = ex2(v[2 * j] + h), eB = ex2(v[2 * j + 1] + h), eC = ex2(h - v[2 * j + 1]);
+                    const float h = hv[j] + hq;
+                    float xA = v[2 * j], xB = v[2 * j + 1];
+                    add2_bcast(xA, xB, h);  // (Re z + h, Im z + h)
+                    const float eA = ex2(xA), eB = ex2(xB), eC = ex2(h - v[2 * j + 1]);
                     float g1[KB], gg[KB];
                     load_coef<KB>(g + e * 2 * KB, g1, gg);
                     // acc1 = g1 E_A + g2 E_C + acc1,  acc2 = g1 E_B + g2 E_A + acc2, users in pairs
 #pragma unroll
                     for (int k = 0; k < KB; k += 2) {
-                        fma2_bcast(acc1[k], acc1[k + 1], gg[k], gg[k + 1], eC);
-                        fma2_bcast(acc1[k], acc1[k + 1], g1[k], g1[k + 1], eA);
-                        fma2_bcast(acc2[k], acc2[k + 1], gg[k], gg[k + 1], eA);
-                        fma2_bcast(acc2[k], acc2[k + 1], g1[k], g1[k + 1], eB);
+                        fma2_pair(acc1[k], acc1[k + 1], gg[k], gg[k + 1], eC);
+                        fma2_pair(acc1[k], acc1[k + 1], g1[k], g1[k + 1], eA);
+                        fma2_pair(acc2[k], acc2[k + 1], gg[k], gg[k + 1], eA);
+                        fma2_pair(acc2[k], acc2[k + 1], g1[k], g1[k + 1], eB);
                     }
                 }
             }
