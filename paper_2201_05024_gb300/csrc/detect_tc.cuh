@@ -16,9 +16,11 @@
 //            hi = tf32(x), lo = tf32(x - hi) (relative error of the Gram ~2^-21);
 //   kHalf    one BF16 or FP16 product per k-step (runtime choice), FP32 accumulation.
 //
-// Roles (256 threads): warps 0-3 = epilogue (query row = thread), warps 4-7 = converters
-// (entry rows of B and the tile's coefficients; thread 128 issues the MMAs).  Two smem stages
-// of B / coefficients and two TMEM accumulators: the converters and the tensor core work on
+// Roles (256 threads): warps 0-3 = epilogue (query row = thread; coefficient sums over user
+// pairs with packed f32x2 FMAs), warps 4-7 = converters (entry rows of B by whole 16-byte core
+// rows where M allows, the tile's coefficients and norms; thread 128 issues the MMAs; the next
+// tile's global loads are issued before the wait for its stage).  Two smem stages of
+// B / coefficients and two TMEM accumulators: the converters and the tensor core work on
 // tile i+1 while the epilogue reads tile i.  All waits are bounded.
 #pragma once
 
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
 
     if (warp >= 4) {
         // ================= converters + MMA issue =================
-        const int ct = tid - 128;  // B row of this thread: entry ct/2, half ct%2
+        const int ct = tid - 128;  // converter index (element-wise form: B row ct = entry ct/2, half ct%2)
         // global loads of a tile issued ahead of the wait for its stage (whole-core-row form)
         constexpr bool kVecG = (2 * KB) % 4 == 0;
         constexpr int kQ = 2 * KB / 4, kGQ = (E * kQ + 127) / 128;
