@@ -277,6 +277,14 @@ apsm_status apsm_batch_destroy(apsm_batch b);
  * Returns APSM_ERR_CUDA if the synchronisation fails. */
 apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream);
 
+/* Failure-detection self-check.  Enqueues on `stream` one CTA that waits, through the same bounded
+ * mbarrier wait every kernel of the library uses, on a barrier that no thread ever arrives at.
+ * The wait gives up after the library's wait budget (about two seconds of SM clock), the kernel
+ * writes APSM_ERR_TIMEOUT to the state's status word (meta[3]) and returns, so that the context
+ * stays usable: apsm_read_status() then reports APSM_ERR_TIMEOUT.  Nothing else of the state is
+ * touched.  Returns APSM_ERR_INVALID_ARG for a null state, APSM_ERR_CUDA if the launch fails. */
+apsm_status apsm_check_wait_timeout(const apsm_state *st, void *stream);
+
 /* Static description of a status code. */
 const char *apsm_status_string(apsm_status s);
 

@@ -67,6 +67,7 @@ def load_library(path: str | None = None):
         lib.apsm_train.argtypes = [P, vp, vp, ctypes.c_int32, vp, S, vp, ctypes.c_size_t, vp, vp]
         lib.apsm_detect.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp]
         lib.apsm_read_status.argtypes = [S, ctypes.POINTER(ctypes.c_int32), vp]
+        lib.apsm_check_wait_timeout.argtypes = [S, vp]
         lib.apsm_state_set.argtypes = [P, vp, vp, vp, ctypes.c_int32, S, vp]
         lib.apsm_detect_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_detect_backward.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
@@ -85,7 +86,7 @@ def load_library(path: str | None = None):
                   "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
                   "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
                   "apsm_train_backward_workspace_bytes", "apsm_train_backward",
-                  "apsm_batch_launch", "apsm_batch_destroy"):
+                  "apsm_batch_launch", "apsm_batch_destroy", "apsm_check_wait_timeout"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -425,6 +426,14 @@ def read_status(state: State) -> int:
     st = state.c()
     _check(lib.apsm_read_status(ctypes.byref(st), ctypes.byref(out), _stream()), "apsm_read_status")
     return out.value
+
+
+def check_wait_timeout(state: State) -> None:
+    """apsm_check_wait_timeout: enqueue the bounded-wait self-check, which leaves APSM_ERR_TIMEOUT
+    in the state's status word (read it with read_status) after about two seconds."""
+    lib = load_library()
+    st = state.c()
+    _check(lib.apsm_check_wait_timeout(ctypes.byref(st), _stream()), "apsm_check_wait_timeout")
 
 
 def launch_count() -> int:

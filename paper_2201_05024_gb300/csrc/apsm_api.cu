@@ -253,6 +253,20 @@ BwdGeom bwd_geom(const apsm_params *p, int N) {
     return b;
 }
 
+// Failure-detection self-check: one CTA waits on an mbarrier that no thread arrives at (its
+// phase 0 never completes), through the bounded wait of every kernel; when the wait budget runs
+// out the status word gets APSM_ERR_TIMEOUT and the CTA returns.
+__global__ void wait_timeout_check_kernel(int *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the initialisation is visible before any thread waits
+    const bool done = mbar_wait_bounded(&bar, 0);
+    if (!done && threadIdx.x == 0) report(status, APSM_ERR_TIMEOUT);
+}
+
 }  // namespace
 }  // namespace apsm
 
@@ -587,6 +601,14 @@ apsm_status apsm_tune_clear(void) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     std::memset(g_tune, 0, sizeof(g_tune));
     return APSM_OK;
+}
+
+apsm_status apsm_check_wait_timeout(const apsm_state *st, void *stream) {
+    if (!st || !st->meta) return APSM_ERR_INVALID_ARG;
+    apsm_status s = check_device();
+    if (s != APSM_OK) return s;
+    wait_timeout_check_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(st->meta + 3);
+    return cudaGetLastError() == cudaSuccess ? APSM_OK : APSM_ERR_CUDA;
 }
 
 apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream) {

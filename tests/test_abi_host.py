@@ -93,6 +93,7 @@ def test_null_pointers_rejected_before_device(lib):
     assert lib.apsm_train(ctypes.byref(p), ctypes.c_void_p(256), ctypes.c_void_p(256), 64, None,
                           ctypes.byref(_cstate()), ctypes.c_void_p(256), 16, None, None) == apsm.APSM_ERR_WORKSPACE
     assert lib.apsm_read_status(None, None, None) == 1
+    assert lib.apsm_check_wait_timeout(None, None) == 1
 
 
 def test_misaligned_arrays_rejected_before_device(lib):
