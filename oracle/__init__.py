@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int), ("K", ctypes.c_int), ("W", ctypes.c_int), ("D", ctypes.c_int),
                 ("sigma", ctypes.c_double), ("mu", ctypes.c_double), ("eps", ctypes.c_double),
-                ("w_L", ctypes.c_double)]
+                ("w_L", ctypes.c_double), ("qam_bits", ctypes.c_int), ("weights", ctypes.c_int)]
 
 
 def _load():
@@ -59,7 +59,9 @@ def _load():
             lib.apsm_oracle_train.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, ctypes.c_int, dp, dp,
                                               dp, ctypes.c_int, ctypes.c_int, dp, dp,
                                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p, dp,
-                                              ctypes.c_void_p]
+                                              ctypes.c_void_p, ctypes.c_int, dp, dp]
+            lib.apsm_oracle_pam_slice.restype = ctypes.c_double
+            lib.apsm_oracle_pam_slice.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
             lib.apsm_oracle_eval.restype = None
             lib.apsm_oracle_eval.argtypes = [ctypes.POINTER(_Params), ctypes.c_int, dp, dp, dp,
                                              ctypes.c_int, ctypes.c_int, dp, dp]
@@ -99,9 +101,12 @@ class Params:
     mu: float = 0.5
     eps: float = 0.01
     w_L: float = 0.5
+    qam_bits: int = 2     # Gray square QAM of decided targets: 2 (QPSK), 4 (16-QAM), 6 (64-QAM)
+    weights: int = 0      # 0: q_j = 1/|J_n|; 1: q_j = 1/|V_n| on the violated slabs V_n
 
     def c(self) -> _Params:
-        return _Params(self.M, self.K, self.W, self.D, self.sigma, self.mu, self.eps, self.w_L)
+        return _Params(self.M, self.K, self.W, self.D, self.sigma, self.mu, self.eps, self.w_L, self.qam_bits,
+                       self.weights)
 
 
 @dataclass
@@ -119,14 +124,20 @@ def default_threads() -> int:
 
 
 def train(p: Params, rx_pilot, sym_pilot, *, n_steps: int = -1, w0=None, threads: int | None = None,
-          log_cases: bool = False, forced=None):
-    """Run the APSM recurrence (Eq. apsm, Eq. beta) over the pilots; users run on parallel threads.
+          log_cases: bool = False, forced=None, decide_from: int | None = None, return_io: bool = False):
+    """Run the APSM recurrence (Eq. apsm, Eq. beta) over the vectors; users run on parallel threads.
 
-    Returns State, plus (case_log [n][W][K] int8, margin_log [n][W][K]) when log_cases."""
+    decide_from: real-split samples n >= decide_from take the decision Q(f_n(x_n)) as their
+    target instead of sym_pilot (decision-directed tracking; sym_pilot may then be None for
+    decide_from = 0).  Returns State, then (pred [P][K] complex, target [P][K] complex) when
+    return_io -- the filter's output at each vector's arrival and the targets trained on -- then
+    (case_log [n][W][K] int8, margin_log [n][W][K]) when log_cases."""
     lib = _load()
     P = int(np.asarray(rx_pilot).shape[0])
     ns = 2 * P if n_steps < 0 else min(int(n_steps), 2 * P)
     rx = _cplx_to_f64(rx_pilot).reshape(P, p.M, 2)
+    if sym_pilot is None:
+        sym_pilot = np.zeros((P, p.K), np.complex128)
     sy = _cplx_to_f64(sym_pilot).reshape(P, p.K, 2)
     L = 2 * p.M
     w_out = np.zeros((p.K, L))
@@ -135,6 +146,9 @@ def train(p: Params, rx_pilot, sym_pilot, *, n_steps: int = -1, w0=None, threads
     w0a = None if w0 is None else _f64(w0).reshape(p.K, L)
     cl = np.full((max(ns, 1), p.W, p.K), 127, dtype=np.int8) if log_cases else None
     ml = np.full((max(ns, 1), p.W, p.K), np.nan) if log_cases else None
+    pred = np.zeros((max(P, 1), p.K, 2)) if return_io else None
+    tgt = np.zeros((max(P, 1), p.K, 2)) if return_io else None
+    dfrom = 2 * P if decide_from is None else int(decide_from)
     fo = None
     if forced is not None:
         fo = np.ascontiguousarray(forced, dtype=np.int8)
@@ -148,7 +162,7 @@ def train(p: Params, rx_pilot, sym_pilot, *, n_steps: int = -1, w0=None, threads
         rc = lib.apsm_oracle_train(ctypes.byref(pc), P, ns, _dp(rx), _dp(sy), _dp(w0a), k0, k1, _dp(w_out),
                                    _dp(g_out), alive.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                                    cl.ctypes.data if cl is not None else None, _dp(ml),
-                                   fo.ctypes.data if fo is not None else None)
+                                   fo.ctypes.data if fo is not None else None, dfrom, _dp(pred), _dp(tgt))
         if rc != 0:
             raise ValueError("oracle train rejected its arguments")
 
@@ -161,9 +175,12 @@ def train(p: Params, rx_pilot, sym_pilot, *, n_steps: int = -1, w0=None, threads
     ent = np.asarray(rx_pilot)[first:first + n_ent]
     st = State(centres=centres_from_entries(p.M, ent), gamma=g_out[:2 * n_ent].copy(), w=w_out,
                first_entry=first, n_entries=n_ent)
+    out = [st]
+    if return_io:
+        out.append((pred[:P, :, 0] + 1j * pred[:P, :, 1], tgt[:P, :, 0] + 1j * tgt[:P, :, 1]))
     if log_cases:
-        return st, cl[:ns], ml[:ns]
-    return st
+        out.extend([cl[:ns], ml[:ns]])
+    return out[0] if len(out) == 1 else tuple(out)
 
 
 def centres_from_entries(M: int, entries) -> np.ndarray:
@@ -249,10 +266,63 @@ def detect_grad(p: Params, st: State, rx, dsoft, threads: int | None = None):
     return dg, dw, float(ds[0]), float(ds[1])
 
 
+def pam_scale(bits: int) -> float:
+    """Amplitude unit a of one axis of a unit-energy Gray square QAM with 2^bits points:
+    levels (2i - (L-1)) a, L = 2^(bits/2), mean energy 2 a^2 (L^2 - 1)/3 = 1."""
+    L = 1 << (bits // 2)
+    return float(np.sqrt(3.0 / (2.0 * (L * L - 1))))
+
+
+def pam_level(y, bits: int) -> np.ndarray:
+    """Nearest amplitude level index of one QAM axis: the number of decision boundaries
+    (2i - L) a, i = 1..L-1, at or below y (on a boundary: the upper level; exactly 0 counts as
+    non-negative)."""
+    L = 1 << (bits // 2)
+    a = pam_scale(bits)
+    y = np.asarray(y, np.float64)
+    lev = np.zeros(y.shape, np.int64)
+    for b in range(1, L):
+        lev += (y >= (2.0 * b - L) * a)
+    return lev
+
+
+def gray_axis(level, bits: int) -> np.ndarray:
+    """Gray label of one axis: the level counted from the top (so that a positive amplitude of
+    QPSK is bit 0), Gray coded: g = u ^ (u >> 1) with u = L - 1 - level."""
+    u = (1 << (bits // 2)) - 1 - np.asarray(level, np.int64)
+    return u ^ (u >> 1)
+
+
+def hard_qam(soft, bits: int = 2) -> np.ndarray:
+    """Gray square-QAM decision: label = gray(Re axis) | gray(Im axis) << (bits/2)."""
+    soft = np.asarray(soft)
+    gi = gray_axis(pam_level(soft.real, bits), bits)
+    gq = gray_axis(pam_level(soft.imag, bits), bits)
+    return (gi | (gq << (bits // 2))).astype(np.uint8)
+
+
 def hard_qpsk(soft) -> np.ndarray:
     """Gray QPSK decision: bit0 = (Re < 0), bit1 = (Im < 0); exactly 0 counts as non-negative."""
-    soft = np.asarray(soft)
-    return ((soft.real < 0).astype(np.uint8) | ((soft.imag < 0).astype(np.uint8) << 1))
+    return hard_qam(soft, 2)
+
+
+def pam_slice(y: float, bits: int):
+    """The C oracle's slicer (used by its decision-directed targets): (decided value, level)."""
+    lev = ctypes.c_int()
+    v = _load().apsm_oracle_pam_slice(float(y), int(bits), ctypes.byref(lev))
+    return v, lev.value
+
+
+def linear_filter(rx_pilot, sym_pilot, noise_var: float):
+    """Conventional linear detector from the pilots (the linear start of Sec. I / Sec. II-D,
+    f_0 = a linear filter): least-squares channel estimate H = Y S^H (S S^H)^-1 from the received
+    pilots Y [M][P] and pilot symbols S [K][P], then the MMSE filter W = H (H^H H + N0 I)^-1 (ZF
+    for N0 = 0), whose soft estimates are W^H r.  FP64 (numpy solves).  Returns W [M][K]."""
+    Y = np.asarray(rx_pilot, np.complex128).T
+    S = np.asarray(sym_pilot, np.complex128).T
+    H = np.linalg.solve((S @ S.conj().T).T, (Y @ S.conj().T).T).T     # Y S^H (S S^H)^-1
+    K = S.shape[0]
+    return H @ np.linalg.inv(H.conj().T @ H + noise_var * np.eye(K))
 
 
 def state_from_arrays(M: int, entries, gamma_entry, clin) -> State:

@@ -20,7 +20,7 @@
  * Readings of points the paper leaves open (each is a parameter or a choice
  * made once here):
  *   - relaxation mu multiplies the projection step (mu = 1 is Eq. apsm as printed);
- *   - weights q_j are uniform, 1/|J_n|;
+ *   - weights q_j are uniform, 1/|J_n|, unless the violated-slab weighting below is chosen;
  *   - W counts real-split samples n (Sec. II-D index);
  *   - the Gaussian dictionary holds at most D entries, one entry per complex
  *     pilot r(t) carrying both centres x_{2t}, x_{2t+1}; when full, the oldest
@@ -31,7 +31,16 @@
  *   - f_0 has no Gaussian part; its linear part w0 is given (zero by default);
  *   - w_G = 1 - w_L;
  *   - kappa(x_j, x_j) = 0 (only possible when w_L = 1 and x_j = 0) gives beta = 0;
- *   - |e| == eps lies inside the hyperslab (Eq. beta, middle case).
+ *   - |e| == eps lies inside the hyperslab (Eq. beta, middle case);
+ *   - adaptive weights (Sec. II-D leaves q_j free beyond q_j >= 0, sum q_j = 1): either
+ *     uniform over the window, or uniform over the violated slabs V_n = {j in J_n : |e_j| > eps}
+ *     and 0 elsewhere (no update when V_n is empty);
+ *   - decision-directed targets (Sec. II-D, tracking through the data symbols): a sample's
+ *     target is the decision on the filter's own output at its arrival, b_n = Q(f_n(x_n)), with
+ *     Q the slicer of one real axis of a Gray square QAM (each real-split sample carries one
+ *     axis of the complex symbol);
+ *   - continuing a trained filter on further vectors is the same recurrence over the
+ *     concatenated sequence, so it needs no separate definition here.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -46,7 +55,26 @@ typedef struct {
     double mu;      /* relaxation of the concurrent projection step           */
     double eps;     /* hyperslab half-width epsilon (Eq. convex_set)          */
     double w_L;     /* weight of the linear kernel; w_G = 1 - w_L (Fact 1)    */
+    int qam_bits;   /* Gray square QAM of decided targets: 2 (QPSK), 4, 6 bits */
+    int weights;    /* 0: q_j = 1/|J_n|;  1: q_j = 1/|V_n| on violated slabs  */
 } apsm_oracle_params;
+
+/* One real axis of a Gray square QAM with 2^bits points and unit mean energy: L = 2^(bits/2)
+ * amplitude levels (2i - (L-1)) a, i = 0..L-1, a = sqrt(3 / (2 (L^2 - 1))), separated by the
+ * decision boundaries (2i - L) a, i = 1..L-1.  The slicer returns the nearest level: its index
+ * is the number of boundaries at or below y (a value on a boundary takes the upper level; for
+ * QPSK this is the sign test with 0 counting as non-negative); it writes the index to *level
+ * when level is not NULL. */
+double apsm_oracle_pam_slice(double y, int bits, int *level)
+{
+    const int L = 1 << (bits / 2);
+    const double a = sqrt(3.0 / (2.0 * ((double)L * L - 1.0)));
+    int i = 0;
+    for (int b = 1; b < L; ++b)
+        if (y >= (2.0 * b - L) * a) i += 1;
+    if (level) *level = i;
+    return (2.0 * i - (L - 1)) * a;
+}
 
 /* Real split of one complex vector r (interleaved re,im, length M) -- Sec. II-D. */
 static void real_split(int M, const double *r, double *x1, double *x2)
@@ -149,13 +177,19 @@ void apsm_oracle_detect(const apsm_oracle_params *p, int n_c, const double *cent
  *          margin_log [n_steps][W][K] (nullable) | |e| - eps |;
  *          forced [n_steps][W][K]   (nullable) a value in {-1, 0, 1} forces that case for the slot
  *                                   (replay of a run that took another branch at a tie); any other
- *                                   value leaves the slot free.
+ *                                   value leaves the slot free;
+ *          decide_from              samples n >= decide_from take the decision b_n = Q(f_n(x_n))
+ *                                   as their target (sym is not read for them); n_steps or more:
+ *                                   every target comes from sym;
+ *          pred_out [P][K][2]       (nullable) f_n(x_n) at each sample's arrival n = 2t + l;
+ *          target_out [P][K][2]     (nullable) the target each sample was trained on.
  * Returns 0, or -1 on invalid arguments / allocation failure.
  */
 int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const double *rx,
                       const double *sym, const double *w0, int k0, int k1, double *w_out,
                       double *gamma_out, int *alive_out, signed char *case_log,
-                      double *margin_log, const signed char *forced)
+                      double *margin_log, const signed char *forced, int decide_from,
+                      double *pred_out, double *target_out)
 {
     const int M = p->M, L = 2 * M, K = p->K, W = p->W, D = p->D;
     if (M < 1 || K < 1 || W < 1 || D < 1 || P < 0 || 2 * D <= W || p->sigma <= 0.0) return -1;
@@ -166,7 +200,9 @@ int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const dou
     double *x = (double *)malloc(sizeof(double) * (size_t)(2 * P + 1) * L);
     double *g = (double *)malloc(sizeof(double) * (size_t)(2 * P + 1));
     double *beta = (double *)malloc(sizeof(double) * (size_t)W);
-    if (!x || !g || !beta) { free(x); free(g); free(beta); return -1; }
+    double *tgt = (double *)malloc(sizeof(double) * (size_t)(2 * P + 1));
+    int *cs_win = (int *)malloc(sizeof(int) * (size_t)W);
+    if (!x || !g || !beta || !tgt || !cs_win) { free(x); free(g); free(beta); free(tgt); free(cs_win); return -1; }
     for (int t = 0; t < P; ++t)
         real_split(M, rx + (size_t)t * 2 * M, x + (size_t)(2 * t) * L, x + (size_t)(2 * t + 1) * L);
 
@@ -186,13 +222,18 @@ int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const dou
             const int c_lo = 2 * first, c_hi = 2 * t + 2;   /* alive centres [c_lo, c_hi) */
             const int j0 = (n >= W - 1) ? n - W + 1 : 0;   /* J_n = [j0, n] */
             const int nJ = n - j0 + 1;
-            const double q = 1.0 / (double)nJ;
             /* All projections of this step are taken from the same f_n (Eq. apsm). */
             for (int j = j0; j <= n; ++j) {
                 const double *xj = x + (size_t)j * L;
-                const double bj = sym[((size_t)(j / 2) * K + k) * 2 + (j % 2)];
                 const double y = eval_f(L, w, c_hi - c_lo, x + (size_t)c_lo * L, g + c_lo, 1, xj,
                                         p->sigma, p->w_L);
+                if (j == n) {   /* the sample arrives: its target is given or decided now */
+                    tgt[n] = (n >= decide_from) ? apsm_oracle_pam_slice(y, p->qam_bits, NULL)
+                                                : sym[((size_t)(n / 2) * K + k) * 2 + (n % 2)];
+                    if (pred_out) pred_out[((size_t)(n / 2) * K + k) * 2 + (n % 2)] = y;
+                    if (target_out) target_out[((size_t)(n / 2) * K + k) * 2 + (n % 2)] = tgt[n];
+                }
+                const double bj = tgt[j];
                 const double e = y - bj;
                 const double kjj = p->w_L * kappa_lin(L, xj, xj) + w_G;   /* kappa(r_j, r_j) */
                 int cs = (e < -p->eps) ? -1 : (e > p->eps ? 1 : 0);
@@ -205,11 +246,20 @@ int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const dou
                     else if (cs > 0) b = (bj - y + p->eps) / kjj;
                 }
                 beta[j - j0] = b;
+                cs_win[j - j0] = cs;
                 if (case_log) case_log[li] = (signed char)cs;
                 if (margin_log) margin_log[li] = fabs(fabs(e) - p->eps);
             }
-            /* f_{n+1} = f_n + mu sum_j q beta_j kappa(x_j, .): coefficient of centre j and the
-             * linear dictionary (Sec. II-D: kappa_L(x_j, .) = sum_m [x_j]_m kappa_L(e_m, .)). */
+            /* weights q_j: uniform over J_n, or uniform over the violated slabs of J_n */
+            double q = 1.0 / (double)nJ;
+            if (p->weights == 1) {
+                int nv = 0;
+                for (int j = j0; j <= n; ++j) nv += (cs_win[j - j0] != 0);
+                q = nv > 0 ? 1.0 / (double)nv : 0.0;
+            }
+            /* f_{n+1} = f_n + mu sum_j q_j beta_j kappa(x_j, .): coefficient of centre j and the
+             * linear dictionary (Sec. II-D: kappa_L(x_j, .) = sum_m [x_j]_m kappa_L(e_m, .)).
+             * (beta_j = 0 wherever q_j = 0 in the violated-slab weighting.) */
             for (int j = j0; j <= n; ++j) {
                 const double a = p->mu * q * beta[j - j0];
                 g[j] += a;
@@ -234,6 +284,8 @@ int apsm_oracle_train(const apsm_oracle_params *p, int P, int n_steps, const dou
     free(x);
     free(g);
     free(beta);
+    free(tgt);
+    free(cs_win);
     return 0;
 }
 
