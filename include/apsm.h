@@ -70,7 +70,19 @@ typedef enum { APSM_FP32 = 0, APSM_BF16 = 1, APSM_FP16 = 2 } apsm_dtype;
  *   eps      hyperslab half-width epsilon >= 0 (Eq. convex_set).
  *   w_L      weight of the linear kernel in [0, 1]; the Gaussian weight is w_G = 1 - w_L.
  *   dtype    apsm_dtype of the detection contractions; training always runs in FP32.
+ *   modulation  bits per symbol of the Gray square QAM used for hard decisions and for the
+ *            decision-directed targets of apsm_train_continue: 2 (QPSK; 0 is read as 2), 4
+ *            (16-QAM) or 6 (64-QAM), unit mean energy (Sec. V, Fig. modulation).  One axis has
+ *            L = 2^(modulation/2) levels (2i - (L-1)) a, a = sqrt(3 / (2 (L^2 - 1))); the
+ *            decision is the number of boundaries (2i - L) a at or below the value (a value on a
+ *            boundary takes the upper level; QPSK: the sign, 0 counting as non-negative); the
+ *            label is the Gray code of (L-1-level) per axis, real axis in the low bits.
+ *   weights  APSM_Q_UNIFORM: q_j = 1/|J_n| over the window; APSM_Q_VIOLATED: q_j = 1/|V_n| over
+ *            the violated slabs V_n = {j in J_n : |e_j| > eps}, 0 elsewhere (Sec. II-D: the
+ *            weights may adaptively prioritise).  The adjoint supports APSM_Q_UNIFORM only.
  */
+typedef enum { APSM_Q_UNIFORM = 0, APSM_Q_VIOLATED = 1 } apsm_weights;
+
 typedef struct {
     int32_t M;
     int32_t K;
@@ -81,6 +93,8 @@ typedef struct {
     float eps;
     float w_L;
     int32_t dtype;
+    int32_t modulation;
+    int32_t weights;
 } apsm_params;
 
 /*
@@ -95,8 +109,12 @@ typedef struct {
  *                               that w_k^T r1 = Re(c_k^H r) and w_k^T r2 = Im(c_k^H r)
  *                               (unweighted: w_L is applied when evaluating).
  *   meta       [4] int32       [0] entries held, [1] slot of the oldest entry,
- *                               [2] pilots consumed, [3] device status (apsm_status code)
- * Slots at or beyond meta[0] are never read by the kernels.
+ *                               [2] vectors consumed, [3] device status (apsm_status code)
+ *   target     [A][K] complex  the target each held entry was trained on (its pilot symbol, or
+ *                               the decision taken in decision-directed mode); read when
+ *                               training continues, to carry the window across calls.
+ * Slot of the vector with running index t (counted over all training calls since the state was
+ * emptied) is t % D.  Slots at or beyond meta[0] are never read by the kernels.
  */
 typedef struct {
     float *dict;
@@ -104,6 +122,7 @@ typedef struct {
     float *gamma;
     float *clin;
     int32_t *meta;
+    float *target;
 } apsm_state;
 
 /* Number of dictionary slots A (>= dict_cap) the state arrays must hold. */
@@ -138,6 +157,55 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
                        const float *clin0, const apsm_state *st, void *workspace, size_t workspace_bytes,
                        int8_t *case_log, void *stream);
 
+/* Bytes of device workspace apsm_train_continue needs for P further vectors (any n_prev). */
+apsm_status apsm_train_continue_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes);
+
+/*
+ * Continue training a state on P further vectors (Eq. apsm / Eq. beta over the window J_n,
+ * Sec. II-D): the recurrence goes on from the state exactly as if these vectors had followed the
+ * earlier ones in one apsm_train call -- the window reaches back into the previous call's last
+ * samples (their targets are kept in st->target), the dictionary ring and its FIFO eviction go on.
+ * With sym == NULL the targets are decided (decision-directed tracking through the data symbols,
+ * Sec. II-D): the target of real-split sample n is the Gray-QAM decision (p->modulation) on the
+ * filter's own output at its arrival, b_n = Q(f_n(x_n)).
+ *   rx       device [P][M] complex    received vectors
+ *   sym      device [P][K] complex    their targets, or NULL for decision-directed targets
+ *   P        >= 0
+ *   n_prev   vectors the state has consumed so far (its meta[2]): the caller's count of every
+ *            vector trained on since the state was emptied (0 continues an empty Gaussian part
+ *            whose linear part is st->clin as it stands)
+ *   st       state, updated in place
+ *   workspace  apsm_train_continue_workspace_bytes(p, P) bytes, 256-byte aligned
+ *   soft     device [P][K] complex, or NULL: the filter's output at each vector's arrival,
+ *            f_{2t}(r1(t)) + i f_{2t+1}(r2(t)) (each half before its own projection; for tracking
+ *            these are the detector's outputs)
+ *   hard     device [P][K] uint8, or NULL: the Gray-QAM labels of the targets trained on (the
+ *            decisions, in decision-directed mode)
+ *   case_log as for apsm_train, for the P new vectors' steps.
+ * Errors as for apsm_train; APSM_ERR_INVALID_ARG also for n_prev < 0.
+ */
+apsm_status apsm_train_continue(const apsm_params *p, const float *rx, const float *sym, int32_t P, int32_t n_prev,
+                                const apsm_state *st, void *workspace, size_t workspace_bytes, float *soft,
+                                uint8_t *hard, int8_t *case_log, void *stream);
+
+/*
+ * Conventional linear start of the filter (Sec. I: start from a linear MMSE/ZF detector; f_0 is
+ * arbitrary in Eq. apsm).  From P pilots it forms the least-squares channel estimate
+ *   H = Y S^H (S S^H)^-1        (Y = [r(0) .. r(P-1)] M x P, S = pilot symbols K x P)
+ * and the MMSE filter W = H (H^H H + noise_var I)^-1 (zero-forcing for noise_var = 0), whose soft
+ * estimates are W^H r, and writes clin0 = W / w_L, so that the linear part of f_0 (weighted by
+ * w_L) detects exactly as W.  One CTA, FP32, fixed-order sums.
+ *   rx_pilot, sym_pilot  device, as for apsm_train; P >= K
+ *   noise_var            >= 0 (per receive antenna, relative to unit symbol energy)
+ *   clin0                device [M][K] complex output (pass it to apsm_train)
+ * Errors: APSM_ERR_INVALID_ARG (P < K, w_L = 0, noise_var < 0 or not finite, null or misaligned
+ * pointers), APSM_ERR_NOT_SM103, APSM_ERR_CUDA.  When S S^H or H^H H + noise_var I is not
+ * positive definite in FP32 (the pilot symbols do not span K independent directions) clin0 is
+ * set to zero.
+ */
+apsm_status apsm_linear_init(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                             float noise_var, float *clin0, void *stream);
+
 /*
  * apsm_train_noalloc -- apsm_train for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a deployment variant of apsm_train, not part of the
@@ -149,8 +217,10 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.
  *   - Training that needs more scratch than the array holds (apsm_train_workspace_bytes(p, P)
  *     > APSM_NOALLOC_SCRATCH_BYTES) is rejected with APSM_ERR_WORKSPACE before any work.
- *   - The first call on a device, with that device current, looks up the array's device
- *     address (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - The first call in a CUDA context (one per device in the usual case of the primary
+ *     context), with that device current, looks up the array's device address there
+ *     (cudaGetSymbolAddress) and caches it for that context, so a context created anew after
+ *     cudaDeviceReset gets a fresh lookup; make that first call before any stream capture.
  *   - All calls on a device share the one array, which keeps the last call's contents (the
  *     training writes every scratch word before reading it).  Calls whose GPU work overlaps --
  *     on different streams, or from different threads -- race on it: serialise them.
@@ -163,9 +233,15 @@ apsm_status apsm_train_noalloc(const apsm_params *p, const float *rx_pilot, cons
  * Detection (Sec. III-B, Fig. detection): for every data vector r and user k,
  *   soft[n][k] = f^k(r1) + i f^k(r2),
  *   f^k(x) = w_L <w_k, x> + w_G sum_{alive centres i} gamma_i^k kappa_G(c_i, x),
- * and the Gray QPSK decision hard[n][k] = (Re soft < 0) | (Im soft < 0) << 1 (an exact zero
- * counts as non-negative).  The number of alive entries is read from st->meta[0] on the device,
- * so a detection queued behind apsm_train on the same stream needs no host synchronisation.
+ * and the Gray square-QAM decision hard[n][k] of soft[n][k] (p->modulation; QPSK:
+ * (Re soft < 0) | (Im soft < 0) << 1, an exact zero counting as non-negative).  The number of
+ * alive entries is read from st->meta[0] on the device, so a detection queued behind apsm_train
+ * on the same stream needs no host synchronisation.
+ * The squared distances are formed from one complex inner product per (vector, entry) pair
+ * (norm expansion).  Where that cancels -- the smallest of a pair's three distances below
+ * theta k2 (||r||^2 + ||r_t||^2), theta = 2^-4 for BF16/FP16 contractions and 2^-12 for FP32 with
+ * inputs outside the factored range -- the pair's distances are recomputed by direct
+ * differences in FP32 (direct-difference fallback).
  *   rx    device [N][M] complex      data vectors
  *   N     >= 0
  *   soft  device [N][K] complex      output
@@ -223,12 +299,14 @@ apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, con
 
 /*
  * Load a given filter into a state (detection with fixed, externally trained coefficients):
- * entries [n][M] complex, gamma [n][2][K] and clin [M][K] complex, all DEVICE, in age order
- * (oldest first), 0 <= n <= dict_cap.  Writes slots 0..n-1, their norms ||r||^2, clin and
- * meta = {n, 0, n, 0}.  Same expansion as Sec. II-D: f^k = w_L <w_k, .> + w_G sum gamma kappa_G.
+ * entries [n][M] complex, gamma [n][2][K], clin [M][K] complex and target [n][K] complex (the
+ * entries' training targets, read only if training continues from this state; NULL: zero), all
+ * DEVICE, in age order (oldest first), 0 <= n <= dict_cap.  Writes slots 0..n-1, their norms
+ * ||r||^2, clin, the targets and meta = {n, 0, n, 0}, so that training can continue with
+ * n_prev = n.  Same expansion as Sec. II-D: f^k = w_L <w_k, .> + w_G sum gamma kappa_G.
  */
 apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,
-                           int32_t n, const apsm_state *st, void *stream);
+                           const float *target, int32_t n, const apsm_state *st, void *stream);
 
 /*
  * Detection launch choice for one class (M, K, dtype), set by the autotuner
@@ -273,8 +351,10 @@ apsm_status apsm_batch_create(const apsm_instance *inst, int32_t n, int32_t lane
 apsm_status apsm_batch_launch(apsm_batch b, void *stream);
 apsm_status apsm_batch_destroy(apsm_batch b);
 
-/* Synchronise `stream`, then copy meta[3] (the device status word) to *device_status and clear it.
- * Returns APSM_ERR_CUDA if the synchronisation fails. */
+/* Read and clear the device status word meta[3] in one atomic exchange enqueued on `stream`,
+ * then wait for `stream` and return the value read in *device_status.  A status that a kernel
+ * on another stream writes after the exchange stays for the next call.  Returns APSM_ERR_CUDA if
+ * the stream fails. */
 apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream);
 
 /* Failure-detection self-check.  Enqueues on `stream` one CTA that waits, through the same bounded
@@ -284,6 +364,18 @@ apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void 
  * stays usable: apsm_read_status() then reports APSM_ERR_TIMEOUT.  Nothing else of the state is
  * touched.  Returns APSM_ERR_INVALID_ARG for a null state, APSM_ERR_CUDA if the launch fails. */
 apsm_status apsm_check_wait_timeout(const apsm_state *st, void *stream);
+
+/*
+ * Process-wide launch options (not part of the method; every setting gives the same results up
+ * to FP32 rounding order):
+ *   APSM_OPT_TRAIN_CHUNK  pilots per training chunk (1..1024, default 64; shared memory may
+ *                         lower it further)
+ *   APSM_OPT_TRAIN_TRACK  1 (default): the next chunk's starting predictions are tracked during
+ *                         the current chunk; 0: they are evaluated between chunks (sequential)
+ * Returns APSM_ERR_INVALID_ARG for an unknown option or a value out of range.
+ */
+typedef enum { APSM_OPT_TRAIN_CHUNK = 0, APSM_OPT_TRAIN_TRACK = 1 } apsm_option;
+apsm_status apsm_set_option(int32_t option, int32_t value);
 
 /* Static description of a status code. */
 const char *apsm_status_string(apsm_status s);

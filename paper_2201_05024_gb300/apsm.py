@@ -21,6 +21,9 @@ APSM_OK, APSM_ERR_INVALID_ARG, APSM_ERR_UNSUPPORTED, APSM_ERR_CUDA, APSM_ERR_TIM
     APSM_ERR_NOT_SM103, APSM_ERR_WORKSPACE = range(7)
 APSM_FP32, APSM_BF16, APSM_FP16 = 0, 1, 2
 _DTYPES = {"fp32": APSM_FP32, "bf16": APSM_BF16, "fp16": APSM_FP16}
+APSM_Q_UNIFORM, APSM_Q_VIOLATED = 0, 1
+_WEIGHTS = {"uniform": APSM_Q_UNIFORM, "violated": APSM_Q_VIOLATED}
+_OPTIONS = {"train_chunk": 0, "train_track": 1}
 
 
 class ApsmError(RuntimeError):
@@ -32,12 +35,13 @@ class ApsmError(RuntimeError):
 class _CParams(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int32), ("K", ctypes.c_int32), ("window", ctypes.c_int32),
                 ("dict_cap", ctypes.c_int32), ("sigma", ctypes.c_float), ("mu", ctypes.c_float),
-                ("eps", ctypes.c_float), ("w_L", ctypes.c_float), ("dtype", ctypes.c_int32)]
+                ("eps", ctypes.c_float), ("w_L", ctypes.c_float), ("dtype", ctypes.c_int32),
+                ("modulation", ctypes.c_int32), ("weights", ctypes.c_int32)]
 
 
 class _CState(ctypes.Structure):
     _fields_ = [("dict", ctypes.c_void_p), ("dict_norm", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
-                ("clin", ctypes.c_void_p), ("meta", ctypes.c_void_p)]
+                ("clin", ctypes.c_void_p), ("meta", ctypes.c_void_p), ("target", ctypes.c_void_p)]
 
 
 class _CInstance(ctypes.Structure):
@@ -68,7 +72,12 @@ def load_library(path: str | None = None):
         lib.apsm_detect.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp]
         lib.apsm_read_status.argtypes = [S, ctypes.POINTER(ctypes.c_int32), vp]
         lib.apsm_check_wait_timeout.argtypes = [S, vp]
-        lib.apsm_state_set.argtypes = [P, vp, vp, vp, ctypes.c_int32, S, vp]
+        lib.apsm_state_set.argtypes = [P, vp, vp, vp, vp, ctypes.c_int32, S, vp]
+        lib.apsm_train_continue_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.apsm_train_continue.argtypes = [P, vp, vp, ctypes.c_int32, ctypes.c_int32, S, vp, ctypes.c_size_t, vp, vp,
+                                            vp, vp]
+        lib.apsm_linear_init.argtypes = [P, vp, vp, ctypes.c_int32, ctypes.c_float, vp, vp]
+        lib.apsm_set_option.argtypes = [ctypes.c_int32, ctypes.c_int32]
         lib.apsm_detect_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_detect_backward.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         i32 = ctypes.c_int32
@@ -86,7 +95,9 @@ def load_library(path: str | None = None):
                   "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
                   "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
                   "apsm_train_backward_workspace_bytes", "apsm_train_backward",
-                  "apsm_batch_launch", "apsm_batch_destroy", "apsm_check_wait_timeout"):
+                  "apsm_batch_launch", "apsm_batch_destroy", "apsm_check_wait_timeout",
+                  "apsm_train_continue_workspace_bytes", "apsm_train_continue", "apsm_linear_init",
+                  "apsm_set_option"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -116,10 +127,12 @@ class Params:
     eps: float = 0.01
     w_L: float = 0.5
     dtype: str = "fp32"
+    modulation: int = 2         # bits per Gray square-QAM symbol: 2 (QPSK), 4 (16-QAM), 6 (64-QAM)
+    weights: str = "uniform"    # q_j: "uniform" (1/|J_n|) or "violated" (1/|V_n| on violated slabs)
 
     def c(self) -> _CParams:
         return _CParams(self.M, self.K, self.window, self.dict_cap, self.sigma, self.mu, self.eps, self.w_L,
-                        _DTYPES[self.dtype])
+                        _DTYPES[self.dtype], self.modulation, _WEIGHTS[self.weights])
 
 
 def _ptr(t):
@@ -168,10 +181,12 @@ class State:
         self.gamma = torch.zeros((A, 2, p.K), dtype=torch.float32, device=device)
         self.clin = torch.zeros((p.M, p.K), dtype=torch.complex64, device=device)
         self.meta = torch.zeros((4,), dtype=torch.int32, device=device)
+        self.target = torch.zeros((A, p.K), dtype=torch.complex64, device=device)
+        self.n_vectors = 0   # host mirror of meta[2]: vectors trained on since the state was emptied
 
     def c(self) -> _CState:
         return _CState(self.dict.data_ptr(), self.dict_norm.data_ptr(), self.gamma.data_ptr(),
-                       self.clin.data_ptr(), self.meta.data_ptr())
+                       self.clin.data_ptr(), self.meta.data_ptr(), self.target.data_ptr())
 
     def entries(self):
         """(entries [n][M], gamma [n][2][K]) in age order (oldest first), copied to the host."""
@@ -202,7 +217,67 @@ def train(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, state: Sta
     _check(lib.apsm_train(ctypes.byref(p.c()), _ptr(rx_pilot), _ptr(sym_pilot), P, _ptr(clin0), ctypes.byref(st),
                           _ptr(workspace), nb if workspace is None else workspace.numel(), _ptr(case_log),
                           _stream()), "apsm_train")
+    state.n_vectors = P
     return state
+
+
+def train_continue_workspace_bytes(p: Params, P: int) -> int:
+    lib = load_library()
+    out = ctypes.c_size_t()
+    _check(lib.apsm_train_continue_workspace_bytes(ctypes.byref(p.c()), int(P), ctypes.byref(out)),
+           "apsm_train_continue_workspace_bytes")
+    return out.value
+
+
+def train_continue(p: Params, rx: torch.Tensor, state: State, sym: torch.Tensor | None = None, *,
+                   soft: torch.Tensor | None = None, hard: torch.Tensor | None = None, want_outputs: bool = True,
+                   workspace: torch.Tensor | None = None, case_log: torch.Tensor | None = None):
+    """apsm_train_continue: go on training `state` on the vectors rx [P][M] complex64, with targets
+    sym [P][K] (or decided at each vector's arrival when sym is None: decision-directed tracking).
+    Returns (soft [P][K] complex64 = the filter's output at each arrival, hard [P][K] uint8 = the
+    Gray-QAM labels of the targets) when want_outputs."""
+    lib = load_library()
+    P = int(rx.shape[0])
+    _dev(rx, torch.complex64, (P, p.M), "rx")
+    if sym is not None:
+        _dev(sym, torch.complex64, (P, p.K), "sym")
+    if want_outputs and soft is None:
+        soft = torch.empty((P, p.K), dtype=torch.complex64, device=rx.device)
+    if want_outputs and hard is None:
+        hard = torch.empty((P, p.K), dtype=torch.uint8, device=rx.device)
+    if soft is not None:
+        _dev(soft, torch.complex64, (P, p.K), "soft")
+    if hard is not None:
+        _dev(hard, torch.uint8, (P, p.K), "hard")
+    if case_log is not None:
+        _dev(case_log, torch.int8, (2 * P, p.window, p.K), "case_log")
+    nb = train_continue_workspace_bytes(p, P)
+    if workspace is None:
+        workspace = torch.empty((max(nb, 1),), dtype=torch.uint8, device=rx.device)
+    st = state.c()
+    _check(lib.apsm_train_continue(ctypes.byref(p.c()), _ptr(rx), _ptr(sym), P, state.n_vectors, ctypes.byref(st),
+                                   _ptr(workspace), workspace.numel(), _ptr(soft), _ptr(hard), _ptr(case_log),
+                                   _stream()), "apsm_train_continue")
+    state.n_vectors += P
+    return soft, hard
+
+
+def linear_init(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, noise_var: float) -> torch.Tensor:
+    """apsm_linear_init: clin0 [M][K] complex64 = W / w_L with W the MMSE filter (ZF for noise_var
+    0) of the least-squares channel estimate from the pilots; pass it to train(..., clin0=...)."""
+    lib = load_library()
+    P = int(rx_pilot.shape[0])
+    _dev(rx_pilot, torch.complex64, (P, p.M), "rx_pilot")
+    _dev(sym_pilot, torch.complex64, (P, p.K), "sym_pilot")
+    clin0 = torch.empty((p.M, p.K), dtype=torch.complex64, device=rx_pilot.device)
+    _check(lib.apsm_linear_init(ctypes.byref(p.c()), _ptr(rx_pilot), _ptr(sym_pilot), P, float(noise_var),
+                                _ptr(clin0), _stream()), "apsm_linear_init")
+    return clin0
+
+
+def set_option(name: str, value: int):
+    """apsm_set_option: process-wide launch options ("train_chunk", "train_track")."""
+    _check(load_library().apsm_set_option(_OPTIONS[name], int(value)), "apsm_set_option")
 
 
 def detect(p: Params, state: State, rx: torch.Tensor, *, soft: torch.Tensor | None = None,
@@ -224,17 +299,22 @@ def detect(p: Params, state: State, rx: torch.Tensor, *, soft: torch.Tensor | No
     return soft, hard
 
 
-def state_set(p: Params, state: State, entries: torch.Tensor, gamma: torch.Tensor, clin: torch.Tensor) -> State:
-    """apsm_state_set: load entries [n][M] complex64, gamma [n][2][K] float32 and clin [M][K]
-    complex64 (device tensors, age order) into `state`."""
+def state_set(p: Params, state: State, entries: torch.Tensor, gamma: torch.Tensor, clin: torch.Tensor,
+              target: torch.Tensor | None = None) -> State:
+    """apsm_state_set: load entries [n][M] complex64, gamma [n][2][K] float32, clin [M][K]
+    complex64 and optionally the entries' targets [n][K] complex64 (device tensors, age order)
+    into `state`."""
     lib = load_library()
     n = int(entries.shape[0])
     _dev(entries, torch.complex64, (n, p.M), "entries")
     _dev(gamma, torch.float32, (n, 2, p.K), "gamma")
     _dev(clin, torch.complex64, (p.M, p.K), "clin")
+    if target is not None:
+        _dev(target, torch.complex64, (n, p.K), "target")
     st = state.c()
-    _check(lib.apsm_state_set(ctypes.byref(p.c()), _ptr(entries), _ptr(gamma), _ptr(clin), n, ctypes.byref(st),
-                              _stream()), "apsm_state_set")
+    _check(lib.apsm_state_set(ctypes.byref(p.c()), _ptr(entries), _ptr(gamma), _ptr(clin), _ptr(target), n,
+                              ctypes.byref(st), _stream()), "apsm_state_set")
+    state.n_vectors = n
     return state
 
 
@@ -269,7 +349,8 @@ class DetectFunction(torch.autograd.Function):
     def forward(ctx, gamma, clin, sigma, w_L, p: Params, state: State, rx):
         q = Params(**{**p.__dict__, "sigma": float(sigma), "w_L": float(w_L)})
         st = State.__new__(State)
-        st.p, st.dict, st.dict_norm, st.meta = q, state.dict, state.dict_norm, state.meta
+        st.p, st.dict, st.dict_norm, st.meta, st.target = q, state.dict, state.dict_norm, state.meta, state.target
+        st.n_vectors = state.n_vectors
         st.gamma, st.clin = gamma.detach().contiguous(), clin.detach().contiguous()
         soft, _ = detect(q, st, rx, want_hard=False)
         ctx.q, ctx.st, ctx.rx = q, st, rx

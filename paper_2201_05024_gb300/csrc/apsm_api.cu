@@ -13,7 +13,6 @@
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "detect_tc.cuh"
-#include "detect_tc2.cuh"
 #include "train_f32.cuh"
 
 namespace apsm {
@@ -41,6 +40,9 @@ apsm_status check_params(const apsm_params *p) {
     if (2LL * p->dict_cap <= p->window) return APSM_ERR_INVALID_ARG;
     if (p->dtype != APSM_FP32 && p->dtype != APSM_BF16 && p->dtype != APSM_FP16) return APSM_ERR_INVALID_ARG;
     if (p->dict_cap > (1 << 26)) return APSM_ERR_INVALID_ARG;
+    if (p->modulation != 0 && p->modulation != 2 && p->modulation != 4 && p->modulation != 6)
+        return APSM_ERR_INVALID_ARG;
+    if (p->weights != APSM_Q_UNIFORM && p->weights != APSM_Q_VIOLATED) return APSM_ERR_INVALID_ARG;
     if (!supported_M(p->M) || p->K > 16 || p->window > 128) return APSM_ERR_UNSUPPORTED;
     return APSM_OK;
 }
@@ -48,7 +50,9 @@ apsm_status check_params(const apsm_params *p) {
 bool aligned16(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15) == 0; }
 
 apsm_status check_state(const apsm_state *st) {
-    if (!st || !st->dict || !st->dict_norm || !st->gamma || !st->clin || !st->meta) return APSM_ERR_INVALID_ARG;
+    if (!st || !st->dict || !st->dict_norm || !st->gamma || !st->clin || !st->meta || !st->target)
+        return APSM_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(st->target) & 7) return APSM_ERR_INVALID_ARG;
     // dictionary tiles are moved by the bulk-copy engine: 16-byte aligned sources
     if (!aligned16(st->dict) || !aligned16(st->dict_norm) || !aligned16(st->gamma)) return APSM_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(st->clin) & 7) || (reinterpret_cast<uintptr_t>(st->meta) & 3))
@@ -92,10 +96,9 @@ int num_sms() {
 constexpr int kMaxChunkThreads = 160;      // phase-B CTA size limit (S <= 5 warps)
 constexpr int kMaxSmemBytes = 227 * 1024;  // opt-in shared memory per CTA
 
-int env_int(const char *name, int dflt) {
-    const char *v = std::getenv(name);
-    return (v && *v) ? std::atoi(v) : dflt;
-}
+// ---- process-wide launch options (apsm_set_option) -------------------------------------------
+std::atomic<int> g_opt_train_chunk{64};  // pilots per training chunk
+std::atomic<int> g_opt_train_track{1};   // next-chunk tracking form (1) or sequential form (0)
 
 inline apsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APSM_OK : APSM_ERR_CUDA; }
 
@@ -130,35 +133,33 @@ TuneEntry tune_get(int M, int K, int dtype) {
 DetectShape detect_shape(int M, int K, int dtype) {
     const TuneEntry te = tune_get(M, K, dtype);
     if (te.set && te.engine == 1) return DetectShape{te.threads, te.split, te.qpt};
-    DetectShape s;
-    s.qpt = env_int("APSM_DETECT_QPT", 1);
-    if (s.qpt != 1 && s.qpt != 2) s.qpt = 1;
-    s.threads = env_int("APSM_DETECT_THREADS", 64);
-    if (s.threads < 32 || s.threads > 256 || s.threads % 32) s.threads = 64;
-    s.split = env_int("APSM_DETECT_SPLIT", 2);
-    if (s.split < 1 || s.split * s.threads > 256) s.split = 1;
-    return s;
+    return DetectShape{64, 2, 1};  // 64 query lanes x 2 entry groups, one query per lane
 }
 
 // ---- training geometry --------------------------------------------------------------------
-TrainGeom train_geom(const apsm_params *p, int P) {
+// Geometry of one training call: P new vectors after n_prev earlier ones (of which the last
+// nc0 = min(n_prev, W/2) pilots are carried, because the first new window reaches back into
+// them).  evict: -1 = decide from the counts, 0/1 = forced (workspace bounds over both cases).
+TrainGeom train_geom(const apsm_params *p, int P, int n_prev, int evict = -1) {
     TrainGeom g;
     g.M = p->M;
     g.K = p->K;
     g.W = p->window;
     g.D = p->dict_cap;
-    g.P = P;
+    g.nc0 = std::min(n_prev, g.W / 2);
+    g.t_base = n_prev - g.nc0;
+    g.P = g.nc0 + P;
+    g.evict = evict >= 0 ? evict : (g.t_base + g.P > g.D ? 1 : 0);
     // Entries dropped inside a chunk must be older than the chunk's live range, whose first pilot
     // is t0 - floor(W/2): D >= T + floor(W/2).  The same bound keeps a chunk's live range in the
     // dictionary at the next chunk's start (needed by the tracked form).
-    int T = env_int("APSM_TRAIN_CHUNK", 64);
-    if (T < 1) T = 64;
+    int T = g_opt_train_chunk.load();
     T = std::min(T, g.D - g.W / 2);
     T = std::min(T, (kMaxChunkThreads - g.W) / 2);  // one thread per live-range sample
     T = std::max(T, 1);
     g.WP = padded_window(g.W);
     g.slice = kTileEntries;
-    const bool want_track = env_int("APSM_TRAIN_TRACK", 1) != 0;
+    const bool want_track = g_opt_train_track.load() != 0;
     for (;; --T) {  // the largest chunk whose phase-B tables fit in shared memory
         g.T = T;
         g.RMAX = 2 * T + g.W;
@@ -173,13 +174,15 @@ TrainGeom train_geom(const apsm_params *p, int P) {
 }
 
 struct TrainWs {
-    size_t kmat, gev, kx, partial[2], track[2], carry, total;
-    int max_slices;
+    size_t kmat, gev, kx, partial[2], track[2], carry, ext_rx, ext_sym, total;
+    int max_slices, part_rows;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-TrainWs train_ws(const TrainGeom &g) {
+// Workspace layout; ext: room for the extended sequence (carried pilots + new vectors and their
+// targets) of a continuation or of decision-directed training.
+TrainWs train_ws(const TrainGeom &g, bool ext) {
     TrainWs w;
     size_t off = 0;
     w.kmat = off;
@@ -188,11 +191,13 @@ TrainWs train_ws(const TrainGeom &g) {
     off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.T * 2 * g.RS);
     w.kx = off;
     if (g.track) off = align256(off + sizeof(float) * (size_t)g.n_chunks * g.RS * g.KXS);
-    // slot segments of the frozen entries start at a tile boundary: up to two extra slices
+    // slot segments of the frozen entries start at a tile boundary: up to two extra slices; the
+    // first chunk of a continuation also evaluates its carried pilots (up to W/2 more rows)
     w.max_slices = (g.D + g.slice - 1) / g.slice + 2;
+    w.part_rows = g.T + g.W / 2;
     for (int i = 0; i < 2; ++i) {
         w.partial[i] = off;
-        if (i == 0 || g.track) off = align256(off + sizeof(float) * (size_t)w.max_slices * g.T * 2 * g.K);
+        if (i == 0 || g.track) off = align256(off + sizeof(float) * (size_t)w.max_slices * w.part_rows * 2 * g.K);
     }
     for (int i = 0; i < 2; ++i) {
         w.track[i] = off;
@@ -200,15 +205,55 @@ TrainWs train_ws(const TrainGeom &g) {
     }
     w.carry = off;
     off = align256(off + sizeof(float) * (size_t)g.W * g.K);
+    w.ext_rx = off;
+    if (ext) off = align256(off + sizeof(float2) * (size_t)g.P * g.M);
+    w.ext_sym = off;
+    if (ext) off = align256(off + sizeof(float2) * (size_t)g.P * g.K);
     w.total = g.n_chunks > 0 ? off : 0;
     return w;
 }
 
+// Workspace bound of a continuation of P vectors, whatever n_prev (carried pilots at most W/2,
+// with or without eviction).
+size_t continue_ws_bytes(const apsm_params *p, int P) {
+    const int n_prev = p->window / 2;  // the largest carried count
+    const size_t a = train_ws(train_geom(p, P, n_prev, 0), true).total;
+    const size_t b = train_ws(train_geom(p, P, n_prev, 1), true).total;
+    return std::max(a, b);
+}
+
+// The extended sequence of a training call: rows [0, nc0) are the carried pilots, read from
+// their dictionary slots with the targets they were trained on; rows [nc0, nc0 + P) are the new
+// vectors and their targets (zero when they are to be decided).
+__global__ void train_ext_kernel(const float2 *__restrict__ rx, const float2 *__restrict__ sym, int P, int nc0,
+                                 int t_base, int D, int M, int K, const float2 *__restrict__ dict,
+                                 const float2 *__restrict__ target, float2 *ext_rx, float2 *ext_sym) {
+    pdl_enter();
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    for (int i = tid; i < (nc0 + P) * M; i += nthr) {
+        const int e = i / M, m = i % M;
+        ext_rx[i] = e < nc0 ? dict[(size_t)((t_base + e) % D) * M + m] : rx[(size_t)(e - nc0) * M + m];
+    }
+    for (int i = tid; i < (nc0 + P) * K; i += nthr) {
+        const int e = i / K, k = i % K;
+        ext_sym[i] = e < nc0 ? target[(size_t)((t_base + e) % D) * K + k]
+                             : (sym ? sym[(size_t)(e - nc0) * K + k] : make_float2(0.f, 0.f));
+    }
+}
+
+int qam_half_of(const apsm_params *p) { return (p->modulation == 0 ? 2 : p->modulation) / 2; }
+float qam_a_of(const apsm_params *p) {
+    const int L = 1 << qam_half_of(p);
+    return (float)std::sqrt(3.0 / (2.0 * ((double)L * L - 1.0)));
+}
+
 __global__ void state_set_kernel(const float2 *__restrict__ entries, const float *__restrict__ gamma,
-                                 const float2 *__restrict__ clin, int n, int M, int K, float2 *dict, float *dict_norm,
-                                 float *gam_out, float2 *clin_out, int *meta) {
+                                 const float2 *__restrict__ clin, const float2 *__restrict__ target, int n, int M,
+                                 int K, float2 *dict, float *dict_norm, float *gam_out, float2 *clin_out,
+                                 float2 *tgt_out, int *meta) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     for (int i = tid; i < n * M; i += nthr) dict[i] = entries[i];
+    for (int i = tid; i < n * K; i += nthr) tgt_out[i] = target ? target[i] : make_float2(0.f, 0.f);
     for (int i = tid; i < n * 2 * K; i += nthr) gam_out[i] = gamma[i];
     for (int i = tid; i < M * K; i += nthr) clin_out[i] = clin[i];
     for (int t = tid; t < n; t += nthr) {
@@ -253,6 +298,12 @@ BwdGeom bwd_geom(const apsm_params *p, int N) {
     return b;
 }
 
+// apsm_read_status: the status word is exchanged with 0 and the old value parked in a
+// library-owned device slot, from which the host copies it.
+__device__ int32_t g_status_slot;
+std::mutex g_status_mu;
+__global__ void status_take_kernel(int *status) { g_status_slot = atomicExch(status, 0); }
+
 // Failure-detection self-check: one CTA waits on an mbarrier that no thread arrives at (its
 // phase 0 never completes), through the bounded wait of every kernel; when the wait budget runs
 // out the status word gets APSM_ERR_TIMEOUT and the CTA returns.
@@ -286,34 +337,35 @@ apsm_status apsm_train_workspace_bytes(const apsm_params *p, int32_t P, size_t *
     apsm_status s = check_params(p);
     if (s != APSM_OK) return s;
     if (!bytes || P < 0) return APSM_ERR_INVALID_ARG;
-    *bytes = train_ws(train_geom(p, P)).total;
+    *bytes = train_ws(train_geom(p, P, 0), false).total;
     return APSM_OK;
 }
 
-apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
-                       const float *clin0, const apsm_state *st, void *workspace, size_t workspace_bytes,
-                       int8_t *case_log, void *stream) {
+apsm_status apsm_train_continue_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes) {
     apsm_status s = check_params(p);
     if (s != APSM_OK) return s;
-    if ((s = check_state(st)) != APSM_OK) return s;
-    if (P < 0 || (P > 0 && (!rx_pilot || !sym_pilot))) return APSM_ERR_INVALID_ARG;
-    if (P > (1 << 26)) return APSM_ERR_INVALID_ARG;
-    if (P > 0 && (!aligned16(rx_pilot) || (reinterpret_cast<uintptr_t>(sym_pilot) & 7))) return APSM_ERR_INVALID_ARG;
-    if (clin0 && (reinterpret_cast<uintptr_t>(clin0) & 7)) return APSM_ERR_INVALID_ARG;
-    const TrainGeom g = train_geom(p, P);
-    const TrainWs ws = train_ws(g);
+    if (!bytes || P < 0) return APSM_ERR_INVALID_ARG;
+    *bytes = continue_ws_bytes(p, P);
+    return APSM_OK;
+}
+
+}  // extern "C"
+
+namespace apsm {
+namespace {
+
+// One training call (apsm_train: fresh = true, n_prev = 0; apsm_train_continue otherwise): P new
+// vectors rx with targets sym (NULL: decided at arrival) after n_prev earlier ones.
+apsm_status train_run(const apsm_params *p, const float *rx_in, const float *sym_in, int P, int n_prev,
+                      const apsm_state *st, void *workspace, size_t workspace_bytes, float *soft, uint8_t *hard,
+                      int8_t *case_log, cudaStream_t strm) {
+    const bool decide = sym_in == nullptr;
+    const TrainGeom g = train_geom(p, P, n_prev);
+    const bool ext = g.nc0 > 0 || decide;
+    const TrainWs ws = train_ws(g, ext);
     if (ws.total > 0 && (!workspace || workspace_bytes < ws.total)) return APSM_ERR_WORKSPACE;
     if (ws.total > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255)) return APSM_ERR_INVALID_ARG;
-    if ((s = check_device()) != APSM_OK) return s;
-    cudaStream_t strm = static_cast<cudaStream_t>(stream);
-
-    // f_0: linear part clin0 (or zero), empty Gaussian part
-    const size_t clin_bytes = sizeof(float) * 2 * (size_t)p->M * p->K;
-    cudaError_t ce = clin0 == nullptr ? cudaMemsetAsync(st->clin, 0, clin_bytes, strm)
-                     : clin0 != st->clin ? cudaMemcpyAsync(st->clin, clin0, clin_bytes, cudaMemcpyDeviceToDevice, strm)
-                                         : cudaSuccess;
-    if (ce != cudaSuccess) return APSM_ERR_CUDA;
-    if (P == 0) return cuda_status(cudaMemsetAsync(st->meta, 0, 3 * sizeof(int32_t), strm));
+    if (P == 0) return APSM_OK;
 
     unsigned char *wsb = static_cast<unsigned char *>(workspace);
     float *kmat = reinterpret_cast<float *>(wsb + ws.kmat);
@@ -324,11 +376,28 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
     float *carry = reinterpret_cast<float *>(wsb + ws.carry);
     const float k2 = k2_of(p->sigma);
     const float wL = p->w_L, wG = 1.f - p->w_L;
-    const float2 *rx = reinterpret_cast<const float2 *>(rx_pilot);
+    const float2 *rx = reinterpret_cast<const float2 *>(rx_in);
+    float2 *sym = const_cast<float2 *>(reinterpret_cast<const float2 *>(sym_in));  // written only when decided
+    if (ext) {  // the extended sequence: carried pilots (from their slots) + the new vectors
+        float2 *erx = reinterpret_cast<float2 *>(wsb + ws.ext_rx);
+        float2 *esym = reinterpret_cast<float2 *>(wsb + ws.ext_sym);
+        const int work = g.P * std::max(g.M, g.K);
+        const int blocks = std::max(1, std::min(2 * num_sms(), (work + 255) / 256));
+        if (launch_pdl(train_ext_kernel, dim3(blocks), dim3(256), 0, strm, rx, reinterpret_cast<const float2 *>(sym_in),
+                       P, g.nc0, g.t_base, g.D, g.M, g.K, reinterpret_cast<const float2 *>(st->dict),
+                       reinterpret_cast<const float2 *>(st->target), erx, esym) != cudaSuccess ||
+            cudaGetLastError() != cudaSuccess)
+            return APSM_ERR_CUDA;
+        g_launches++;
+        rx = erx;
+        sym = esym;
+    }
 
     {   // kernel values of every chunk's live range, of dropped entries against it, and against
         // the next chunk's samples
-        if (launch_train_gram(rx, g, k2, wL, wG, kmat, gev, kx, strm) != cudaSuccess) return APSM_ERR_CUDA;
+        if (launch_train_gram(rx, reinterpret_cast<const float2 *>(st->dict), g, k2, wL, wG, kmat, gev, kx, strm) !=
+            cudaSuccess)
+            return APSM_ERR_CUDA;
         g_launches++;
     }
 
@@ -338,14 +407,13 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
     const ChunkLauncher chunk = chunk_launcher(g.RS / 32, g.WP);
     if (!chunk) return APSM_ERR_UNSUPPORTED;
 
-    // phase A: the partial Gaussian sums of f at the start of chunk cq, at cq's pilots, over the
-    // dictionary slots [lo, lo + n) (mod D) -- the whole dictionary, or its frozen entries
-    auto phase_a = [&](int cq, int lo, int n, float *dst, int &n_slices, bool late) -> bool {
-        int t0, Tc, s0, s1, l0;
-        chunk_range(g, cq, t0, Tc, s0, s1, l0);
+    // phase A: the partial Gaussian sums of f, at the extended pilots [q0, q0 + nq), over the
+    // dictionary entries with running indices [lo, lo + n) (their slots mod D) -- the whole
+    // dictionary, or its frozen entries
+    auto phase_a = [&](int q0, int nq, int lo, int n, float *dst, int &n_slices, bool late) -> bool {
         DetectArgs da{};
-        da.rx = rx + (size_t)t0 * g.M;
-        da.N = Tc;
+        da.rx = rx + (size_t)q0 * g.M;
+        da.N = nq;
         da.dict = reinterpret_cast<const float2 *>(st->dict);
         da.dict_norm = st->dict_norm;
         da.gamma = st->gamma;
@@ -359,6 +427,8 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         da.partial = dst;
         da.pdl_late = late ? 1 : 0;
         da.status = st->meta + 3;
+        da.qam_half = 1;
+        da.qam_a = 1.f;
         const int first = lo % g.D, hi0 = std::min(g.D, first + n), hi1 = first + n - g.D;
         da.seg0_lo = first;
         da.seg0_hi = hi0;
@@ -371,24 +441,33 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         }
         da.seg_slices = ns0;
         n_slices = ns0 + ns1;
-        const int thr = std::min(256, round_up(Tc, 32));
+        const int thr = std::min(256, round_up(nq, 32));
         const DetectShape sh{thr, std::max(1, 256 / thr), 1};  // entry groups share each tile
         if (det(da, n_slices, sh, strm) != cudaSuccess) return false;
         g_launches++;
         return true;
     };
 
+    const int tb = g.t_base;
     int slices_of[2] = {0, 0};  // phase-A slices waiting in partial[c & 1]
     for (int c = 0; c < g.n_chunks; ++c) {
         int t0, Tc, s0, s1, l0;
         chunk_range(g, c, t0, Tc, s0, s1, l0);
-        int mode = 0;
-        if (!g.track) {
-            // f at the chunk start over the whole dictionary, between the chunks
-            const int n_alive = std::min(t0, g.D);
+        int mode = 0, part_p0 = t0, part_rows = Tc, fresh_carry = 0;
+        const bool cont0 = c == 0 && n_prev > 0;  // first chunk of a continuation: dictionary not empty
+        if (cont0 || !g.track) {
+            // f at the chunk start over the whole dictionary, between the chunks (in the first chunk
+            // of a continuation also at the carried pilots, whose predictions start from it)
+            const int held = std::min(tb + t0, g.D);
+            if (cont0) {
+                part_p0 = l0 / 2;
+                part_rows = t0 + Tc - part_p0;
+                fresh_carry = g.nc0 > 0 ? 1 : 0;
+            }
             slices_of[0] = 0;
-            if (n_alive > 0) {
-                if (!phase_a(c, t0 - n_alive, n_alive, partial[0], slices_of[0], false)) return APSM_ERR_CUDA;
+            if (held > 0) {
+                if (!phase_a(part_p0, part_rows, tb + t0 - held, held, partial[0], slices_of[0], false))
+                    return APSM_ERR_CUDA;
                 mode = 2;
             }
         } else {
@@ -404,7 +483,7 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         ca.wL = wL;
         ca.wG = wG;
         ca.rx = rx;
-        ca.sym = reinterpret_cast<const float2 *>(sym_pilot);
+        ca.sym = sym;
         ca.dict = reinterpret_cast<float2 *>(st->dict);
         ca.dict_norm = st->dict_norm;
         ca.gamma = st->gamma;
@@ -412,33 +491,96 @@ apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float 
         ca.meta = st->meta;
         ca.kmat = kmat;
         ca.gev = gev;
-        const int pb = g.track ? (c & 1) : 0;  // the tracked form alternates two phase-A buffers
+        const int pb = (g.track && !cont0) ? (c & 1) : 0;  // the tracked form alternates two phase-A buffers
         ca.partial = partial[pb];
         ca.n_slices = slices_of[pb];
+        ca.part_p0 = part_p0;
+        ca.part_rows = part_rows;
+        ca.fresh_carry = fresh_carry;
         ca.carry = carry;
         ca.case_log = case_log;
+        ca.target = st->target;
+        ca.soft_out = soft;
+        ca.hard_out = hard;
+        ca.decide = decide ? 1 : 0;
+        ca.qviol = p->weights == APSM_Q_VIOLATED ? 1 : 0;
+        ca.qam_half = qam_half_of(p);
+        ca.qam_a = qam_a_of(p);
         if (g.track) {
             ca.kx = kx + (size_t)c * g.RS * g.KXS;
-            ca.track_in = c > 0 ? track[c & 1] : nullptr;
+            ca.track_in = (c > 0) ? track[c & 1] : nullptr;
             ca.track_out = c + 1 < g.n_chunks ? track[(c + 1) & 1] : nullptr;
         }
         ca.pdl_mode = mode;
         if (chunk(ca, layout.bytes, strm) != cudaSuccess) return APSM_ERR_CUDA;
         g_launches++;
         if (g.track && c + 1 < g.n_chunks) {
-            // frozen part of the next chunk's starting filter: pilots older than this chunk's live
+            // frozen part of the next chunk's starting filter: entries older than this chunk's live
             // range still held at the next chunk's start.  Their coefficients are final once the
             // previous chunk's phase B completed, which this chunk's phase B waits for before it
             // lets this launch start; it runs beside this chunk's phase B.
             int t0n, Tcn, s0n, s1n, l0n;
             chunk_range(g, c + 1, t0n, Tcn, s0n, s1n, l0n);
-            const int f0 = std::max(0, t0n - g.D), f1 = l0 / 2;
+            const int f0 = std::max(0, tb + t0n - g.D), f1 = tb + l0 / 2;
             slices_of[(c + 1) & 1] = 0;
-            if (f1 > f0 && !phase_a(c + 1, f0, f1 - f0, partial[(c + 1) & 1], slices_of[(c + 1) & 1], true))
+            if (f1 > f0 &&
+                !phase_a(t0n, Tcn, f0, f1 - f0, partial[(c + 1) & 1], slices_of[(c + 1) & 1], true))
                 return APSM_ERR_CUDA;
         }
     }
     return APSM_OK;
+}
+
+apsm_status check_train_args(const apsm_params *p, const float *rx, const float *sym, int P, const apsm_state *st,
+                             bool sym_required) {
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if ((s = check_state(st)) != APSM_OK) return s;
+    if (P < 0 || (P > 0 && (!rx || (sym_required && !sym)))) return APSM_ERR_INVALID_ARG;
+    if (P > (1 << 26)) return APSM_ERR_INVALID_ARG;
+    if (P > 0 && (!aligned16(rx) || (reinterpret_cast<uintptr_t>(sym) & 7))) return APSM_ERR_INVALID_ARG;
+    return APSM_OK;
+}
+
+}  // namespace
+}  // namespace apsm
+
+extern "C" {
+
+apsm_status apsm_train(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                       const float *clin0, const apsm_state *st, void *workspace, size_t workspace_bytes,
+                       int8_t *case_log, void *stream) {
+    apsm_status s = check_train_args(p, rx_pilot, sym_pilot, P, st, true);
+    if (s != APSM_OK) return s;
+    if (clin0 && (reinterpret_cast<uintptr_t>(clin0) & 7)) return APSM_ERR_INVALID_ARG;
+    const TrainWs ws = train_ws(train_geom(p, P, 0), false);
+    if (ws.total > 0 && (!workspace || workspace_bytes < ws.total)) return APSM_ERR_WORKSPACE;
+    if (ws.total > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255)) return APSM_ERR_INVALID_ARG;
+    if ((s = check_device()) != APSM_OK) return s;
+    cudaStream_t strm = static_cast<cudaStream_t>(stream);
+
+    // f_0: linear part clin0 (or zero), empty Gaussian part
+    const size_t clin_bytes = sizeof(float) * 2 * (size_t)p->M * p->K;
+    cudaError_t ce = clin0 == nullptr ? cudaMemsetAsync(st->clin, 0, clin_bytes, strm)
+                     : clin0 != st->clin ? cudaMemcpyAsync(st->clin, clin0, clin_bytes, cudaMemcpyDeviceToDevice, strm)
+                                         : cudaSuccess;
+    if (ce != cudaSuccess) return APSM_ERR_CUDA;
+    if (P == 0) return cuda_status(cudaMemsetAsync(st->meta, 0, 3 * sizeof(int32_t), strm));
+    return train_run(p, rx_pilot, sym_pilot, P, 0, st, workspace, workspace_bytes, nullptr, nullptr, case_log, strm);
+}
+
+apsm_status apsm_train_continue(const apsm_params *p, const float *rx, const float *sym, int32_t P, int32_t n_prev,
+                                const apsm_state *st, void *workspace, size_t workspace_bytes, float *soft,
+                                uint8_t *hard, int8_t *case_log, void *stream) {
+    apsm_status s = check_train_args(p, rx, sym, P, st, false);
+    if (s != APSM_OK) return s;
+    if (n_prev < 0 || n_prev > (1 << 30) - P) return APSM_ERR_INVALID_ARG;
+    if ((soft && (reinterpret_cast<uintptr_t>(soft) & 7))) return APSM_ERR_INVALID_ARG;
+    if (P > 0 && (!workspace || continue_ws_bytes(p, P) > workspace_bytes)) return APSM_ERR_WORKSPACE;
+    if (P > 0 && (reinterpret_cast<uintptr_t>(workspace) & 255)) return APSM_ERR_INVALID_ARG;
+    if ((s = check_device()) != APSM_OK) return s;
+    return train_run(p, rx, sym, P, n_prev, st, workspace, workspace_bytes, soft, hard, case_log,
+                     static_cast<cudaStream_t>(stream));
 }
 
 apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
@@ -452,17 +594,12 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     if (N == 0) return APSM_OK;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
     // Engine: the Gram on the tensor cores (TF32 x3 for FP32, BF16/FP16 as requested) where a
-    // kernel exists for (M, K); FFMA otherwise (APSM_DETECT_ENGINE=ffma forces it for FP32).
-    // APSM_DETECT_TC_COEF=1 also moves the FP32 coefficient sums onto the tensor cores
-    // (detect_tc2.cuh; correct, not yet faster than the FMA epilogue, so not the default).
-    const char *eng = std::getenv("APSM_DETECT_ENGINE");
+    // kernel exists for (M, K); FFMA otherwise, or where the tuning table chose it for FP32.
     const TuneEntry te = tune_get(p->M, p->K, p->dtype);
-    const bool force_ffma = eng ? std::strcmp(eng, "ffma") == 0 : (te.set && te.engine == 1);
+    const bool force_ffma = te.set && te.engine == 1;
     if (p->dtype != APSM_FP32 || !force_ffma) {
-        const bool coef_tc = env_int("APSM_DETECT_TC_COEF", 0) != 0;
-        const int prec = p->dtype == APSM_FP32 ? (coef_tc ? kTF32x3Coef : kTF32x3) : kHalf;
+        const int prec = p->dtype == APSM_FP32 ? kTF32x3 : kHalf;
         TcLauncher tc = detect_tc_launcher(p->M, p->K, prec);
-        if (!tc && prec == kTF32x3Coef) tc = detect_tc_launcher(p->M, p->K, kTF32x3);
         if (tc) {
             TcArgs ta{};
             ta.rx = reinterpret_cast<const float2 *>(rx);
@@ -481,6 +618,8 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
             ta.soft = reinterpret_cast<float2 *>(soft);
             ta.hard = hard;
             ta.status = st->meta + 3;
+            ta.qam_half = qam_half_of(p);
+            ta.qam_a = qam_a_of(p);
             if (tc(ta, strm) != cudaSuccess) return APSM_ERR_CUDA;
             g_launches++;
             return APSM_OK;
@@ -506,6 +645,8 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     da.hard = hard;
     da.partial = nullptr;
     da.status = st->meta + 3;
+    da.qam_half = qam_half_of(p);
+    da.qam_a = qam_a_of(p);
     const DetectShape sh = detect_shape(p->M, p->K, p->dtype);
     if (det(da, 1, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches++;
@@ -513,18 +654,19 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
 }
 
 apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,
-                           int32_t n, const apsm_state *st, void *stream) {
+                           const float *target, int32_t n, const apsm_state *st, void *stream) {
     apsm_status s = check_params(p);
     if (s != APSM_OK) return s;
     if ((s = check_state(st)) != APSM_OK) return s;
     if (n < 0 || n > p->dict_cap || !clin || (n > 0 && (!entries || !gamma))) return APSM_ERR_INVALID_ARG;
+    if (target && (reinterpret_cast<uintptr_t>(target) & 7)) return APSM_ERR_INVALID_ARG;
     if ((s = check_device()) != APSM_OK) return s;
     const int work = std::max(n * p->M, std::max(n * 2 * p->K, p->M * p->K));
     const int blocks = std::max(1, std::min(1024, (work + 255) / 256));
     state_set_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        reinterpret_cast<const float2 *>(entries), gamma, reinterpret_cast<const float2 *>(clin), n, p->M, p->K,
-        reinterpret_cast<float2 *>(st->dict), st->dict_norm, st->gamma, reinterpret_cast<float2 *>(st->clin),
-        st->meta);
+        reinterpret_cast<const float2 *>(entries), gamma, reinterpret_cast<const float2 *>(clin),
+        reinterpret_cast<const float2 *>(target), n, p->M, p->K, reinterpret_cast<float2 *>(st->dict), st->dict_norm,
+        st->gamma, reinterpret_cast<float2 *>(st->clin), reinterpret_cast<float2 *>(st->target), st->meta);
     g_launches++;
     return cuda_status(cudaGetLastError());
 }
@@ -597,6 +739,20 @@ apsm_status apsm_tune_set(int32_t M, int32_t K, int32_t dtype, int32_t engine, i
     return APSM_OK;
 }
 
+apsm_status apsm_set_option(int32_t option, int32_t value) {
+    switch (option) {
+        case APSM_OPT_TRAIN_CHUNK:
+            if (value < 1 || value > 1024) return APSM_ERR_INVALID_ARG;
+            g_opt_train_chunk.store(value);
+            return APSM_OK;
+        case APSM_OPT_TRAIN_TRACK:
+            if (value != 0 && value != 1) return APSM_ERR_INVALID_ARG;
+            g_opt_train_track.store(value);
+            return APSM_OK;
+        default: return APSM_ERR_INVALID_ARG;
+    }
+}
+
 apsm_status apsm_tune_clear(void) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     std::memset(g_tune, 0, sizeof(g_tune));
@@ -613,11 +769,21 @@ apsm_status apsm_check_wait_timeout(const apsm_state *st, void *stream) {
 
 apsm_status apsm_read_status(const apsm_state *st, int32_t *device_status, void *stream) {
     if (!st || !st->meta || !device_status) return APSM_ERR_INVALID_ARG;
+    apsm_status s = check_device();
+    if (s != APSM_OK) return s;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
-    if (cudaStreamSynchronize(strm) != cudaSuccess) return APSM_ERR_CUDA;
+    // one atomic read-and-clear in stream order (a status a kernel on another stream writes
+    // afterwards stays for the next call), then a copy of the read value on the same stream; the
+    // slot is library-owned, so concurrent callers are serialised on the host
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    status_take_kernel<<<1, 1, 0, strm>>>(st->meta + 3);
     int32_t v = 0;
-    if (cudaMemcpy(&v, st->meta + 3, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return APSM_ERR_CUDA;
-    if (cudaMemset(st->meta + 3, 0, sizeof(int32_t)) != cudaSuccess) return APSM_ERR_CUDA;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyFromSymbolAsync(&v, g_status_slot, sizeof(v), 0, cudaMemcpyDeviceToHost, strm) != cudaSuccess ||
+        cudaStreamSynchronize(strm) != cudaSuccess) {
+        cudaGetLastError();
+        return APSM_ERR_CUDA;
+    }
     *device_status = v;
     return APSM_OK;
 }

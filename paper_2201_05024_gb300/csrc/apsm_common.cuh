@@ -78,6 +78,32 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
+// Gray square QAM of apsm_params.modulation, one axis: L = 2^half levels (2i - (L-1)) a.  The
+// level is the number of decision boundaries (2b - L) a, b = 1..L-1, at or below y (QPSK: the
+// sign, 0 counting as non-negative); the axis label is the Gray code of L - 1 - level.
+__device__ __forceinline__ int pam_level(float y, int half, float a) {
+    const int L = 1 << half;
+    int lev = 0;
+    for (int b = 1; b < L; ++b) lev += (y >= (float)(2 * b - L) * a) ? 1 : 0;
+    return lev;
+}
+
+// The decided amplitude of one axis.
+__device__ __forceinline__ float pam_value(int lev, int half, float a) {
+    return (float)(2 * lev - ((1 << half) - 1)) * a;
+}
+
+__device__ __forceinline__ uint32_t pam_gray(int lev, int half) {
+    const uint32_t u = (uint32_t)((1 << half) - 1 - lev);
+    return u ^ (u >> 1);
+}
+
+// Label of the complex decision: real axis in the low `half` bits, imaginary axis above.
+__device__ __forceinline__ uint8_t qam_label(float y1, float y2, int half, float a) {
+    if (half == 1) return (uint8_t)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
+    return (uint8_t)(pam_gray(pam_level(y1, half, a), half) | (pam_gray(pam_level(y2, half, a), half) << half));
+}
+
 __device__ __forceinline__ void report(int *status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

@@ -27,6 +27,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "apsm_common.cuh"
 #include "detect_f32.cuh"
 
@@ -37,6 +39,11 @@ enum TcPrec { kTF32x3 = 0, kHalf = 1 };
 constexpr int kTcRows = 128;     // queries per CTA (MMA M)
 constexpr int kTcEntries = 64;   // entries per tile (MMA N = 2 * kTcEntries)
 constexpr int kTcThreads = 256;
+
+// Cancellation-guard thresholds theta of the per-pair direct-difference fallback (relative to
+// k2 (n_s + n_t)): 2^-4 for a BF16/FP16 Gram, 2^-12 for the TF32 x3 Gram.
+constexpr float kGuardHalf = 0.0625f;
+constexpr float kGuardF32 = 1.f / 4096.f;
 
 struct TcArgs {
     const float2 *rx;         // [N][M]
@@ -53,6 +60,8 @@ struct TcArgs {
     float2 *soft;             // [N][K]
     uint8_t *hard;            // [N][K] nullable
     int *status;
+    int qam_half;             // bits per axis of the Gray-QAM decisions
+    float qam_a;              // amplitude unit of one axis
 };
 
 // Operand layout: K-major, no swizzle; core matrix = 8 rows x 16 bytes.  KD = contraction
@@ -501,45 +510,114 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
         // ================= epilogue: exponentials and coefficient sums =================
         const float hq = cta_in_range ? 0.f : -a.k2 * nq;  // unfactored exponent when out of range
         const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-        for (int tile = 0; tile < n_tiles; ++tile) {
-            const int st = tile & 1;
-            // warp-uniform decision: tcgen05.ld below is executed by whole warps only
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(&mma_done[st], (tile >> 1) & 1))) {
-                ok = false;
-                break;
+        const int s_row = q0 + tid;
+        // Cancellation guard (direct-difference fallback).  With S = k2 (n_s + n_t) and v the
+        // Gram's exponent columns (2 k2 Re z, 2 k2 Im z), the three scaled squared distances are
+        // S - v_re, S - v_im and S + v_im; their minimum is S - max(v_re, |v_im|).  A pair whose
+        // minimum falls below theta S (theta = kGuardHalf for BF16/FP16, kGuardF32 for TF32 x3)
+        // is one where the norm expansion cancels while its exponential still matters: its
+        // terms are dropped from the fast loop (exponent -inf) and recomputed from the FP32 query
+        // and entry by direct differences.  TF32 x3 needs it only for queries outside the factor
+        // range (inside it the Gram error is below 2^-21 S <= 6e-5 in the exponent).
+        const bool guard = kPrec == kHalf || !cta_in_range;
+        const float one_m_theta = 1.f - (kPrec == kHalf ? kGuardHalf : kGuardF32);
+        const float thr_q = one_m_theta * a.k2 * nq;  // (1 - theta) k2 n_s
+        const float base_q = a.k2 * nq + hq;           // exponent offset of the exact terms
+        const float *g_all = sG;
+        // exact terms of entry e of the current tile (stage st): three squared distances by direct
+        // differences of the FP32 query and entry (no norm expansion)
+        auto exact_pair = [&](int st, int e, int e0) {
+            const int t = e0 + e;
+            if (t >= n_ent || s_row >= a.N) return;
+            const float2 *rq = a.rx + (size_t)s_row * M;
+            const float2 *rt = a.dict + (size_t)t * M;
+            float dA = 0.f, dB = 0.f, dC = 0.f;
+#pragma unroll 4
+            for (int m = 0; m < M; ++m) {
+                const float2 q = __ldg(rq + m), d = __ldg(rt + m);
+                const float ax = d.x - q.x, ay = d.y - q.y;  // r_t - r_s
+                const float bx = d.x - q.y, by = d.y + q.x;  // r_t + i r_s  (r1(t) vs r2(s))
+                const float cx = d.x + q.y, cy = d.y - q.x;  // r_t - i r_s  (r2(t) vs r1(s))
+                dA = fmaf(ax, ax, fmaf(ay, ay, dA));
+                dB = fmaf(bx, bx, fmaf(by, by, dB));
+                dC = fmaf(cx, cx, fmaf(cy, cy, dC));
             }
-            tc_fence_after();
-            const float *g = sG + st * E * 2 * KB;
-            const float *hh = sH + st * E;
+            const float eA = ex2(base_q - a.k2 * dA), eB = ex2(base_q - a.k2 * dB), eC = ex2(base_q - a.k2 * dC);
+            float g1[KB], gg[KB];
+            load_coef<KB>(g_all + (st * E + e) * 2 * KB, g1, gg);
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                acc1[k] = fmaf(g1[k], eA, fmaf(gg[k], eC, acc1[k]));
+                acc2[k] = fmaf(g1[k], eB, fmaf(gg[k], eA, acc2[k]));
+            }
+        };
+        auto run_tiles = [&](auto guard_c) {
+            constexpr bool kGuard = decltype(guard_c)::value;
+            for (int tile = 0; tile < n_tiles; ++tile) {
+                const int st = tile & 1;
+                // warp-uniform decision: tcgen05.ld below is executed by whole warps only
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&mma_done[st], (tile >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const float *g = sG + st * E * 2 * KB;
+                const float *hh = sH + st * E;
 #pragma unroll 1
-            for (int c = 0; c < NB / 16; ++c) {
-                float v[16], hv[8];
-                tmem_ld16(tmem + lane_base + (uint32_t)(st * NB + 16 * c), v);
-                *reinterpret_cast<float4 *>(hv) = *reinterpret_cast<const float4 *>(hh + 8 * c);
-                *reinterpret_cast<float4 *>(hv + 4) = *reinterpret_cast<const float4 *>(hh + 8 * c + 4);
+                for (int c = 0; c < NB / 16; ++c) {
+                    float v[16], hv[8];
+                    tmem_ld16(tmem + lane_base + (uint32_t)(st * NB + 16 * c), v);
+                    *reinterpret_cast<float4 *>(hv) = *reinterpret_cast<const float4 *>(hh + 8 * c);
+                    *reinterpret_cast<float4 *>(hv + 4) = *reinterpret_cast<const float4 *>(hh + 8 * c + 4);
+                    bool flagged = false;
+                    uint32_t fbits = 0;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int e = 8 * c + j;
-                    const float h = hv[j] + hq;
-                    float xA = v[2 * j], xB = v[2 * j + 1];
-                    add2_bcast(xA, xB, h);  // (Re z + h, Im z + h)
-                    const float eA = ex2(xA), eB = ex2(xB), eC = ex2(h - v[2 * j + 1]);
-                    float g1[KB], gg[KB];
-                    load_coef<KB>(g + e * 2 * KB, g1, gg);
-                    // acc1 = g1 E_A + g2 E_C + acc1,  acc2 = g1 E_B + g2 E_A + acc2, users in pairs
+                    for (int j = 0; j < 8; ++j) {
+                        const int e = 8 * c + j;
+                        float h = hv[j] + hq;
+                        if constexpr (kGuard) {
+                            // flagged: max(v_re, |v_im|) > (1 - theta) k2 (n_s + n_t)
+                            const bool f = fmaxf(v[2 * j], fabsf(v[2 * j + 1])) > fmaf(-one_m_theta, hv[j], thr_q);
+                            h = f ? -INFINITY : h;
+                            fbits |= f ? (1u << j) : 0u;
+                            flagged |= f;
+                        }
+                        float xA = v[2 * j], xB = v[2 * j + 1];
+                        add2_bcast(xA, xB, h);  // (Re z + h, Im z + h)
+                        const float eA = ex2(xA), eB = ex2(xB), eC = ex2(h - v[2 * j + 1]);
+                        float g1[KB], gg[KB];
+                        load_coef<KB>(g + e * 2 * KB, g1, gg);
+                        // acc1 = g1 E_A + g2 E_C + acc1,  acc2 = g1 E_B + g2 E_A + acc2, users in pairs
 #pragma unroll
-                    for (int k = 0; k < KB; k += 2) {
-                        fma2_pair(acc1[k], acc1[k + 1], gg[k], gg[k + 1], eC);
-                        fma2_pair(acc1[k], acc1[k + 1], g1[k], g1[k + 1], eA);
-                        fma2_pair(acc2[k], acc2[k + 1], gg[k], gg[k + 1], eA);
-                        fma2_pair(acc2[k], acc2[k + 1], g1[k], g1[k + 1], eB);
+                        for (int k = 0; k < KB; k += 2) {
+                            fma2_pair(acc1[k], acc1[k + 1], gg[k], gg[k + 1], eC);
+                            fma2_pair(acc1[k], acc1[k + 1], g1[k], g1[k + 1], eA);
+                            fma2_pair(acc2[k], acc2[k + 1], gg[k], gg[k + 1], eA);
+                            fma2_pair(acc2[k], acc2[k + 1], g1[k], g1[k + 1], eB);
+                        }
+                    }
+                    if constexpr (kGuard) {
+                        if (__any_sync(0xffffffffu, flagged)) {
+#pragma unroll 1
+                            while (fbits) {
+                                const int j = __ffs(fbits) - 1;
+                                fbits &= fbits - 1;
+                                exact_pair(st, 8 * c + j, tile * E);
+                            }
+                        }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(&epi_done[st]);
             }
-            tc_fence_before();
-            mbar_arrive(&epi_done[st]);
+        };
+        if constexpr (kPrec == kHalf) {
+            run_tiles(std::true_type{});
+        } else {
+            if (guard) run_tiles(std::true_type{});
+            else run_tiles(std::false_type{});
         }
-        const int s = q0 + tid;
+        const int s = s_row;
         if (ok && s < a.N) {
             const float fq = cta_in_range ? ex2(-a.k2 * nq) : 1.f;  // query factor
             const float2 *rq = a.rx + (size_t)s * M;
@@ -557,7 +635,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                 y1 = fmaf(a.wL, l1, a.wG * fq * y1);
                 y2 = fmaf(a.wL, l2, a.wG * fq * y2);
                 a.soft[(size_t)s * a.K + k] = make_float2(y1, y2);
-                if (a.hard) a.hard[(size_t)s * a.K + k] = (uint8_t)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
+                if (a.hard) a.hard[(size_t)s * a.K + k] = qam_label(y1, y2, a.qam_half, a.qam_a);
             }
         }
     }

@@ -3,7 +3,6 @@
 #pragma once
 
 #include "detect_tc.cuh"
-#include "detect_tc2.cuh"
 
 #define APSM_TC_CAT2(a, b) a##b
 #define APSM_TC_CAT(a, b) APSM_TC_CAT2(a, b)
@@ -13,19 +12,6 @@ namespace apsm {
 // kb: user bucket (2, 4, 6, 8, 12, 16); prec: kTF32x3 or kHalf.
 TcLauncher APSM_TC_CAT(detect_tc_launcher_m, APSM_TC_M)(int kb, int prec) {
     constexpr int M = APSM_TC_M;
-    if (prec == kTF32x3Coef) {
-        if constexpr (M <= 32) {
-            switch (kb) {
-                case 2: return launch_detect_tc2<M, 2>;
-                case 4: return launch_detect_tc2<M, 4>;
-                case 6: return launch_detect_tc2<M, 6>;
-                case 8: return launch_detect_tc2<M, 8>;
-                case 12: return launch_detect_tc2<M, 12>;
-                case 16: return launch_detect_tc2<M, 16>;
-            }
-        }
-        return nullptr;
-    }
     if (prec == kTF32x3) {
         if constexpr (M <= 32) {
             switch (kb) {

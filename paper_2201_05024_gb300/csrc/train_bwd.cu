@@ -325,6 +325,7 @@ apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, con
     if (s != APSM_OK) return s;
     if (P < 1 || !rx_pilot || !sym_pilot || !dgamma || !dclin || !dscalars || !dclin0) return APSM_ERR_INVALID_ARG;
     if (P > 8192) return APSM_ERR_UNSUPPORTED;
+    if (p->weights != APSM_Q_UNIFORM) return APSM_ERR_UNSUPPORTED;  // the adjoint of q = 1/|J_n| only
     const BwdLayout b = bwd_layout(p, P);
     if (!workspace || workspace_bytes < b.total) return APSM_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return APSM_ERR_INVALID_ARG;

@@ -35,7 +35,11 @@
 namespace apsm {
 
 struct TrainGeom {
-    int M, K, W, D, P;
+    int M, K, W, D;
+    int P;         // pilots of the extended sequence: nc0 carried + the call's new vectors
+    int nc0;       // pilots carried over from the previous call (the window reaches into them)
+    int t_base;    // running index of extended pilot 0 (vectors trained on before it)
+    int evict;     // FIFO eviction can occur in this call (t_base + P > D, or unknown)
     int T;         // pilots per chunk
     int n_chunks;
     int RMAX;      // 2T + W: live-range capacity
@@ -49,9 +53,10 @@ struct TrainGeom {
 // first sample of the live range of a chunk starting at sample s0 (a pilot boundary)
 __host__ __device__ inline int live_start(int s0, int W) { return max(0, s0 - W + 1) & ~1; }
 
+// Chunk c covers extended pilots [t0, t0 + Tc), after the nc0 carried ones.
 __host__ __device__ inline void chunk_range(const TrainGeom &g, int c, int &t0, int &Tc, int &s0, int &s1,
                                             int &l0) {
-    t0 = c * g.T;
+    t0 = g.nc0 + c * g.T;
     Tc = min(g.T, g.P - t0);
     s0 = 2 * t0;
     s1 = 2 * (t0 + Tc);
@@ -81,15 +86,17 @@ __device__ inline void sample_pair(const float2 *ra, const float2 *rb, int M, in
 //   gev[c][e][l][v] = kappa_G(x_{2(t0+e-D)+l}, x_{l0+v})            entry t0+e-D dropped at n = 2(t0+e)
 //   kx[c][u][v] = kappa(x_{l0+u}, x_{s1+v})                         v < next chunk's 2Tc (stride KXS)
 // (train_gram_kernel, defined in train_chunk.cu; kx only when g.track).
-cudaError_t launch_train_gram(const float2 *rx, const TrainGeom &g, float k2, float wL, float wG, float *kmat,
-                              float *gev, float *kx, cudaStream_t stream);
+// Pilot vectors come from the extended sequence rx; an entry dropped during the call that was
+// trained on before it (running index < t_base) is read from its dictionary slot.
+cudaError_t launch_train_gram(const float2 *rx, const float2 *dict, const TrainGeom &g, float k2, float wL, float wG,
+                              float *kmat, float *gev, float *kx, cudaStream_t stream);
 
 struct ChunkArgs {
     TrainGeom g;
     int chunk;
     float mu, eps, wL, wG;
-    const float2 *rx;       // [P][M]
-    const float2 *sym;      // [P][K]
+    const float2 *rx;       // [P][M] extended sequence (carried pilots, then the new ones)
+    float2 *sym;            // [P][K] its targets (decision-directed: decided ones written back)
     float2 *dict;           // [A][M]
     float *dict_norm;       // [A]
     float *gamma;           // [A][2][K]
@@ -97,10 +104,19 @@ struct ChunkArgs {
     int *meta;              // [4]
     const float *kmat;      // [n_chunks][RS][RS]
     const float *gev;       // [n_chunks][T][2][RS]
-    const float *partial;   // [n_slices][Tc][2K]
+    const float *partial;   // [n_slices][part_rows][2K]: rows = pilots part_p0, part_p0 + 1, ..
     int n_slices;
+    int part_p0, part_rows;
+    int fresh_carry;        // carried samples start from phase A (first chunk of a continuation)
     float *carry;           // [W][K]
-    int8_t *case_log;       // [2P][W][K] nullable
+    int8_t *case_log;       // [2 (P - nc0)][W][K] nullable
+    float *target;          // state: [A][K] complex targets of the held entries
+    float *soft_out;        // [P - nc0][K] complex output at arrival, nullable
+    uint8_t *hard_out;      // [P - nc0][K] labels of the targets, nullable
+    int decide;             // targets of the new samples are decided at arrival
+    int qviol;              // weights q_j = 1/|V_n| on the violated slabs
+    int qam_half;           // slicer: bits per axis and amplitude unit
+    float qam_a;
     const float *kx;        // [RS][KXS] of this chunk (tracking)
     const float *track_in;  // [2T][K]: tracked part of f at this chunk's start, at its samples
     float *track_out;       // [2T][K]: the same for the next chunk (null: no tracking)
@@ -114,17 +130,18 @@ struct ChunkArgs {
 
 // Shared-memory layout of phase B (bytes; every region 16-byte aligned).
 struct ChunkSmem {
-    int bar, kmat, gev, egam, beta, dg, clin, pil, trk, bytes;
+    int bar, kmat, gev, egam, beta, dg, tgt, clin, pil, trk, bytes;
     __host__ __device__ ChunkSmem(const TrainGeom &g) {
         const int RS = g.RS;
         const int npil = g.T + (g.W + 1) / 2 + 1;
         bar = 0;
         kmat = 16;                                   // WP zero rows, then RS rows of RS
         gev = kmat + (g.WP + RS) * RS * 4;
-        egam = gev + (g.P > g.D ? g.T * 2 * RS * 4 : 0);   // dropped-entry table only when P > D
+        egam = gev + (g.evict ? g.T * 2 * RS * 4 : 0);     // dropped-entry table only with eviction
         beta = egam + round_up(g.T * 2 * 4, 16);
-        dg = beta + (4 * RS + 2 * g.WP + 160) * 4;  // beta ring, or p / gamma / b / 1/kappa + rings
-        clin = dg + RS * 4;
+        dg = beta + (4 * RS + 2 * g.WP + 224) * 4;  // beta ring, or p / gamma / b / 1/kappa + rings + mu q tables
+        tgt = dg + RS * 4;                          // final targets of the live range
+        clin = tgt + RS * 4;
         pil = clin + round_up(g.M * 8, 16);
         trk = pil + npil * g.M * 8;                   // carried coefficients [32], reduced filter [M]
         bytes = trk + (g.track ? 32 * 4 + g.M * 8 : 0);
@@ -154,6 +171,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     float *s_egam = reinterpret_cast<float *>(smem + L.egam);
     float *s_beta = reinterpret_cast<float *>(smem + L.beta);
     float *s_dg = reinterpret_cast<float *>(smem + L.dg);
+    float *s_tgt = reinterpret_cast<float *>(smem + L.tgt);
     float2 *s_clin = reinterpret_cast<float2 *>(smem + L.clin);
     float2 *s_pil = reinterpret_cast<float2 *>(smem + L.pil);
     float *s_gcar = reinterpret_cast<float *>(smem + L.trk);             // carried gamma at chunk start
@@ -167,7 +185,10 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     const int npil = t0 + Tc - pa0;
     const int k = blockIdx.x;  // user
     const int u = threadIdx.x;  // live-range sample of this thread
-    const bool evict = (t0 + Tc - 1) >= D;
+    const int tb = g.t_base;    // running index = tb + extended pilot index; its slot is that mod D
+    const int sb = 2 * tb;      // running index of extended sample 0
+    const int n_first = 2 * g.nc0;  // first sample this call trains on (case log / outputs index from it)
+    const bool evict = (tb + t0 + Tc - 1) >= D;
 
     // ---- stage the chunk's kernel tables and pilots with the bulk-copy engine ---------------
     if (u == 0) {
@@ -183,16 +204,13 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     __syncthreads();  // the barrier's initialisation is visible before any thread waits on it
     const bool valid = u < R;
     const int m = l0 + u, pa = m >> 1, l = m & 1;
-    float b = 0.f;
-    if (valid) {
-        const float2 sy = a.sym[(size_t)pa * K + k];
-        b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
-    }
     for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
     for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
     float rk = 0.f;  // 1 / kappa(x_j, x_j)
+    // Every thread reaches this wait; the CTA votes on its outcome so that either all threads
+    // go on or all leave together (no thread may skip a later barrier the others wait at).
     auto tables_ready = [&]() {
-        if (!mbar_wait_bounded(bar, 0)) {
+        if (!__syncthreads_and(mbar_wait_bounded(bar, 0))) {
             if (u == 0) report(a.meta + 3, APSM_ERR_TIMEOUT);
             return false;
         }
@@ -208,21 +226,28 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         pdl_trigger();
     }
     // every global load of the prologue is issued before the first use (one round trip)
+    // (targets after the wait: in decision-directed mode the previous chunk decided them)
+    float b = 0.f;
+    if (valid) {
+        const float2 sy = a.sym[(size_t)pa * K + k];
+        b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
+    }
     float2 clin_r[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // M <= 64 <= 2 RS
 #pragma unroll
     for (int i = 0; i < 2; ++i)
         if (u + i * RS < M) clin_r[i] = a.clin[(u + i * RS) * K + k];
     // coefficients of the entries dropped in this chunk (entry t0+e-D at step 2(t0+e))
+    // (the dropped entry and the arriving one share the slot (tb + t0 + e) mod D)
     float egam_r = 0.f;
-    if (evict && u < 2 * Tc && t0 + (u >> 1) >= D)
-        egam_r = a.gamma[((size_t)((t0 + (u >> 1) - D) % D) * 2 + (u & 1)) * K + k];
+    if (evict && u < 2 * Tc && tb + t0 + (u >> 1) >= D)
+        egam_r = a.gamma[((size_t)((tb + t0 + (u >> 1)) % D) * 2 + (u & 1)) * K + k];
 
     // ---- this thread's sample: target, coefficient, prediction at chunk start ---------------
     float p = 0.f, gam = 0.f;
     if (valid) {
         if (m < s0) {
-            p = a.carry[u * K + k];
-            gam = a.gamma[((size_t)(pa % D) * 2 + l) * K + k];
+            if (!a.fresh_carry) p = a.carry[u * K + k];
+            gam = a.gamma[((size_t)((tb + pa) % D) * 2 + l) * K + k];
         } else if (a.track_in) {
             p = a.track_in[(m - s0) * K + k];
         }
@@ -237,7 +262,10 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     if (track && u < 32) s_gcar[u] = (valid && m < s0) ? gam : 0.f;
     __syncthreads();
     if (a.pdl_mode != 1 && !tables_ready()) return;
-    if (valid && m >= s0 && !a.track_in) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
+    // samples whose prediction starts from phase A: the chunk's new ones (untracked form), and
+    // in the first chunk of a continuation also the carried ones
+    const bool from_a = valid && ((m >= s0 && !a.track_in) || (m < s0 && a.fresh_carry));
+    if (from_a) {  // linear part w_L <w, x_m> = w_L Re / Im (c^H r) at chunk start
         // each pilot starts at its own antenna so the lanes of a warp hit distinct banks
         const float2 *rv = s_pil + (pa - pa0) * M;
         float lin0 = 0.f, lin1 = 0.f;
@@ -257,11 +285,11 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         pdl_wait();
         pdl_trigger();
     }
-    if (valid && m >= s0) {
+    if (valid && (m >= s0 || a.fresh_carry)) {
         // Gaussian part of f_{s0}(x_m) from the phase-A slices: 32 loads in flight at a time,
         // summed into eight partial sums (slice i into sum i mod 8) combined in a fixed order
-        const float *src = a.partial + (size_t)(pa - t0) * 2 * K + l * K + k;
-        const size_t stride = (size_t)Tc * 2 * K;
+        const float *src = a.partial + (size_t)(pa - a.part_p0) * 2 * K + l * K + k;
+        const size_t stride = (size_t)a.part_rows * 2 * K;
         float gs[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int sl = 0; sl < a.n_slices; sl += 32) {
             float v[32];
@@ -305,7 +333,11 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
             s_b[u] = b;
             s_rk[u] = rk;
         }
-        if (u < 32) s_muq[u] = a.mu / (float)(u + 1);  // mu q while the window is filling (n < W - 1)
+        float *s_muqv = s_muq + 32;
+        if (u < 32) {
+            s_muq[u] = a.mu / (float)(u + 1);                 // mu q while the window is filling (n < W - 1)
+            s_muqv[u] = u == 0 ? 0.f : a.mu / (float)u;       // mu q with q = 1/|V_n|, |V_n| = u
+        }
         for (int i = u; i < 64; i += RS) s_w[i] = 0.f;
         __syncthreads();
         const int lane = u & 31;
@@ -401,11 +433,12 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 const int ms = wl0 + lane, lu = ms - l0;
                 const bool lv = lane < NL && ms >= l0 && ms < s1;
                 const int col = lv ? lu : 0;
-                float pl = 0.f, c1 = 0.f, c2 = 0.f, rkl = 0.f, agg = 0.f;
+                float pl = 0.f, c1 = 0.f, c2 = 0.f, rkl = 0.f, agg = 0.f, bl = 0.f;
                 if (lv) {
                     pl = s_p[lu];
-                    c1 = s_b[lu] - a.eps;  // the hyperslab [b - eps, b + eps]
-                    c2 = s_b[lu] + a.eps;
+                    bl = s_b[lu];
+                    c1 = bl - a.eps;  // the hyperslab [b - eps, b + eps]
+                    c2 = bl + a.eps;
                     rkl = s_rk[lu];
                 }
                 float kc[NL];  // kappa(x_{wl0+j}, x of this lane)
@@ -415,26 +448,42 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                     // beta is 0: clamp instead of branching so that the loads issue together
                     kc[j] = s_kmat[min(wl0 + j - l0, R - 1) * RS + col];
                 }
-                // kChecked: a partial last block, the filling window (n < W - 1) or case logging
-                auto steps = [&](auto checked_c, auto evict_c) {
+                // kChecked: a partial last block, the filling window (n < W - 1), case logging,
+                // outputs at arrival or decided targets; kViol: weights on the violated slabs
+                auto steps = [&](auto checked_c, auto evict_c, auto viol_c) {
                     constexpr bool kChecked = decltype(checked_c)::value, kEvict = decltype(evict_c)::value;
+                    constexpr bool kViol = decltype(viol_c)::value;
 #pragma unroll
                     for (int s = 0; s < B; ++s) {
                         const int n = n0 + s;
                         if (kChecked && n >= s1) break;
-                        if (kEvict && !(n & 1) && (n >> 1) >= D) {
+                        if (kEvict && !(n & 1) && (n >> 1) + tb >= D) {
                             const int e = (n >> 1) - t0;
                             pl -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + col],
                                               s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + col]);
                         }
-                        const float muq = kChecked && n < W - 1 ? s_muq[n] : muq_full;  // mu q, q = 1/|J_n|
+                        if (kChecked && lane == s + WP - 1) {  // sample n arrives: pl = f_n(x_n)
+                            if (a.soft_out) a.soft_out[((size_t)((n - n_first) >> 1) * K + k) * 2 + (n & 1)] = pl;
+                            if (a.decide) {  // its target: the decision on the filter's own output
+                                bl = pam_value(pam_level(pl, a.qam_half, a.qam_a), a.qam_half, a.qam_a);
+                                c1 = bl - a.eps;
+                                c2 = bl + a.eps;
+                            }
+                        }
                         // window J_n = samples [n - W + 1, n] = lanes [s + WP - W, s + WP - 1]
                         const bool inw = lv && lane >= s + WP - W && lane <= s + WP - 1;
+                        float muq;
+                        if constexpr (kViol) {  // mu q with q = 1/|V_n| on the violated slabs
+                            const bool viol = inw && (pl < c1 || pl > c2);
+                            muq = s_muqv[__popc(__ballot_sync(0xffffffffu, viol))];
+                        } else {                // mu q with q = 1/|J_n|
+                            muq = kChecked && n + sb < W - 1 ? s_muq[n + sb] : muq_full;
+                        }
                         const float sc = inw ? muq * rkl : 0.f;
                         const float mb = (fminf(fmaxf(pl, c1), c2) - pl) * sc;  // mu q beta_j
                         agg += mb;
                         if (kChecked && log_cases && inw)
-                            a.case_log[((size_t)n * W + (ms - n + W - 1)) * K + k] =
+                            a.case_log[((size_t)(n - n_first) * W + (ms - n + W - 1)) * K + k] =
                                 (int8_t)(pl < c1 ? -1 : (pl > c2 ? 1 : 0));
                         float *ring = s_w + (s & 1) * 32;
                         ring[lane] = mb;
@@ -456,17 +505,21 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 };
                 using T_ = std::true_type;
                 using F_ = std::false_type;
-                const bool checked = n0 + B > s1 || n0 < W - 1 || log_cases;
-                if (evict) {
-                    if (checked) steps(T_{}, T_{});
-                    else steps(F_{}, T_{});
+                const bool checked = n0 + B > s1 || n0 + sb < W - 1 || log_cases || a.decide || a.soft_out;
+                if (a.qviol) {
+                    if (evict) steps(T_{}, T_{}, T_{});
+                    else steps(T_{}, F_{}, T_{});
+                } else if (evict) {
+                    if (checked) steps(T_{}, T_{}, F_{});
+                    else steps(F_{}, T_{}, F_{});
                 } else {
-                    if (checked) steps(T_{}, F_{});
-                    else steps(F_{}, F_{});
+                    if (checked) steps(T_{}, F_{}, F_{});
+                    else steps(F_{}, F_{}, F_{});
                 }
                 if (lv) {
                     s_p[lu] = pl;
                     s_g[lu] += agg;
+                    s_b[lu] = bl;
                 }
                 agg_cur[lane] = lv ? agg : 0.f;
             }
@@ -481,7 +534,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 float pv = s_p[u] + ((acc[0] + acc[1]) + (acc[2] + acc[3]));
                 if (evict) {
                     for (int n = n0 + (n0 & 1); n < min(n0 + B, s1); n += 2) {
-                        if ((n >> 1) < D) continue;
+                        if ((n >> 1) + tb < D) continue;
                         const int e = (n >> 1) - t0;
                         pv -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u],
                                           s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
@@ -504,6 +557,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         if (valid) {
             p = s_p[u];
             gam = s_g[u];
+            b = s_b[u];
         }
     } else if constexpr (WP <= kRingMax) {
         // Window ring: sample j sits in slot (j - s0) mod WP.  kc[r] holds kappa(x_j, x_u) of the
@@ -521,28 +575,39 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 if (n >= s1) break;
                 const int un = n - l0;
                 kc[r] = kcol[un * RS];  // sample n enters slot r
-                if (evict && !(n & 1) && (n >> 1) >= D) {
+                if (evict && !(n & 1) && (n >> 1) + tb >= D) {
                     const int e = (n >> 1) - t0;
                     p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u],
                                      s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
                 }
+                if (valid && m == n) {  // sample n arrives: p = f_n(x_n)
+                    if (a.soft_out) a.soft_out[((size_t)((n - n_first) >> 1) * K + k) * 2 + (n & 1)] = p;
+                    if (a.decide) b = pam_value(pam_level(p, a.qam_half, a.qam_a), a.qam_half, a.qam_a);
+                }
                 float muq = muq_full;
-                if (n < W - 1) muq = a.mu / (float)(n + 1);  // mu q, q = 1/|J_n|
+                if (n + sb < W - 1) muq = a.mu / (float)(n + sb + 1);  // mu q, q = 1/|J_n|
                 float *ring = s_beta + (r & 1) * WP;          // nb - s0 is a multiple of WP (even)
+                float beta = 0.f;
+                bool viol = false;
                 if (valid && m <= n && m > n - WP) {
-                    float beta = 0.f;
                     if (m > n - W) {
                         const float e = p - b;  // <f_n, kappa(x_j,.)> - b_j
                         // Eq. beta without branches: (-e - eps) below the slab, (eps - e) above, 0 inside
                         beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
-                        gam = fmaf(muq, beta, gam);
+                        viol = e < -a.eps || e > a.eps;
                         if (log_cases)
-                            a.case_log[((size_t)n * W + (m - n + W - 1)) * K + k] =
+                            a.case_log[((size_t)(n - n_first) * W + (m - n + W - 1)) * K + k] =
                                 (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
                     }
                     ring[slot] = beta;
                 }
-                __syncthreads();
+                if (a.qviol) {  // q = 1/|V_n| on the violated slabs
+                    const int nv = __syncthreads_count(viol);
+                    muq = nv > 0 ? a.mu / (float)nv : 0.f;
+                } else {
+                    __syncthreads();
+                }
+                gam = fmaf(muq, beta, gam);  // (beta = 0 outside the window)
                 // p_u += mu q sum_{i in J_n} beta_i kappa(x_i, x_u)
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -560,25 +625,38 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         for (int n = s0; n < s1; ++n) {
             const int un = n - l0;
             // a new pilot arrives at n = 2t: the oldest entry is dropped once D are held
-            if (evict && !(n & 1) && (n >> 1) >= D) {
+            if (evict && !(n & 1) && (n >> 1) + tb >= D) {
                 const int e = (n >> 1) - t0;
                 p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u], s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
             }
+            if (valid && m == n) {  // sample n arrives: p = f_n(x_n)
+                if (a.soft_out) a.soft_out[((size_t)((n - n_first) >> 1) * K + k) * 2 + (n & 1)] = p;
+                if (a.decide) b = pam_value(pam_level(p, a.qam_half, a.qam_a), a.qam_half, a.qam_a);
+            }
             const int ujlo = max(0, n - W + 1) - l0;
-            const float muq = (n >= W - 1) ? muq_full : a.mu / (float)(n + 1);  // mu q, q = 1/|J_n|
+            float muq = (n + sb >= W - 1) ? muq_full : a.mu / (float)(n + sb + 1);  // mu q, q = 1/|J_n|
             float *bb = s_beta + (n & 1) * (WP + RS) + WP;
+            float beta = 0.f;
+            bool viol = false;
             if (u >= ujlo && u <= un) {
                 const float e = p - b;  // <f_n, kappa(x_j,.)> - b_j
                 // Eq. beta without branches: (-e - eps) below the slab, (eps - e) above it, 0 inside
-                const float beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
-                gam = fmaf(muq, beta, gam);
+                beta = (fmaxf(-e - a.eps, 0.f) - fmaxf(e - a.eps, 0.f)) * rk;
+                viol = e < -a.eps || e > a.eps;
                 bb[u] = beta;
                 if (log_cases)
-                    a.case_log[((size_t)n * W + (m - n + W - 1)) * K + k] = (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
+                    a.case_log[((size_t)(n - n_first) * W + (m - n + W - 1)) * K + k] =
+                        (int8_t)(e < -a.eps ? -1 : (e > a.eps ? 1 : 0));
             } else if (u < ujlo && u > un - WP) {
                 bb[u] = 0.f;
             }
-            __syncthreads();
+            if (a.qviol) {  // q = 1/|V_n| on the violated slabs
+                const int nv = __syncthreads_count(viol);
+                muq = nv > 0 ? a.mu / (float)nv : 0.f;
+            } else {
+                __syncthreads();
+            }
+            gam = fmaf(muq, beta, gam);  // (beta = 0 outside the window)
             // p_u += mu q sum_{i in J_n} beta_i kappa(x_i, x_u)
             const float *kp = kcol + (un - WP + 1) * RS;
             const float *bp = bb + (un - WP + 1);
@@ -594,12 +672,20 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
 
     // ---- write back: coefficients, carried predictions, linear filter ---------------------------
     if (valid) {
-        a.gamma[((size_t)(pa % D) * 2 + l) * K + k] = gam;
+        const size_t slot = (size_t)((tb + pa) % D);
+        a.gamma[(slot * 2 + l) * K + k] = gam;
         s_dg[u] = gam - gam0;
+        s_tgt[u] = b;
         const int l0n = live_start(s1, W);
         if (m >= l0n) a.carry[(m - l0n) * K + k] = p;
+        if (m >= s0) {  // the chunk's new samples: their targets (decided or given) join the state
+            a.target[(slot * K + k) * 2 + l] = b;
+            if (a.decide) reinterpret_cast<float *>(a.sym)[((size_t)pa * K + k) * 2 + l] = b;
+        }
     }
     __syncthreads();
+    if (a.hard_out && valid && l == 0 && m >= s0)  // Gray-QAM label of the vector's two targets
+        a.hard_out[(size_t)(pa - g.nc0) * K + k] = qam_label(s_tgt[u], s_tgt[u + 1], a.qam_half, a.qam_a);
     // c_k += sum_u dgamma_u x~_u, with x~ = r(t) for r1(t) and -i r(t) for r2(t): the live range
     // is split into np parts per antenna, partial sums combined in a fixed order
     {
@@ -647,22 +733,23 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         }
     }
 
-    // ---- new dictionary entries of this chunk (slot t % D), their norms, bookkeeping -------
+    // ---- new dictionary entries of this chunk (slot (tb + t) % D), their norms, bookkeeping --
     if (k == 0) {
         for (int i = u; i < Tc * M; i += RS) {
             const int t = t0 + i / M, mm = i % M;
-            a.dict[(size_t)(t % D) * M + mm] = s_pil[(t - pa0) * M + mm];
+            a.dict[(size_t)((tb + t) % D) * M + mm] = s_pil[(t - pa0) * M + mm];
         }
         for (int i = u; i < Tc; i += RS) {
             const float2 *rv = s_pil + (t0 + i - pa0) * M;
             float nrm = 0.f;
             for (int mm = 0; mm < M; ++mm) nrm = fmaf(rv[mm].x, rv[mm].x, fmaf(rv[mm].y, rv[mm].y, nrm));
-            a.dict_norm[(t0 + i) % D] = nrm;
+            a.dict_norm[(tb + t0 + i) % D] = nrm;
         }
         if (a.chunk == g.n_chunks - 1 && u == 0) {
-            a.meta[0] = min(g.P, D);
-            a.meta[1] = g.P >= D ? g.P % D : 0;
-            a.meta[2] = g.P;
+            const int total = tb + g.P;  // vectors trained on since the state was emptied
+            a.meta[0] = min(total, D);
+            a.meta[1] = total >= D ? total % D : 0;
+            a.meta[2] = total;
         }
     }
 }

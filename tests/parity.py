@@ -18,7 +18,8 @@ TOL_FP32 = 1e-4
 
 def gpu_params(op: oracle.Params, dtype="fp32") -> apsm.Params:
     return apsm.Params(M=op.M, K=op.K, window=op.W, dict_cap=op.D, sigma=op.sigma, mu=op.mu, eps=op.eps,
-                       w_L=op.w_L, dtype=dtype)
+                       w_L=op.w_L, dtype=dtype, modulation=op.qam_bits,
+                       weights="violated" if op.weights == 1 else "uniform")
 
 
 def to_dev(a, dtype=None):
@@ -60,12 +61,22 @@ def assert_soft_close(y, ref, tol=TOL_FP32, what="soft"):
     return float(err.max()) if err.size else 0.0
 
 
-def assert_hard_match(hard, ref_soft, tol=TOL_FP32):
+def boundary_distance(y, bits=2):
+    """Distance of real values y to the nearest decision boundary (2b - L) a of one Gray-QAM axis."""
+    L = 1 << (bits // 2)
+    a = oracle.pam_scale(bits)
+    bnd = np.array([(2 * b - L) * a for b in range(1, L)])
+    return np.min(np.abs(np.asarray(y, np.float64)[..., None] - bnd), axis=-1)
+
+
+def assert_hard_match(hard, ref_soft, tol=TOL_FP32, bits=2):
+    """Gray-QAM labels identical except where the FP64 value's deciding component lies within
+    tol * rms of a decision boundary."""
     ref_soft = np.asarray(ref_soft)
-    ref_hard = oracle.hard_qpsk(ref_soft)
+    ref_hard = oracle.hard_qam(ref_soft, bits)
     hard = np.asarray(hard)
     _, rms = rel_errors(ref_soft, ref_soft)
-    near = (np.abs(ref_soft.real) < tol * rms) | (np.abs(ref_soft.imag) < tol * rms)
+    near = (boundary_distance(ref_soft.real, bits) < tol * rms) | (boundary_distance(ref_soft.imag, bits) < tol * rms)
     bad = (hard != ref_hard) & ~near
     assert not bad.any(), f"{int(bad.sum())} hard decisions differ away from a decision boundary"
 

@@ -60,6 +60,7 @@ def test_dict_alloc_rounds_to_whole_tiles(lib):
     (dict(sigma=0.0), 1), (dict(sigma=-1.0), 1), (dict(mu=0.0), 1), (dict(mu=2.5), 1), (dict(eps=-0.1), 1),
     (dict(w_L=1.5), 1), (dict(window=0), 1), (dict(dict_cap=8, window=16), 1), (dict(K=0), 1),
     (dict(M=3), 2), (dict(M=128), 2), (dict(K=17), 2), (dict(window=129, dict_cap=4096), 2),
+    (dict(modulation=3), 1), (dict(modulation=8), 1),
 ])
 def test_parameter_validation(lib, bad, code):
     from paper_2201_05024_gb300 import apsm
@@ -78,7 +79,7 @@ def test_workspace_query(lib):
 
 def _cstate(ptr=256):
     from paper_2201_05024_gb300 import apsm
-    return apsm._CState(ptr, ptr, ptr, ptr, ptr)
+    return apsm._CState(ptr, ptr, ptr, ptr, ptr, ptr)
 
 
 def test_null_pointers_rejected_before_device(lib):
@@ -100,7 +101,7 @@ def test_misaligned_arrays_rejected_before_device(lib):
     p = params().c()
     good = _cstate(256)
     from paper_2201_05024_gb300 import apsm
-    bad_state = apsm._CState(256 + 8, 256, 256, 256, 256)     # dict only 8-byte aligned
+    bad_state = apsm._CState(256 + 8, 256, 256, 256, 256, 256)     # dict only 8-byte aligned
     rc = lib.apsm_detect(ctypes.byref(p), ctypes.byref(bad_state), ctypes.c_void_p(256), 4, ctypes.c_void_p(256),
                          None, None)
     assert rc == apsm.APSM_ERR_INVALID_ARG
@@ -160,3 +161,65 @@ def test_batch_create_validates_every_instance_first(lib):
     assert lib.apsm_batch_create(arr, 0, 4, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
     assert lib.apsm_batch_create(arr, 1, 0, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
     assert lib.apsm_batch_launch(None, None) == apsm.APSM_ERR_INVALID_ARG
+
+
+def test_parameter_validation_of_weights(lib):
+    from paper_2201_05024_gb300 import apsm
+    p = params().c()
+    p.weights = 2
+    out = ctypes.c_int32()
+    assert lib.apsm_dict_alloc(ctypes.byref(p), ctypes.byref(out)) == apsm.APSM_ERR_INVALID_ARG
+    for ok in (0, 1):
+        p.weights = ok
+        assert lib.apsm_dict_alloc(ctypes.byref(p), ctypes.byref(out)) == apsm.APSM_OK
+    for m in (0, 2, 4, 6):
+        assert apsm.dict_alloc(params(modulation=m)) == 1024
+
+
+def test_state_without_targets_rejected(lib):
+    from paper_2201_05024_gb300 import apsm
+    p = params().c()
+    st = apsm._CState(256, 256, 256, 256, 256, None)
+    assert lib.apsm_detect(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(256), 4, ctypes.c_void_p(256),
+                           None, None) == apsm.APSM_ERR_INVALID_ARG
+    st = apsm._CState(256, 256, 256, 256, 256, 256 + 4)        # targets not 8-byte aligned
+    assert lib.apsm_detect(ctypes.byref(p), ctypes.byref(st), ctypes.c_void_p(256), 4, ctypes.c_void_p(256),
+                           None, None) == apsm.APSM_ERR_INVALID_ARG
+
+
+def test_continue_validation_before_device(lib):
+    from paper_2201_05024_gb300 import apsm
+    p = params().c()
+    st = _cstate()
+    nb = ctypes.c_size_t()
+    assert lib.apsm_train_continue_workspace_bytes(ctypes.byref(p), 256, ctypes.byref(nb)) == 0
+    assert nb.value >= apsm.train_workspace_bytes(params(), 256)   # room for the carried window
+    ws = ctypes.c_void_p(256)
+    call = lambda P, n_prev, rx, size: lib.apsm_train_continue(ctypes.byref(p), rx, None, P, n_prev,
+                                                               ctypes.byref(st), ws, size, None, None, None, None)
+    assert call(64, -1, ctypes.c_void_p(256), nb.value) == apsm.APSM_ERR_INVALID_ARG   # n_prev < 0
+    assert call(-1, 0, ctypes.c_void_p(256), nb.value) == apsm.APSM_ERR_INVALID_ARG
+    assert call(64, 0, None, nb.value) == apsm.APSM_ERR_INVALID_ARG                    # no vectors
+    assert call(64, 100, ctypes.c_void_p(256), 16) == apsm.APSM_ERR_WORKSPACE
+    assert call(64, 100, ctypes.c_void_p(256 + 8), nb.value) == apsm.APSM_ERR_INVALID_ARG  # misaligned rx
+
+
+def test_linear_init_validation_before_device(lib):
+    from paper_2201_05024_gb300 import apsm
+    p = params().c()
+    f = lib.apsm_linear_init
+    v = ctypes.c_void_p(256)
+    assert f(ctypes.byref(p), v, v, 5, ctypes.c_float(0.1), v, None) == apsm.APSM_ERR_INVALID_ARG      # P < K
+    assert f(ctypes.byref(p), v, v, 64, ctypes.c_float(-0.1), v, None) == apsm.APSM_ERR_INVALID_ARG    # N0 < 0
+    assert f(ctypes.byref(p), None, v, 64, ctypes.c_float(0.1), v, None) == apsm.APSM_ERR_INVALID_ARG
+    q = params(w_L=0.0).c()
+    assert f(ctypes.byref(q), v, v, 64, ctypes.c_float(0.1), v, None) == apsm.APSM_ERR_INVALID_ARG      # w_L = 0
+
+
+def test_set_option_validation(lib):
+    from paper_2201_05024_gb300 import apsm
+    assert lib.apsm_set_option(0, 64) == apsm.APSM_OK
+    assert lib.apsm_set_option(1, 1) == apsm.APSM_OK
+    assert lib.apsm_set_option(0, 0) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_set_option(1, 2) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_set_option(7, 1) == apsm.APSM_ERR_INVALID_ARG

@@ -42,14 +42,15 @@ DETECT_CASES = [
 
 
 @pytest.fixture(params=["tensor", "ffma"])
-def engine(request, monkeypatch):
+def engine(request):
     """FP32 detection engine: Gram on the tensor cores (TF32 x3, the default where a kernel exists)
-    or on the FP32 FMA pipe."""
+    or on the FP32 FMA pipe (chosen for every class through the launch-choice table)."""
     if request.param == "ffma":
-        monkeypatch.setenv("APSM_DETECT_ENGINE", "ffma")
-    else:
-        monkeypatch.delenv("APSM_DETECT_ENGINE", raising=False)
-    return request.param
+        for M in (2, 4, 8, 16, 32, 64):
+            for K in range(1, 17):
+                apsm.tune_set(M, K, "fp32", "ffma", 64, 2, 1)
+    yield request.param
+    apsm.tune_clear()
 
 
 @pytest.mark.parametrize("M,K,D,N,sigma,wL", DETECT_CASES)
@@ -125,6 +126,89 @@ def test_detect_reduced_precision_matches_oracle(M, K, D, N, dtype):
     err = assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what=dtype)
     assert err > 1e-6  # really the reduced-precision path
     assert_hard_match(hard.cpu().numpy(), ref, tol=TOL_HALF)
+
+
+
+def _unnormalised(case, M, K):
+    """Inputs far outside the gain-controlled range (shared by the FP32 and BF16/FP16 checks)."""
+    D, N = 200, 700
+    rng = np.random.default_rng(11)
+    ent, gam, clin = synth.random_state(M, K, D, instance=5)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=6)
+    rx = inst.rx_data.copy()
+    sigma = 0.5
+    if case == "offset":
+        base = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) * 1.6
+        ent = (ent + base).astype(np.complex64)
+        rx = (rx * 0.5 + base).astype(np.complex64)
+        sigma = 0.8
+    elif case == "mixed_entries":
+        ent = ent.copy()
+        ent[64:128] *= 6.0                      # tiles 2 and 3 out of range
+    else:
+        rx[::97] *= 5.0                          # a few queries out of range
+    return ent, gam, clin, rx, sigma
+
+
+def _bf16(x):
+    """Round-to-nearest-even BF16 of float32 values (test-side emulation, for the regression check)."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def _unguarded_bf16_detect(M, K, ent, gam, clin, rx, sigma, w_L):
+    """What a BF16 Gram with the norm expansion alone would return (no direct-difference fallback):
+    exponent 2 k2 Re/Im z from BF16-rounded operands, minus k2 (n_s + n_t) in FP64."""
+    k2 = 1.0 / (2 * sigma * sigma)
+    q = rx.astype(np.complex128)
+    e = ent.astype(np.complex128)
+    qa = _bf16(np.concatenate([q.real, q.imag], 1) * 2 * k2).astype(np.float64)
+    ea = _bf16(np.concatenate([e.real, e.imag], 1)).astype(np.float64)
+    eb = _bf16(np.concatenate([-e.imag, e.real], 1)).astype(np.float64)
+    vr, vi = qa @ ea.T, qa @ eb.T                     # 2 k2 Re z, 2 k2 Im z
+    h = k2 * (np.sum(np.abs(q) ** 2, 1)[:, None] + np.sum(np.abs(e) ** 2, 1)[None, :])
+    EA, EB, EC = np.exp(vr - h), np.exp(vi - h), np.exp(-vi - h)
+    g1, g2 = gam[:, 0, :].astype(np.float64), gam[:, 1, :].astype(np.float64)
+    lin = q @ np.conj(clin.astype(np.complex128))
+    y1 = w_L * lin.real + (1 - w_L) * (EA @ g1 + EC @ g2)
+    y2 = w_L * lin.imag + (1 - w_L) * (EB @ g1 + EA @ g2)
+    return y1 + 1j * y2
+
+
+@pytest.mark.parametrize("M,K", [(16, 6), (64, 5)])
+@pytest.mark.parametrize("case", ["offset", "mixed_entries", "mixed_queries"])
+@pytest.mark.parametrize("dtype", ["bf16", "fp16"])
+def test_detect_reduced_precision_unnormalised_inputs(case, M, K, dtype):
+    """BF16/FP16 Gram on inputs outside the gain-controlled range: the pairs where the norm
+    expansion cancels (smallest distance below 2^-4 k2 (||r||^2 + ||r_t||^2)) are recomputed by
+    direct differences in FP32, so the result stays within 2e-2 of the FP64 oracle."""
+    ent, gam, clin, rx, sigma = _unnormalised(case, M, K)
+    op = oracle.Params(M=M, K=K, W=1, D=ent.shape[0], sigma=sigma, w_L=0.5)
+    gp = gpu_params(op, dtype=dtype)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, to_dev(rx))
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), rx)
+    assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what=f"{dtype} {case}")
+    assert_hard_match(hard.cpu().numpy(), ref, tol=TOL_HALF)
+    assert apsm.read_status(st) == 0
+
+
+def test_direct_difference_fallback_regression():
+    """The offset case at 16 antennas: with a BF16 Gram and the norm expansion alone (emulated on
+    the CPU) the error is far above the 2e-2 tolerance -- the case needs the fallback -- while
+    the GPU's guarded BF16 path stays within it."""
+    M, K = 16, 6
+    ent, gam, clin, rx, sigma = _unnormalised("offset", M, K)
+    op = oracle.Params(M=M, K=K, W=1, D=ent.shape[0], sigma=sigma, w_L=0.5)
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), rx)
+    from parity import rel_errors
+    unguarded, _ = rel_errors(_unguarded_bf16_detect(M, K, ent, gam, clin, rx, sigma, 0.5), ref)
+    assert unguarded.max() > 5 * TOL_HALF
+    gp = gpu_params(op, dtype="bf16")
+    st = load_state(gp, ent, gam, clin)
+    soft, _ = apsm.detect(gp, st, to_dev(rx))
+    assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what="guarded bf16")
 
 
 def test_detect_empty_dictionary_is_linear_filter():
@@ -242,37 +326,23 @@ def test_train_matches_oracle(M, K, P, W, D, sigma, mu, eps, wL, N):
 
 
 @pytest.mark.parametrize("M,K,P,W,D", [(16, 6, 600, 16, 200), (8, 3, 333, 8, 1000), (4, 2, 100, 8, 20)])
-def test_tracked_and_sequential_training_agree(M, K, P, W, D, monkeypatch):
+def test_tracked_and_sequential_training_agree(M, K, P, W, D):
     """The next-chunk tracking form (frozen-entry phase A beside phase B) and the sequential form
     (whole-dictionary phase A between chunks) compute the same recurrence; both match the oracle."""
     inst = synth.make_instance(M, K, P, 200, 10.0, instance=7 * P + D)
     op = oracle.Params(M=M, K=K, W=W, D=D)
     results = []
-    for track in ("1", "0"):
-        monkeypatch.setenv("APSM_TRAIN_TRACK", track)
-        gp, st, cl, ref = _train_both(op, inst)
-        _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
-        results.append((st.gamma.cpu().numpy(), st.clin.cpu().numpy()))
+    try:
+        for track in (1, 0):
+            apsm.set_option("train_track", track)
+            gp, st, cl, ref = _train_both(op, inst)
+            _compare_training(op, inst, gp, st, cl, ref, tol_coef=1e-4)
+            results.append((st.gamma.cpu().numpy(), st.clin.cpu().numpy()))
+    finally:
+        apsm.set_option("train_track", 1)
     (g1, c1), (g0, c0) = results
     assert np.abs(g1 - g0).max() <= 1e-4 * rms(g0)
     assert np.abs(c1 - c0).max() <= 1e-4 * rms(np.abs(c0))
-
-
-@pytest.mark.parametrize("M,K,D,N", [(16, 6, 1024, 3000), (4, 2, 37, 500), (32, 12, 200, 700), (8, 16, 65, 300)])
-def test_detect_coefficient_sums_on_tensor_cores(M, K, D, N, monkeypatch):
-    """The opt-in FP32 path with both contractions on the tensor cores (E x G with E read from
-    tensor memory) against the oracle, including ragged tiles and the 12- and 16-user buckets."""
-    monkeypatch.setenv("APSM_DETECT_TC_COEF", "1")
-    ent, gam, clin = synth.random_state(M, K, D, instance=M * K + D)
-    inst = synth.make_instance(M, K, 4, N, 10.0, instance=N + K)
-    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.5, w_L=0.5)
-    gp = gpu_params(op)
-    st = load_state(gp, ent, gam, clin)
-    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
-    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
-    assert_soft_close(soft.cpu().numpy(), ref, what="tensor-core coefficient sums")
-    assert_hard_match(hard.cpu().numpy(), ref)
-    assert apsm.read_status(st) == 0
 
 
 def test_train_with_initial_linear_filter():

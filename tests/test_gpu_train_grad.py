@@ -19,6 +19,8 @@ CASES = [
     (4, 2, 40, 4, 40, 150, 0.6, 0.5, 0.05, 0.5),     # no eviction, two checkpoint segments
     (4, 2, 70, 6, 12, 150, 0.6, 0.7, 0.05, 0.4),     # FIFO eviction
     (8, 3, 33, 3, 33, 120, 0.5, 0.9, 0.02, 0.6),     # (mu = 1 lands residuals exactly on the slab edge)
+    (16, 6, 256, 8, 256, 512, 0.5, 0.5, 0.01, 0.5),  # the differentiation-form shape: 8 checkpoint
+                                                     # segments, one warp per window slot at W = 8
 ]
 
 
