@@ -23,7 +23,7 @@ DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
 DetectBwdLauncher detect_bwd_launcher(int M, int K);  // detect_f32_m*.cu
 TcLauncher detect_tc_launcher(int M, int K, int prec);  // detect_tc_m*.cu
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
-ChunkLauncher chunk_launcher(int S, int WP);        // train_chunk.cu
+ChunkLauncher chunk_launcher(int S, int WP, bool ext);  // train_chunk.cu
 int padded_window(int W);                           // train_chunk.cu
 
 namespace {
@@ -247,6 +247,27 @@ float qam_a_of(const apsm_params *p) {
     return (float)std::sqrt(3.0 / (2.0 * ((double)L * L - 1.0)));
 }
 
+// Gray square-QAM labels of soft outputs (the same FP32 values the detection wrote).
+__global__ void qam_label_kernel(const float2 *__restrict__ soft, uint8_t *__restrict__ hard, long long n, int half,
+                                 float a) {
+    pdl_enter();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 y = soft[i];
+        hard[i] = qam_label(y.x, y.y, half, a);
+    }
+}
+
+apsm_status qam_labels(float *soft, uint8_t *hard, int N, const apsm_params *p, cudaStream_t strm) {
+    const long long n = (long long)N * p->K;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>(4 * num_sms(), (n + 255) / 256));
+    if (launch_pdl(qam_label_kernel, dim3(blocks), dim3(256), 0, strm, reinterpret_cast<const float2 *>(soft), hard,
+                   n, qam_half_of(p), qam_a_of(p)) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess)
+        return APSM_ERR_CUDA;
+    g_launches++;
+    return APSM_OK;
+}
+
 __global__ void state_set_kernel(const float2 *__restrict__ entries, const float *__restrict__ gamma,
                                  const float2 *__restrict__ clin, const float2 *__restrict__ target, int n, int M,
                                  int K, float2 *dict, float *dict_norm, float *gam_out, float2 *clin_out,
@@ -404,7 +425,9 @@ apsm_status train_run(const apsm_params *p, const float *rx_in, const float *sym
     DetectLauncher det = detect_f32_launcher(p->M, p->K);
     if (!det) return APSM_ERR_UNSUPPORTED;
     const ChunkSmem layout(g);
-    const ChunkLauncher chunk = chunk_launcher(g.RS / 32, g.WP);
+    // the extended instantiation only for the modes that need it
+    const bool ext_modes = decide || soft != nullptr || hard != nullptr || p->weights == APSM_Q_VIOLATED;
+    const ChunkLauncher chunk = chunk_launcher(g.RS / 32, g.WP, ext_modes);
     if (!chunk) return APSM_ERR_UNSUPPORTED;
 
     // phase A: the partial Gaussian sums of f, at the extended pilots [q0, q0 + nq), over the
@@ -427,8 +450,6 @@ apsm_status train_run(const apsm_params *p, const float *rx_in, const float *sym
         da.partial = dst;
         da.pdl_late = late ? 1 : 0;
         da.status = st->meta + 3;
-        da.qam_half = 1;
-        da.qam_a = 1.f;
         const int first = lo % g.D, hi0 = std::min(g.D, first + n), hi1 = first + n - g.D;
         da.seg0_lo = first;
         da.seg0_hi = hi0;
@@ -593,6 +614,9 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     if ((s = check_device()) != APSM_OK) return s;
     if (N == 0) return APSM_OK;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
+    // square-QAM labels: the detection kernel writes QPSK decisions only; labels of larger
+    // constellations are formed from the soft outputs by one extra pass
+    const bool qam_pass = hard != nullptr && qam_half_of(p) > 1;
     // Engine: the Gram on the tensor cores (TF32 x3 for FP32, BF16/FP16 as requested) where a
     // kernel exists for (M, K); FFMA otherwise, or where the tuning table chose it for FP32.
     const TuneEntry te = tune_get(p->M, p->K, p->dtype);
@@ -618,11 +642,10 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
             ta.soft = reinterpret_cast<float2 *>(soft);
             ta.hard = hard;
             ta.status = st->meta + 3;
-            ta.qam_half = qam_half_of(p);
-            ta.qam_a = qam_a_of(p);
+            if (qam_pass) ta.hard = nullptr;
             if (tc(ta, strm) != cudaSuccess) return APSM_ERR_CUDA;
             g_launches++;
-            return APSM_OK;
+            return qam_pass ? qam_labels(soft, hard, N, p, strm) : APSM_OK;
         }
         if (p->dtype != APSM_FP32) return APSM_ERR_UNSUPPORTED;
     }
@@ -645,12 +668,11 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     da.hard = hard;
     da.partial = nullptr;
     da.status = st->meta + 3;
-    da.qam_half = qam_half_of(p);
-    da.qam_a = qam_a_of(p);
+    if (qam_pass) da.hard = nullptr;
     const DetectShape sh = detect_shape(p->M, p->K, p->dtype);
     if (det(da, 1, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches++;
-    return APSM_OK;
+    return qam_pass ? qam_labels(soft, hard, N, p, strm) : APSM_OK;
 }
 
 apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,

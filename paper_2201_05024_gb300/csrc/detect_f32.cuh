@@ -63,8 +63,6 @@ struct DetectArgs {
     uint8_t *hard;             // [N][K] nullable
     float *partial;            // [gridDim.y][N][2K] partial mode (full mode: nullptr)
     int *status;               // device status word
-    int qam_half;              // bits per axis of the Gray-QAM decisions
-    float qam_a;               // amplitude unit of one axis
     // Optional slot segments (partial mode): when seg0_hi or seg1_hi is nonzero, grid.y slices
     // [0, seg_slices) cover slots [seg0_lo, seg0_hi) and the rest cover [seg1_lo, seg1_hi), each
     // segment sliced from its first 32-slot tile boundary; slots below a segment start are masked.
@@ -459,7 +457,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
             const float y1 = fmaf(a.wL * inv_g2, l1, a.wG * fq * acc1[i][j]);
             const float y2 = fmaf(a.wL * inv_g2, l2, a.wG * fq * acc2[i][j]);
             if (live && (QS == 1 || part * KH + j < K)) a.soft[(size_t)q * K + k] = make_float2(y1, y2);
-            hbits[j] = qam_label(y1, y2, a.qam_half, a.qam_a);
+            hbits[j] = (unsigned char)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));  // QPSK (QAM: separate pass)
         }
         if (a.hard && live) {
 #pragma unroll

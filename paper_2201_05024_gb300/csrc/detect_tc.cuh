@@ -16,6 +16,9 @@
 //            hi = tf32(x), lo = tf32(x - hi) (relative error of the Gram ~2^-21);
 //   kHalf    one BF16 or FP16 product per k-step (runtime choice), FP32 accumulation.
 //
+// Hard decisions here are QPSK (sign test); square-QAM labels are formed from the soft outputs by
+// a separate pass (apsm_api.cu), so that this loop compiles the same for every modulation.
+//
 // Roles (256 threads): warps 0-3 = epilogue (query row = thread; coefficient sums over user
 // pairs with packed f32x2 FMAs), warps 4-7 = converters (entry rows of B by whole 16-byte core
 // rows where M allows, the tile's coefficients and norms; thread 128 issues the MMAs; the next
@@ -60,8 +63,6 @@ struct TcArgs {
     float2 *soft;             // [N][K]
     uint8_t *hard;            // [N][K] nullable
     int *status;
-    int qam_half;             // bits per axis of the Gray-QAM decisions
-    float qam_a;              // amplitude unit of one axis
 };
 
 // Operand layout: K-major, no swizzle; core matrix = 8 rows x 16 bytes.  KD = contraction
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                 y1 = fmaf(a.wL, l1, a.wG * fq * y1);
                 y2 = fmaf(a.wL, l2, a.wG * fq * y2);
                 a.soft[(size_t)s * a.K + k] = make_float2(y1, y2);
-                if (a.hard) a.hard[(size_t)s * a.K + k] = qam_label(y1, y2, a.qam_half, a.qam_a);
+                if (a.hard) a.hard[(size_t)s * a.K + k] = (uint8_t)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
             }
         }
     }

@@ -118,11 +118,16 @@ cudaError_t launch_train_gram(const float2 *rx, const float2 *dict, const TrainG
 }
 
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
-ChunkLauncher chunk_launcher_s1(int WP);  // train_chunk_s*.cu: one translation unit per S
-ChunkLauncher chunk_launcher_s2(int WP);
-ChunkLauncher chunk_launcher_s3(int WP);
-ChunkLauncher chunk_launcher_s4(int WP);
-ChunkLauncher chunk_launcher_s5(int WP);
+ChunkLauncher chunk_launcher_s1_x0(int WP);
+ChunkLauncher chunk_launcher_s1_x1(int WP);  // train_chunk_s*{p,x}.cu: one translation unit per (S, plain or extended)
+ChunkLauncher chunk_launcher_s2_x0(int WP);
+ChunkLauncher chunk_launcher_s2_x1(int WP);
+ChunkLauncher chunk_launcher_s3_x0(int WP);
+ChunkLauncher chunk_launcher_s3_x1(int WP);
+ChunkLauncher chunk_launcher_s4_x0(int WP);
+ChunkLauncher chunk_launcher_s4_x1(int WP);
+ChunkLauncher chunk_launcher_s5_x0(int WP);
+ChunkLauncher chunk_launcher_s5_x1(int WP);
 
 // Smallest supported padded window >= W (0 if W is too large).
 int padded_window(int W) {
@@ -132,13 +137,13 @@ int padded_window(int W) {
     return 0;
 }
 
-ChunkLauncher chunk_launcher(int S, int WP) {
+ChunkLauncher chunk_launcher(int S, int WP, bool ext) {
     switch (S) {
-        case 1: return chunk_launcher_s1(WP);
-        case 2: return chunk_launcher_s2(WP);
-        case 3: return chunk_launcher_s3(WP);
-        case 4: return chunk_launcher_s4(WP);
-        case 5: return chunk_launcher_s5(WP);
+        case 1: return ext ? chunk_launcher_s1_x1(WP) : chunk_launcher_s1_x0(WP);
+        case 2: return ext ? chunk_launcher_s2_x1(WP) : chunk_launcher_s2_x0(WP);
+        case 3: return ext ? chunk_launcher_s3_x1(WP) : chunk_launcher_s3_x0(WP);
+        case 4: return ext ? chunk_launcher_s4_x1(WP) : chunk_launcher_s4_x0(WP);
+        case 5: return ext ? chunk_launcher_s5_x1(WP) : chunk_launcher_s5_x0(WP);
         default: return nullptr;
     }
 }

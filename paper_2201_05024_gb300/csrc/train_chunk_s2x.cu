@@ -1,0 +1,4 @@
+// Phase-B training kernels for S = 2 live-range warps, extended instantiations.
+#define APSM_CHUNK_S 2
+#define APSM_CHUNK_EXT 1
+#include "train_chunk_inst.cuh"

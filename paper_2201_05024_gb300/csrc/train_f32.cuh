@@ -155,8 +155,11 @@ constexpr int kBlockMin = 8;  // shortest step block of the blocked form (padded
 // (RS = 32 S threads); a step is one CTA barrier: window threads publish their beta, then every
 // thread adds the window's contribution to its own prediction.  WP is the window rounded up to a
 // multiple of 4; the WP slots below the window hold zero so the sum has a fixed length.
-template <int S, int WP>
-__global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) {
+// kExt: the instantiation that also serves violated-slab weights, outputs at arrival and
+// decision-directed targets; the plain one (kExt = false) compiles none of that into its step
+// loops, which keeps the recurrence's code as small as the method itself needs.
+template <int S, int WP, bool kExt>
+__global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int RS = 32 * S;
     if (a.pdl_mode == 0) {
@@ -204,6 +207,16 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
     __syncthreads();  // the barrier's initialisation is visible before any thread waits on it
     const bool valid = u < R;
     const int m = l0 + u, pa = m >> 1, l = m & 1;
+    // targets: given ones are read at once; decided ones only after the wait below (the previous
+    // chunk decides the carried samples' targets)
+    float b = 0.f;
+    auto read_target = [&]() {
+        if (valid) {
+            const float2 sy = a.sym[(size_t)pa * K + k];
+            b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
+        }
+    };
+    if (!a.decide) read_target();
     for (int i = u; i < 2 * (WP + RS); i += RS) s_beta[i] = 0.f;
     for (int i = u; i < WP * RS; i += RS) s_kmat[i - WP * RS] = 0.f;
     float rk = 0.f;  // 1 / kappa(x_j, x_j)
@@ -226,12 +239,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
         pdl_trigger();
     }
     // every global load of the prologue is issued before the first use (one round trip)
-    // (targets after the wait: in decision-directed mode the previous chunk decided them)
-    float b = 0.f;
-    if (valid) {
-        const float2 sy = a.sym[(size_t)pa * K + k];
-        b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
-    }
+    if (a.decide) read_target();
     float2 clin_r[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // M <= 64 <= 2 RS
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -462,7 +470,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                             pl -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + col],
                                               s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + col]);
                         }
-                        if (kChecked && lane == s + WP - 1) {  // sample n arrives: pl = f_n(x_n)
+                        if (kExt && kChecked && lane == s + WP - 1) {  // sample n arrives: pl = f_n(x_n)
                             if (a.soft_out) a.soft_out[((size_t)((n - n_first) >> 1) * K + k) * 2 + (n & 1)] = pl;
                             if (a.decide) {  // its target: the decision on the filter's own output
                                 bl = pam_value(pam_level(pl, a.qam_half, a.qam_a), a.qam_half, a.qam_a);
@@ -505,10 +513,12 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 };
                 using T_ = std::true_type;
                 using F_ = std::false_type;
-                const bool checked = n0 + B > s1 || n0 + sb < W - 1 || log_cases || a.decide || a.soft_out;
-                if (a.qviol) {
-                    if (evict) steps(T_{}, T_{}, T_{});
-                    else steps(T_{}, F_{}, T_{});
+                const bool checked = n0 + B > s1 || n0 + sb < W - 1 || log_cases || (kExt && (a.decide || a.soft_out));
+                if (kExt && a.qviol) {
+                    if constexpr (kExt) {
+                        if (evict) steps(T_{}, T_{}, T_{});
+                        else steps(T_{}, F_{}, T_{});
+                    }
                 } else if (evict) {
                     if (checked) steps(T_{}, T_{}, F_{});
                     else steps(F_{}, T_{}, F_{});
@@ -580,7 +590,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                     p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u],
                                      s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
                 }
-                if (valid && m == n) {  // sample n arrives: p = f_n(x_n)
+                if (kExt && valid && m == n) {  // sample n arrives: p = f_n(x_n)
                     if (a.soft_out) a.soft_out[((size_t)((n - n_first) >> 1) * K + k) * 2 + (n & 1)] = p;
                     if (a.decide) b = pam_value(pam_level(p, a.qam_half, a.qam_a), a.qam_half, a.qam_a);
                 }
@@ -601,7 +611,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                     }
                     ring[slot] = beta;
                 }
-                if (a.qviol) {  // q = 1/|V_n| on the violated slabs
+                if (kExt && a.qviol) {  // q = 1/|V_n| on the violated slabs
                     const int nv = __syncthreads_count(viol);
                     muq = nv > 0 ? a.mu / (float)nv : 0.f;
                 } else {
@@ -629,7 +639,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
                 const int e = (n >> 1) - t0;
                 p -= a.wG * fmaf(s_egam[2 * e], s_gev[e * 2 * RS + u], s_egam[2 * e + 1] * s_gev[(e * 2 + 1) * RS + u]);
             }
-            if (valid && m == n) {  // sample n arrives: p = f_n(x_n)
+            if (kExt && valid && m == n) {  // sample n arrives: p = f_n(x_n)
                 if (a.soft_out) a.soft_out[((size_t)((n - n_first) >> 1) * K + k) * 2 + (n & 1)] = p;
                 if (a.decide) b = pam_value(pam_level(p, a.qam_half, a.qam_a), a.qam_half, a.qam_a);
             }
@@ -650,7 +660,7 @@ __global__ void __launch_bounds__(32 * S) train_chunk_kernel(const ChunkArgs a) 
             } else if (u < ujlo && u > un - WP) {
                 bb[u] = 0.f;
             }
-            if (a.qviol) {  // q = 1/|V_n| on the violated slabs
+            if (kExt && a.qviol) {  // q = 1/|V_n| on the violated slabs
                 const int nv = __syncthreads_count(viol);
                 muq = nv > 0 ? a.mu / (float)nv : 0.f;
             } else {
