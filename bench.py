@@ -300,6 +300,15 @@ def run_batched(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    # the detection phase alone (one persistent launch per class), on the trained states
+    evd = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in evd:
+        a.record(stream)
+        batch.launch_detect()
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms_det = sum(a.elapsed_time(b) for a, b in evd) / args.steps
+    n_classes, n_batched = batch.info()
     n_vec = sum(s["N"] for s in shapes)
     n_pil = sum(s["D"] * s["K"] for s in shapes)
     pairs = sum(s["N"] * s["D"] for s in shapes)
@@ -314,6 +323,9 @@ def run_batched(args):
                    "l2": "inputs larger than L2 (%.1f GB of data vectors)" % (n_vec * 8 * 16 / 1e9)},
         "train": {"value": n_pil / (ms / 1e3), "unit": "pilot-updates/s (within the same step)"},
         "pairs_per_s": pairs / (ms / 1e3),
+        "detect_phase": {"ms": ms_det, "pairs_per_s": pairs / (ms_det / 1e3), "classes": n_classes,
+                         "instances_persistent": n_batched,
+                         "roofline": batched_roofline(shapes, ms_det / 1e3)},
         "graph": {"build_s": t_graph, "inputs_s": t_gen},
         "instances_with_status": bad, "clocks": clocks,
     }
@@ -344,6 +356,27 @@ def run_batched(args):
                                                            f"each ({t_cpu:.1f} s), extrapolated by pair work"}
         out["err_vs_fp64"] = {"max_scaled": max(errs), "instances": sample}
     print(json.dumps(out))
+
+
+def batched_roofline(shapes, seconds):
+    """Roofline of the persistent detection phase over uneven instances: per resource the summed
+    algorithmic work of every instance (as in detect_roofline, TF32 x3 Gram), against one peak."""
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    tensor = alu = mufu = 0.0
+    for s in shapes:
+        pairs = s["N"] * s["D"]
+        tensor += 3 * 2 * (2 * s["M"]) * 2 * pairs
+        alu += 2 * (4 * s["K"] + 3) * pairs
+        mufu += 3 * pairs
+    res = {"tensor": (tensor, bf16 * (1.1 / 2.25) * 1e12, "TFLOP/s"), "alu": (alu, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s"),
+           "mufu": (mufu, MUFU_PEAK_PER_S, "Gex2/s")}
+    tmin = {k: v[0] / v[1] for k, v in res.items()}
+    bound = max(tmin, key=tmin.get)
+    work, peak, unit = res[bound]
+    scale = 1e12 if unit == "TFLOP/s" else 1e9
+    return {"bound": bound, "achieved": work / seconds / scale, "peak": peak / scale, "unit": unit,
+            "frac": tmin[bound] / seconds, "frac_by_resource": {k: round(v / seconds, 4) for k, v in tmin.items()}}
 
 
 def _time_events(fn, steps, warmup):

@@ -340,15 +340,36 @@ typedef struct {
 typedef struct apsm_batch_s *apsm_batch;
 
 /*
- * Record, into one CUDA graph, apsm_train (from f_0 = 0) followed by apsm_detect for every
- * instance; instances are spread over `lanes` (1..64) parallel graph branches, longest first,
- * each onto the currently least-loaded branch.  The descriptors (and the buffers they point to)
- * are bound at creation: apsm_batch_launch replays the same work on new data in the same
- * buffers.  Every instance is validated before anything is recorded.  The handle owns the graph.
+ * Bytes of device workspace apsm_batch_create needs for these instances (the work lists of the
+ * persistent detection launches; 0 when no instance is in the batched kernel's range).
  */
-apsm_status apsm_batch_create(const apsm_instance *inst, int32_t n, int32_t lanes, apsm_batch *out);
+apsm_status apsm_batch_workspace_bytes(const apsm_instance *inst, int32_t n, size_t *bytes);
+
+/*
+ * Record the whole batch into one CUDA graph:
+ *   training   -- apsm_train (from f_0 = 0) of every instance, spread over `lanes` (1..64) parallel
+ *                 graph branches, longest first, each onto the currently least-loaded branch;
+ *   detection  -- per class (antenna count, user bucket of K) ONE persistent launch whose resident
+ *                 CTAs take (instance, 128-vector tile) work items from a device counter, listed
+ *                 longest instance first, until none is left (the counters are reset by memset
+ *                 nodes of the graph).  This covers FP32 detection up to 32 antennas with QPSK
+ *                 decisions (or no hard output) in classes the launch-choice table does not give
+ *                 to the FMA engine; any other instance is detected by apsm_detect on its
+ *                 branch after its training.  Per instance the outputs equal apsm_train followed
+ *                 by apsm_detect bit for bit.
+ * The descriptors (and the buffers they point to) are bound at creation: apsm_batch_launch replays
+ * the same work on new data in the same buffers.  Every instance is validated before anything is
+ * recorded.  workspace: apsm_batch_workspace_bytes bytes, 256-byte aligned, caller-owned, kept
+ * for the life of the batch (written once here, synchronously).  The handle owns the graphs.
+ */
+apsm_status apsm_batch_create(const apsm_instance *inst, int32_t n, int32_t lanes, void *workspace,
+                              size_t workspace_bytes, apsm_batch *out);
 /* Launch the whole batch (one graph launch) on `stream`. */
 apsm_status apsm_batch_launch(apsm_batch b, void *stream);
+/* Launch only the persistent detection phase (a second graph; for timing it alone). */
+apsm_status apsm_batch_launch_detect(apsm_batch b, void *stream);
+/* Number of classes detected by persistent launches and of instances in them. */
+apsm_status apsm_batch_info(apsm_batch b, int32_t *n_classes, int32_t *n_batched);
 apsm_status apsm_batch_destroy(apsm_batch b);
 
 /* Read and clear the device status word meta[3] in one atomic exchange enqueued on `stream`,

@@ -85,8 +85,11 @@ def load_library(path: str | None = None):
         lib.apsm_train_backward.argtypes = [P, vp, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.apsm_tune_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
         lib.apsm_tune_clear.argtypes = []
-        lib.apsm_batch_create.argtypes = [ctypes.POINTER(_CInstance), i32, i32, ctypes.POINTER(vp)]
+        lib.apsm_batch_workspace_bytes.argtypes = [ctypes.POINTER(_CInstance), i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.apsm_batch_create.argtypes = [ctypes.POINTER(_CInstance), i32, i32, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
         lib.apsm_batch_launch.argtypes = [vp, vp]
+        lib.apsm_batch_launch_detect.argtypes = [vp, vp]
+        lib.apsm_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.apsm_batch_destroy.argtypes = [vp]
         lib.apsm_status_string.argtypes = [ctypes.c_int]
         lib.apsm_status_string.restype = ctypes.c_char_p
@@ -97,7 +100,8 @@ def load_library(path: str | None = None):
                   "apsm_train_backward_workspace_bytes", "apsm_train_backward",
                   "apsm_batch_launch", "apsm_batch_destroy", "apsm_check_wait_timeout",
                   "apsm_train_continue_workspace_bytes", "apsm_train_continue", "apsm_linear_init",
-                  "apsm_set_option"):
+                  "apsm_set_option", "apsm_batch_workspace_bytes", "apsm_batch_launch_detect",
+                  "apsm_batch_info"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -476,18 +480,34 @@ class BatchInstance:
 
 
 class Batch:
-    """apsm_batch: train + detect of many uneven instances replayed as one CUDA graph."""
+    """apsm_batch: train + detect of many uneven instances replayed as one CUDA graph (training on
+    parallel branches, detection as one persistent launch per class)."""
 
     def __init__(self, instances, lanes: int = 16):
         lib = load_library()
         self.instances = list(instances)   # keeps every buffer alive while the graph exists
         arr = (_CInstance * len(self.instances))(*[x.c() for x in self.instances])
+        nb = ctypes.c_size_t()
+        _check(lib.apsm_batch_workspace_bytes(arr, len(self.instances), ctypes.byref(nb)), "apsm_batch_workspace_bytes")
+        dev = self.instances[0].rx.device
+        self.workspace = torch.empty((max(nb.value, 1),), dtype=torch.uint8, device=dev)
         h = ctypes.c_void_p()
-        _check(lib.apsm_batch_create(arr, len(self.instances), lanes, ctypes.byref(h)), "apsm_batch_create")
+        _check(lib.apsm_batch_create(arr, len(self.instances), lanes, _ptr(self.workspace), self.workspace.numel(),
+                                     ctypes.byref(h)), "apsm_batch_create")
         self._h = h
 
     def launch(self):
         _check(load_library().apsm_batch_launch(self._h, _stream()), "apsm_batch_launch")
+
+    def launch_detect(self):
+        """Replay only the persistent detection phase."""
+        _check(load_library().apsm_batch_launch_detect(self._h, _stream()), "apsm_batch_launch_detect")
+
+    def info(self):
+        """(classes with a persistent detection launch, instances detected by them)."""
+        a, b = ctypes.c_int32(), ctypes.c_int32()
+        _check(load_library().apsm_batch_info(self._h, ctypes.byref(a), ctypes.byref(b)), "apsm_batch_info")
+        return a.value, b.value
 
     def close(self):
         if self._h:

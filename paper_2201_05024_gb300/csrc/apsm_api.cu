@@ -232,11 +232,11 @@ __global__ void train_ext_kernel(const float2 *__restrict__ rx, const float2 *__
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     for (int i = tid; i < (nc0 + P) * M; i += nthr) {
         const int e = i / M, m = i % M;
-        ext_rx[i] = e < nc0 ? dict[(size_t)((t_base + e) % D) * M + m] : rx[(size_t)(e - nc0) * M + m];
+        ext_rx[i] = e < nc0 ? __ldcg(dict + (size_t)((t_base + e) % D) * M + m) : rx[(size_t)(e - nc0) * M + m];
     }
     for (int i = tid; i < (nc0 + P) * K; i += nthr) {
         const int e = i / K, k = i % K;
-        ext_sym[i] = e < nc0 ? target[(size_t)((t_base + e) % D) * K + k]
+        ext_sym[i] = e < nc0 ? __ldcg(target + (size_t)((t_base + e) % D) * K + k)
                              : (sym ? sym[(size_t)(e - nc0) * K + k] : make_float2(0.f, 0.f));
     }
 }
@@ -252,7 +252,7 @@ __global__ void qam_label_kernel(const float2 *__restrict__ soft, uint8_t *__res
                                  float a) {
     pdl_enter();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float2 y = soft[i];
+        const float2 y = __ldcg(soft + i);
         hard[i] = qam_label(y.x, y.y, half, a);
     }
 }
@@ -340,6 +340,13 @@ __global__ void wait_timeout_check_kernel(int *status) {
 }
 
 }  // namespace
+
+// The launch-choice table forces the FMA engine for this class (batch.cu follows it).
+bool tune_forces_ffma(int M, int K, int dtype) {
+    const TuneEntry te = tune_get(M, K, dtype);
+    return te.set && te.engine == 1;
+}
+
 }  // namespace apsm
 
 using namespace apsm;

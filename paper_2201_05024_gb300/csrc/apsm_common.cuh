@@ -123,6 +123,12 @@ __device__ __forceinline__ void pdl_enter() {
     pdl_trigger();
 }
 
+// Reads of what another kernel of this library wrote (the state, training tables, carried
+// values, partial sums, soft outputs) go through L2: __ldcg or bulk copies, never the L1 /
+// read-only path.  A kernel launched this way can become resident on an SM beside the previous
+// kernel's CTAs, and an L1 line cached there before the previous kernel's other CTAs wrote the
+// data was observed to be read after the wait (the FMA detection engine behind training read a
+// stale linear filter and entry count until its loads went through L2).
 template <typename... KArgs, typename... Args>
 cudaError_t launch_pdl(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
                        Args... args) {

@@ -2,6 +2,7 @@
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "detect_tc.cuh"
+#include "detect_tc_batch.cuh"
 
 namespace apsm {
 
@@ -26,6 +27,13 @@ TcLauncher detect_tc_launcher_m16(int kb, int prec);
 TcLauncher detect_tc_launcher_m32(int kb, int prec);
 TcLauncher detect_tc_launcher_m64(int kb, int prec);
 
+TcBatchLauncher detect_tc_batch_launcher_m2(int kb, int *ctas_per_sm);
+TcBatchLauncher detect_tc_batch_launcher_m4(int kb, int *ctas_per_sm);
+TcBatchLauncher detect_tc_batch_launcher_m8(int kb, int *ctas_per_sm);
+TcBatchLauncher detect_tc_batch_launcher_m16(int kb, int *ctas_per_sm);
+TcBatchLauncher detect_tc_batch_launcher_m32(int kb, int *ctas_per_sm);
+TcBatchLauncher detect_tc_batch_launcher_m64(int kb, int *ctas_per_sm);
+
 // Smallest supported user bucket >= K for the tensor-core kernels (0 if none).
 int tc_user_bucket(int K) {
     static const int kB[] = {2, 4, 6, 8, 12, 16};
@@ -44,6 +52,21 @@ TcLauncher detect_tc_launcher(int M, int K, int prec) {
         case 16: return detect_tc_launcher_m16(kb, prec);
         case 32: return detect_tc_launcher_m32(kb, prec);
         case 64: return detect_tc_launcher_m64(kb, prec);
+        default: return nullptr;
+    }
+}
+
+// Batched persistent detection (FP32 accuracy) for class (M, user bucket of K); nullptr if none.
+TcBatchLauncher detect_tc_batch_launcher(int M, int K, int *ctas_per_sm) {
+    const int kb = tc_user_bucket(K);
+    if (!kb) return nullptr;
+    switch (M) {
+        case 2: return detect_tc_batch_launcher_m2(kb, ctas_per_sm);
+        case 4: return detect_tc_batch_launcher_m4(kb, ctas_per_sm);
+        case 8: return detect_tc_batch_launcher_m8(kb, ctas_per_sm);
+        case 16: return detect_tc_batch_launcher_m16(kb, ctas_per_sm);
+        case 32: return detect_tc_batch_launcher_m32(kb, ctas_per_sm);
+        case 64: return detect_tc_batch_launcher_m64(kb, ctas_per_sm);
         default: return nullptr;
     }
 }

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
     else pdl_enter();
 
     int n_ent = a.n_entries;
-    if (a.meta) n_ent = min(n_ent, max(__ldg(a.meta), 0));
+    if (a.meta) n_ent = min(n_ent, max(__ldcg(a.meta), 0));
     int e_begin, e_end, e_lo = 0;
     if (a.seg0_hi > 0 || a.seg1_hi > 0) {
         const bool second = (int)blockIdx.y >= a.seg_slices;
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
         fence_mbar_init();
     }
     if (a.partial == nullptr)
-        for (int i = tid; i < M * K; i += nthreads) s_clin[i] = a.clin[i];
+        for (int i = tid; i < M * K; i += nthreads) s_clin[i] = __ldcg(a.clin + i);
     __syncthreads();
     if (tid == 0) {
         if (n_tiles > 0) issue(0);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) detect_f32_kernel(const DetectArgs a) {
             const float4 *src = reinterpret_cast<const float4 *>(a.rx + (size_t)q * M + part * MH);
 #pragma unroll
             for (int m = 0; m < MH / 2; ++m) {
-                const float4 v = __ldg(src + m);
+                const float4 v = __ldcg(src + m);
                 r[i][2 * m] = make_float2(v.x, v.y);
                 r[i][2 * m + 1] = make_float2(v.z, v.w);
             }

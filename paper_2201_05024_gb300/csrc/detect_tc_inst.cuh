@@ -3,6 +3,7 @@
 #pragma once
 
 #include "detect_tc.cuh"
+#include "detect_tc_batch.cuh"
 
 #define APSM_TC_CAT2(a, b) a##b
 #define APSM_TC_CAT(a, b) APSM_TC_CAT2(a, b)
@@ -34,6 +35,24 @@ TcLauncher APSM_TC_CAT(detect_tc_launcher_m, APSM_TC_M)(int kb, int prec) {
         case 16: return launch_detect_tc<M, 16, kHalf>;
         default: return nullptr;
     }
+}
+
+// Batched (persistent) form, FP32 accuracy (TF32 x3), antenna counts up to 32: launcher and
+// resident CTAs per SM for user bucket kb.
+TcBatchLauncher APSM_TC_CAT(detect_tc_batch_launcher_m, APSM_TC_M)(int kb, int *ctas_per_sm) {
+    constexpr int M = APSM_TC_M;
+    if constexpr (M <= 32) {
+        switch (kb) {
+            case 2: *ctas_per_sm = tc_batch_ctas_per_sm<M, 2, kTF32x3>(); return launch_detect_tc_batch<M, 2, kTF32x3>;
+            case 4: *ctas_per_sm = tc_batch_ctas_per_sm<M, 4, kTF32x3>(); return launch_detect_tc_batch<M, 4, kTF32x3>;
+            case 6: *ctas_per_sm = tc_batch_ctas_per_sm<M, 6, kTF32x3>(); return launch_detect_tc_batch<M, 6, kTF32x3>;
+            case 8: *ctas_per_sm = tc_batch_ctas_per_sm<M, 8, kTF32x3>(); return launch_detect_tc_batch<M, 8, kTF32x3>;
+            case 12: *ctas_per_sm = tc_batch_ctas_per_sm<M, 12, kTF32x3>(); return launch_detect_tc_batch<M, 12, kTF32x3>;
+            case 16: *ctas_per_sm = tc_batch_ctas_per_sm<M, 16, kTF32x3>(); return launch_detect_tc_batch<M, 16, kTF32x3>;
+        }
+    }
+    (void)ctas_per_sm;
+    return nullptr;
 }
 
 }  // namespace apsm

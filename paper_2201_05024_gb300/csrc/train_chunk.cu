@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(256) train_gram_kernel(const float2 *__restric
     for (int idx = threadIdx.x; idx < 32 * M; idx += blockDim.x) {
         const int i = idx / M, mm = idx % M;
         const float2 *src = i < 16 ? row_src(i) : col_src(i - 16);
-        const float2 v = src ? __ldg(src + mm) : make_float2(0.f, 0.f);
+        const float2 v = src ? __ldcg(src + mm) : make_float2(0.f, 0.f);
         (i < 16 ? s_row + i * MS : s_col + (i - 16) * MS)[mm] = v;
     }
     __syncthreads();

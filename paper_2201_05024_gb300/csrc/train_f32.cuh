@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
     float b = 0.f;
     auto read_target = [&]() {
         if (valid) {
-            const float2 sy = a.sym[(size_t)pa * K + k];
+            const float2 sy = __ldcg(a.sym + (size_t)pa * K + k);
             b = l ? sy.y : sy.x;  // b_{2t} = Re b(t), b_{2t+1} = Im b(t)
         }
     };
@@ -243,21 +243,21 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
     float2 clin_r[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};  // M <= 64 <= 2 RS
 #pragma unroll
     for (int i = 0; i < 2; ++i)
-        if (u + i * RS < M) clin_r[i] = a.clin[(u + i * RS) * K + k];
+        if (u + i * RS < M) clin_r[i] = __ldcg(a.clin + (u + i * RS) * K + k);
     // coefficients of the entries dropped in this chunk (entry t0+e-D at step 2(t0+e))
     // (the dropped entry and the arriving one share the slot (tb + t0 + e) mod D)
     float egam_r = 0.f;
     if (evict && u < 2 * Tc && tb + t0 + (u >> 1) >= D)
-        egam_r = a.gamma[((size_t)((tb + t0 + (u >> 1)) % D) * 2 + (u & 1)) * K + k];
+        egam_r = __ldcg(a.gamma + ((size_t)((tb + t0 + (u >> 1)) % D) * 2 + (u & 1)) * K + k);
 
     // ---- this thread's sample: target, coefficient, prediction at chunk start ---------------
     float p = 0.f, gam = 0.f;
     if (valid) {
         if (m < s0) {
-            if (!a.fresh_carry) p = a.carry[u * K + k];
-            gam = a.gamma[((size_t)((tb + pa) % D) * 2 + l) * K + k];
+            if (!a.fresh_carry) p = __ldcg(a.carry + u * K + k);
+            gam = __ldcg(a.gamma + ((size_t)((tb + pa) % D) * 2 + l) * K + k);
         } else if (a.track_in) {
-            p = a.track_in[(m - s0) * K + k];
+            p = __ldcg(a.track_in + (m - s0) * K + k);
         }
     }
     const float gam0 = gam;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
         for (int sl = 0; sl < a.n_slices; sl += 32) {
             float v[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = sl + j < a.n_slices ? src[(sl + j) * stride] : 0.f;
+            for (int j = 0; j < 32; ++j) v[j] = sl + j < a.n_slices ? __ldcg(src + (sl + j) * stride) : 0.f;
 #pragma unroll
             for (int j = 0; j < 32; ++j) gs[j & 7] += v[j];
         }
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
                 const float2 *rv = a.rx + (size_t)tv * M;
                 float l0s = 0.f, l1s = 0.f;
                 for (int mm = 0; mm < M; mm += 2) {
-                    const float4 x = __ldg(reinterpret_cast<const float4 *>(rv + mm));
+                    const float4 x = __ldcg(reinterpret_cast<const float4 *>(rv + mm));
                     const float2 c = s_clinw[mm], cb = s_clinw[mm + 1];
                     l0s = lvv ? fmaf(c.x, x.y, fmaf(-c.y, x.x, l0s)) : fmaf(c.x, x.x, fmaf(c.y, x.y, l0s));
                     l1s = lvv ? fmaf(cb.x, x.w, fmaf(-cb.y, x.z, l1s)) : fmaf(cb.x, x.z, fmaf(cb.y, x.w, l1s));
@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
                 float acc4[4] = {a.wL * (l0s + l1s), 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    acc4[j & 3] = fmaf(s_gcar[j], __ldg(a.kx + (size_t)min(j, R - 1) * g.KXS + v), acc4[j & 3]);
+                    acc4[j & 3] = fmaf(s_gcar[j], __ldcg(a.kx + (size_t)min(j, R - 1) * g.KXS + v), acc4[j & 3]);
                 tp[i] = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
             }
         };
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
                 // so that all NL loads are in flight together
                 float kv[NL];
 #pragma unroll
-                for (int j = 0; j < NL; ++j) kv[j] = __ldg(a.kx + (size_t)min(max(r0 + j, 0), R - 1) * g.KXS + v);
+                for (int j = 0; j < NL; ++j) kv[j] = __ldcg(a.kx + (size_t)min(max(r0 + j, 0), R - 1) * g.KXS + v);
                 float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int j = 0; j < NL; ++j) acc[j & 3] = fmaf(agg[j], kv[j], acc[j & 3]);

@@ -154,13 +154,20 @@ def test_batch_create_validates_every_instance_first(lib):
     bad_ws = apsm._CInstance(p, 64, 10, 256, 256, 256, 256, None, st, 256, 16)
     bad_rx = apsm._CInstance(p, 64, 10, 256, 256, None, 256, None, st, 256, 1 << 30)
     h = C.c_void_p()
+    nb = C.c_size_t()
     for bad, code in ((bad_ws, apsm.APSM_ERR_WORKSPACE), (bad_rx, apsm.APSM_ERR_INVALID_ARG)):
         arr = (apsm._CInstance * 2)(good, bad)
-        assert lib.apsm_batch_create(arr, 2, 4, C.byref(h)) == code
+        assert lib.apsm_batch_create(arr, 2, 4, C.c_void_p(256), 1 << 20, C.byref(h)) == code
+        assert lib.apsm_batch_workspace_bytes(arr, 2, C.byref(nb)) == code
     arr = (apsm._CInstance * 1)(good)
-    assert lib.apsm_batch_create(arr, 0, 4, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
-    assert lib.apsm_batch_create(arr, 1, 0, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_batch_create(arr, 0, 4, C.c_void_p(256), 1 << 20, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_batch_create(arr, 1, 0, C.c_void_p(256), 1 << 20, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
+    # the work lists of the persistent detection need a workspace, 256-byte aligned
+    assert lib.apsm_batch_workspace_bytes(arr, 1, C.byref(nb)) == 0 and nb.value > 0
+    assert lib.apsm_batch_create(arr, 1, 2, None, 0, C.byref(h)) == apsm.APSM_ERR_WORKSPACE
+    assert lib.apsm_batch_create(arr, 1, 2, C.c_void_p(256 + 16), nb.value, C.byref(h)) == apsm.APSM_ERR_INVALID_ARG
     assert lib.apsm_batch_launch(None, None) == apsm.APSM_ERR_INVALID_ARG
+    assert lib.apsm_batch_launch_detect(None, None) == apsm.APSM_ERR_INVALID_ARG
 
 
 def test_parameter_validation_of_weights(lib):

@@ -88,3 +88,43 @@ def test_autotuned_table_keeps_parity():
             assert_soft_close(soft.cpu().numpy(), ref, what=f"ffma {t}x{s}x{q}")
     finally:
         apsm.tune_clear()
+
+
+def test_persistent_detection_phase_replays_and_mixes_with_per_instance_detection():
+    """The detection phase as one persistent launch per (antennas, user bucket) class: replayed
+    alone (its work counters are reset by the graph each time) it gives the same outputs again;
+    instances outside the batched kernel's range (64 antennas, BF16, 16-QAM labels) are detected
+    per instance on their branch.  Everything equals the single-instance calls bit for bit."""
+    shapes = [  # M, K, P, D, N, dtype, bits
+        (16, 6, 300, 256, 2000, "fp32", 2), (16, 5, 200, 300, 700, "fp32", 2), (8, 3, 150, 200, 1000, "fp32", 2),
+        (64, 4, 100, 100, 300, "fp32", 2), (16, 6, 120, 128, 500, "bf16", 2), (16, 6, 140, 200, 640, "fp32", 4),
+    ]
+    data = []
+    for i, (M, K, P, D, N, dt, bits) in enumerate(shapes):
+        x = synth.make_instance(M, K, P, N, 10.0, instance=700 + i, bits=bits)
+        p = apsm.Params(M=M, K=K, window=16, dict_cap=D, dtype=dt, modulation=bits)
+        data.append((p, x))
+    bis = [apsm.BatchInstance(p, to_dev(x.rx_pilot), to_dev(x.sym_pilot), to_dev(x.rx_data)) for p, x in data]
+    batch = apsm.Batch(bis, lanes=3)
+    n_classes, n_batched = batch.info()
+    assert n_classes == 2 and n_batched == 3        # (16, 6) holds two instances, (8, 4) one
+    batch.launch()
+    torch.cuda.synchronize()
+    first = [b.soft.clone() for b in bis]
+    for rep in range(2):
+        for b in bis:
+            b.soft.zero_()
+        batch.launch_detect() if rep == 0 else batch.launch()
+        torch.cuda.synchronize()
+        for (p, x), b, f in zip(data, bis, first):
+            if rep == 0 and not (p.dtype == "fp32" and p.M <= 32 and p.modulation == 2):
+                continue                            # detected on the training branches only
+            assert torch.equal(b.soft, f), (p, rep)
+    for (p, x), b in zip(data, bis):
+        st = apsm.State(p)
+        apsm.train(p, b.rx_pilot, b.sym_pilot, st)
+        soft, hard = apsm.detect(p, st, b.rx)
+        assert torch.equal(soft, b.soft), p
+        assert torch.equal(hard, b.hard), p
+        assert apsm.read_status(b.state) == 0
+    batch.close()

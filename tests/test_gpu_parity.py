@@ -497,3 +497,33 @@ def test_detect_autograd_matches_finite_differences():
             fd = (L(clin_=cp_) - L(clin_=cm_)) / (2 * h)
             got = c_t.grad[m, k].item()
             assert (got.real if unit == 1.0 else got.imag) == pytest.approx(fd, rel=2e-3, abs=1e-4)
+
+
+@pytest.mark.parametrize("M,K,P,D,engine", [(64, 4, 300, 300, "ffma"), (16, 6, 300, 256, "ffma"),
+                                            (16, 6, 300, 256, "tensor"), (8, 3, 100, 20, "tensor")])
+def test_detect_right_behind_training_on_a_fresh_state(M, K, P, D, engine):
+    """Detection queued directly behind training on the same stream (no host synchronisation
+    between them) on a state that held nothing: every read of the trained state goes through L2,
+    so the result equals detection after a synchronisation.  (The FMA engine's small CTAs can
+    run beside the last training CTAs; before its state reads bypassed L1 it saw a stale linear
+    filter and entry count here.)"""
+    x = synth.make_instance(M, K, P, 500, 10.0, instance=1700 + M + D)
+    p = apsm.Params(M=M, K=K, window=16 if D > 20 else 8, dict_cap=D)
+    if engine == "ffma":
+        apsm.tune_set(M, K, "fp32", "ffma", 64, 2, 1)
+    try:
+        rp, sp, rd = to_dev(x.rx_pilot), to_dev(x.sym_pilot), to_dev(x.rx_data)
+        st = apsm.State(p)
+        apsm.train(p, rp, sp, st)
+        torch.cuda.synchronize()
+        ref, ref_h = apsm.detect(p, st, rd)
+        torch.cuda.synchronize()
+        for _ in range(4):
+            st = apsm.State(p)
+            torch.cuda.synchronize()
+            apsm.train(p, rp, sp, st)
+            soft, hard = apsm.detect(p, st, rd)
+            torch.cuda.synchronize()
+            assert torch.equal(soft, ref) and torch.equal(hard, ref_h)
+    finally:
+        apsm.tune_clear()
