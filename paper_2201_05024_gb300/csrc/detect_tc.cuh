@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
     const int tid = threadIdx.x, warp = tid >> 5;
     const int q0 = blockIdx.x * kTcRows;
     int n_ent = a.n_entries;
-    if (a.meta) n_ent = min(n_ent, max(__ldcg(a.meta), 0));
+    if (a.meta) n_ent = min(n_ent, max(__ldg(a.meta), 0));
     const int n_tiles = (n_ent + E - 1) / E;
     const float g2 = 2.f * a.k2;
 
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
                     const float4 *src = reinterpret_cast<const float4 *>(rq + p * C);
 #pragma unroll
                     for (int q = 0; q < C / 2; ++q) {
-                        const float4 v = __ldcg(src + q);
+                        const float4 v = __ldg(src + q);
                         re[2 * q] = v.x; im[2 * q] = v.y; re[2 * q + 1] = v.z; im[2 * q + 1] = v.w;
                     }
                 } else {
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
             }
         } else {
             for (int m = 0; m < M; ++m) {
-                const float2 v = s < a.N ? __ldcg(rq + m) : make_float2(0.f, 0.f);
+                const float2 v = s < a.N ? __ldg(rq + m) : make_float2(0.f, 0.f);
                 nq = fmaf(v.x, v.x, fmaf(v.y, v.y, nq));
                 put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, m), g2 * v.x, a.half_fmt);
                 put_elem<kPrec>(sA, Sh::kBytesA, Sh::off(tid, M + m), g2 * v.y, a.half_fmt);
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
             float dA = 0.f, dB = 0.f, dC = 0.f;
 #pragma unroll 4
             for (int m = 0; m < M; ++m) {
-                const float2 q = __ldcg(rq + m), d = __ldcg(rt + m);
+                const float2 q = __ldg(rq + m), d = __ldg(rt + m);
                 const float ax = d.x - q.x, ay = d.y - q.y;  // r_t - r_s
                 const float bx = d.x - q.y, by = d.y + q.x;  // r_t + i r_s  (r1(t) vs r2(s))
                 const float cx = d.x + q.y, cy = d.y - q.x;  // r_t - i r_s  (r2(t) vs r1(s))
@@ -624,7 +624,7 @@ __global__ void __launch_bounds__(kTcThreads, (tc_min_blocks<M, KB, kPrec>())) d
             for (int k = 0; k < a.K && k < KB; ++k) {
                 float l1 = 0.f, l2 = 0.f;  // c_k^H r
                 for (int m = 0; m < M; ++m) {
-                    const float2 c = __ldcg(a.clin + m * a.K + k), r = __ldcg(rq + m);
+                    const float2 c = __ldg(a.clin + m * a.K + k), r = __ldg(rq + m);
                     l1 = fmaf(c.x, r.x, fmaf(c.y, r.y, l1));
                     l2 = fmaf(c.x, r.y, fmaf(-c.y, r.x, l2));
                 }
@@ -658,9 +658,9 @@ cudaError_t launch_detect_tc(const TcArgs &a, cudaStream_t stream) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
     if (e != cudaSuccess) return e;
     // An ordinary launch (not a programmatic dependent one): the kernel starts only after the
-    // previous work of the stream has finished, so its dictionary tiles can be read through L1
-    // (each tile is read by both CTAs of an SM); an early launch would have to take them through
-    // L2 (see launch_pdl).
+    // previous work of the stream has finished, so every read (dictionary tiles, which both CTAs
+    // of an SM share, and the linear filter, read per query row) may take the L1 path; an early
+    // launch would have to take them through L2 (see launch_pdl).
     fn<<<grid, kTcThreads, L::kBytes, stream>>>(a);
     return cudaGetLastError();
 }
