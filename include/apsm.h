@@ -393,9 +393,13 @@ apsm_status apsm_check_wait_timeout(const apsm_state *st, void *stream);
  *                         lower it further)
  *   APSM_OPT_TRAIN_TRACK  1 (default): the next chunk's starting predictions are tracked during
  *                         the current chunk; 0: they are evaluated between chunks (sequential)
+ *   APSM_OPT_DETECT_TMA   1 (default): FP32 detection with 4, 8 or 16 antennas and an even user
+ *                         count in {2, 4, 6, 8, 12, 16} stages every operand by TMA (entry rows
+ *                         as stored, the real split's rotation on the query side); 0: the
+ *                         tensor-core form that converts entry rows in shared memory
  * Returns APSM_ERR_INVALID_ARG for an unknown option or a value out of range.
  */
-typedef enum { APSM_OPT_TRAIN_CHUNK = 0, APSM_OPT_TRAIN_TRACK = 1 } apsm_option;
+typedef enum { APSM_OPT_TRAIN_CHUNK = 0, APSM_OPT_TRAIN_TRACK = 1, APSM_OPT_DETECT_TMA = 2 } apsm_option;
 apsm_status apsm_set_option(int32_t option, int32_t value);
 
 /* Static description of a status code. */

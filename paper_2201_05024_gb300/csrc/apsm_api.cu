@@ -13,6 +13,7 @@
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "detect_tc.cuh"
+#include "detect_tma.cuh"
 #include "train_f32.cuh"
 
 namespace apsm {
@@ -22,6 +23,7 @@ std::atomic<long long> g_launches{0};
 DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
 DetectBwdLauncher detect_bwd_launcher(int M, int K);  // detect_f32_m*.cu
 TcLauncher detect_tc_launcher(int M, int K, int prec);  // detect_tc_m*.cu
+TmaLauncher detect_tma_launcher(int M, int K);         // detect_tma_m*.cu
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
 ChunkLauncher chunk_launcher(int S, int WP, bool ext);  // train_chunk.cu
 int padded_window(int W);                           // train_chunk.cu
@@ -99,6 +101,7 @@ constexpr int kMaxSmemBytes = 227 * 1024;  // opt-in shared memory per CTA
 // ---- process-wide launch options (apsm_set_option) -------------------------------------------
 std::atomic<int> g_opt_train_chunk{64};  // pilots per training chunk
 std::atomic<int> g_opt_train_track{1};   // next-chunk tracking form (1) or sequential form (0)
+std::atomic<int> g_opt_detect_tma{1};     // TMA-staged FP32 detection where it applies (1) or not (0)
 
 inline apsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APSM_OK : APSM_ERR_CUDA; }
 
@@ -631,7 +634,8 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     if (p->dtype != APSM_FP32 || !force_ffma) {
         const int prec = p->dtype == APSM_FP32 ? kTF32x3 : kHalf;
         TcLauncher tc = detect_tc_launcher(p->M, p->K, prec);
-        if (tc) {
+        TmaLauncher tma = (p->dtype == APSM_FP32 && g_opt_detect_tma.load()) ? detect_tma_launcher(p->M, p->K) : nullptr;
+        if (tc || tma) {
             TcArgs ta{};
             ta.rx = reinterpret_cast<const float2 *>(rx);
             ta.N = N;
@@ -650,7 +654,10 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
             ta.hard = hard;
             ta.status = st->meta + 3;
             if (qam_pass) ta.hard = nullptr;
-            if (tc(ta, strm) != cudaSuccess) return APSM_ERR_CUDA;
+            // the TMA-staged form where it applies (shape, alignment), else the converter form
+            const int r = tma ? tma(ta, strm) : 1;
+            if (r < 0) return APSM_ERR_CUDA;
+            if (r > 0 && (!tc || tc(ta, strm) != cudaSuccess)) return tc ? APSM_ERR_CUDA : APSM_ERR_UNSUPPORTED;
             g_launches++;
             return qam_pass ? qam_labels(soft, hard, N, p, strm) : APSM_OK;
         }
@@ -777,6 +784,10 @@ apsm_status apsm_set_option(int32_t option, int32_t value) {
         case APSM_OPT_TRAIN_TRACK:
             if (value != 0 && value != 1) return APSM_ERR_INVALID_ARG;
             g_opt_train_track.store(value);
+            return APSM_OK;
+        case APSM_OPT_DETECT_TMA:
+            if (value != 0 && value != 1) return APSM_ERR_INVALID_ARG;
+            g_opt_detect_tma.store(value);
             return APSM_OK;
         default: return APSM_ERR_INVALID_ARG;
     }

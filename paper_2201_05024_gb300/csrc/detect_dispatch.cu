@@ -1,8 +1,11 @@
 // detect_dispatch.cu -- maps (M, K) to the FP32 detection kernels (and adjoint) instantiated for it.
+#include <atomic>
+
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "detect_tc.cuh"
 #include "detect_tc_batch.cuh"
+#include "detect_tma.cuh"
 
 namespace apsm {
 
@@ -33,6 +36,38 @@ TcBatchLauncher detect_tc_batch_launcher_m8(int kb, int *ctas_per_sm);
 TcBatchLauncher detect_tc_batch_launcher_m16(int kb, int *ctas_per_sm);
 TcBatchLauncher detect_tc_batch_launcher_m32(int kb, int *ctas_per_sm);
 TcBatchLauncher detect_tc_batch_launcher_m64(int kb, int *ctas_per_sm);
+
+TmaLauncher detect_tma_launcher_m4(int K);
+TmaLauncher detect_tma_launcher_m8(int K);
+TmaLauncher detect_tma_launcher_m16(int K);
+
+TmaEncodeFn tma_encode_fn() {
+    static std::atomic<TmaEncodeFn> fn{nullptr};
+    static std::atomic<int> tried{0};
+    TmaEncodeFn f = fn.load();
+    if (f || tried.load()) return f;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess && p) {
+        f = reinterpret_cast<TmaEncodeFn>(p);
+        fn.store(f);
+    } else {
+        cudaGetLastError();
+    }
+    tried.store(1);
+    return f;
+}
+
+// TMA-staged FP32 detection for (M, K); nullptr where no instantiation exists.
+TmaLauncher detect_tma_launcher(int M, int K) {
+    switch (M) {
+        case 4: return detect_tma_launcher_m4(K);
+        case 8: return detect_tma_launcher_m8(K);
+        case 16: return detect_tma_launcher_m16(K);
+        default: return nullptr;
+    }
+}
 
 // Smallest supported user bucket >= K for the tensor-core kernels (0 if none).
 int tc_user_bucket(int K) {

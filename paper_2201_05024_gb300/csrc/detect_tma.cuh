@@ -1,0 +1,549 @@
+// detect_tma.cuh -- FP32-accuracy detection on the tensor cores with every operand staged by
+// the tensor memory accelerator (Sec. III-B detection; the same result as detect_tc.cuh).
+//
+// For a tile of 128 queries r_s and E = 64 dictionary entries r_t the complex Gram z = r_t^H r_s
+// is two real GEMMs over the 2M interleaved components [Re r_1, Im r_1, Re r_2, ...]:
+//   Re z = <[Re r_s, Im r_s]-pairs, raw entry row>      (A_re = the query row as stored)
+//   Im z = <[Im r_s, -Re r_s]-pairs, raw entry row>     (A_im = each pair swapped, one negated)
+// so the entry operand B is the dictionary row exactly as the state stores it, and the
+// rotation of the real split (Sec. II-D) moves to the query operand, built once per CTA.  Both
+// products run in TF32 x3 (hi*hi + hi*lo + lo*hi, hi = tf32(x), lo = tf32(x - hi)) into two
+// TMEM accumulators of 64 columns each.  The epilogue forms
+//   E_A = 2^(2 k2 Re z - k2 n_t),  E_B = 2^(2 k2 Im z - k2 n_t),  E_C = 2^(-2 k2 Im z - k2 n_t)
+// and the coefficient sums as detect_tc.cuh does (query factor 2^(-k2 n_s) applied at the end,
+// the unfactored exponent and the direct-difference fallback for a CTA with a query outside the
+// factor range).
+//
+// Staging: the query tile, each entry tile, its coefficients and its norms are tiled TMA loads
+// (2-D tensor maps, boxes of 16-byte k-chunks x rows, so that every chunk lands as the
+// core matrices of the no-swizzle K-major operand layout; rows past the tensor read as zero).
+// A short shared-memory pass by the epilogue threads splits each landed tile into its TF32 hi
+// and lo copies (zeroing rows past the held entries), turns the entry norms into -k2 n_t and
+// builds the rotated query operand.
+//
+// Roles (288 threads): warps 0-7 = epilogue; warp w reads TMEM lanes 32 (w mod 4) .. and the
+// entries 32 (w / 4) .. 32 (w / 4) + 31 of each tile, so two threads share every query row and
+// merge their sums in a fixed order at the end.  Warp 8, lane 0 = producer: issues the TMA loads
+// and the MMAs.  B (hi, lo) has two stages, the coefficient and norm tiles three, TMEM two
+// accumulator pairs.  The pass for tile t+1 runs at the start of the epilogue of tile t, and the
+// MMAs of tile t+1 then run beside that epilogue; the loads of tile t+2 are issued as soon as
+// the MMAs of tile t (entries) and the epilogue of tile t-1 (coefficients) are done, a whole
+// tile ahead of their pass.  All waits are bounded.
+//
+// Used for FP32 detection with 4, 8 or 16 antennas and an even user count that is its own
+// bucket (2, 4, 6, 8, 12, 16), where the state's arrays are 16-byte aligned.
+#pragma once
+
+#include <cuda.h>
+
+#include "detect_tc.cuh"
+
+namespace apsm {
+
+constexpr int kTmaRows = 128;        // queries per CTA (MMA M)
+constexpr int kTmaEntries = 64;      // entries per tile (MMA N of each accumulator)
+constexpr int kTmaEpi = 256;         // epilogue threads
+constexpr int kTmaThreads = 288;     // + one producer warp
+
+struct TmaArgs {
+    CUtensorMap tm_q;   // queries   [N][2M] float, box {4, 128}
+    CUtensorMap tm_d;   // entries   [D][2M] float, box {4, 64}
+    CUtensorMap tm_g;   // coefficients [D][2K] float, box {2K, 64}
+    CUtensorMap tm_n;   // entry norms [D] float, box {64}
+    const float2 *rx;   // [N][M] (exact fallback, linear part)
+    int N;
+    const float2 *dict;  // [D][M] (exact fallback)
+    const float2 *clin;  // [M][K], K = KB
+    const int *meta;
+    int n_entries;       // host bound D
+    float k2, wL, wG;
+    float2 *soft;
+    uint8_t *hard;
+    int *status;
+};
+
+template <int M, int KB>
+struct TmaSmem {
+    static constexpr int kRow = 8 * M;                    // bytes of one stored row (2M floats)
+    static constexpr int kACopy = kTmaRows * kRow;        // one query operand copy
+    static constexpr int kBCopy = kTmaEntries * kRow;     // one entry operand copy
+    static constexpr int kALbo = kTmaRows * 16;           // bytes between k-adjacent core matrices
+    static constexpr int kBLbo = kTmaEntries * 16;
+    static constexpr int kCStage = kTmaEntries * 2 * KB * 4;
+    static constexpr int kA = 0;                          // [re_hi, re_lo, im_hi, im_lo]
+    static constexpr int kB = kA + 4 * kACopy;            // 2 stages x [hi, lo]
+    static constexpr int kC = kB + 4 * kBCopy;            // 3 stages of coefficients [E][2K]
+    static constexpr int kN = kC + 3 * kCStage;           // 3 stages of norms [E]
+    static constexpr int kH = kN + 3 * kTmaEntries * 4;   // 3 stages of -k2 n_t [E]
+    static constexpr int kQ = kH + 3 * kTmaEntries * 4;   // partial query norms [256]
+    static constexpr int kBar = kQ + kTmaEpi * 4;         // 12 mbarriers
+    static constexpr int kTmem = kBar + 12 * 8;
+    static constexpr int kBytes = kTmem + 16;
+    static_assert(kRow % 16 == 0, "rows of whole 16-byte chunks");
+    static_assert(kC % 1024 == 0 && kCStage % 128 == 0, "TMA destinations 128-byte aligned");
+    // the merged sums (4 KB floats per row) reuse the operands once all MMAs are done
+    static constexpr bool kFits = kTmaRows * 4 * KB * 4 <= kC;
+};
+
+template <int M, int KB>
+constexpr int tma_min_blocks() { return TmaSmem<M, KB>::kBytes <= 113 * 1024 ? 2 : 1; }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: lbo = bytes between k-adjacent core
+// matrices, sbo = bytes between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_1d(void *dst, const CUtensorMap *tm, int x, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 16 columns of this warp's TMEM lanes, without waiting (tmem_wait_ld completes the loads).
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// (x0, x1) = (x0, x1) * a + (b, b), one packed FP32 FMA.
+__device__ __forceinline__ void fma2_scale(float &x0, float &x1, float a, float b) {
+    asm("{\n\t.reg .b64 x, a, b;\n\t"
+        "mov.b64 x, {%0, %1};\n\tmov.b64 a, {%2, %2};\n\tmov.b64 b, {%3, %3};\n\t"
+        "fma.rn.f32x2 x, x, a, b;\n\tmov.b64 {%0, %1}, x;\n\t}"
+        : "+f"(x0), "+f"(x1)
+        : "f"(a), "f"(b));
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(tf32_rna(x)); }
+
+// AND over the 256 epilogue threads (named barrier 2); also orders their shared-memory writes.
+__device__ __forceinline__ bool epi_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 256, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
+template <int M, int KB>
+__global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
+    detect_tma_kernel(const __grid_constant__ TmaArgs a) {
+    using L = TmaSmem<M, KB>;
+    constexpr int E = kTmaEntries, CH = M / 2;  // 16-byte k-chunks per row
+    constexpr int kSteps = M / 4;               // MMA k-steps of 8 TF32 elements
+    static_assert(M % 4 == 0 && KB % 2 == 0, "whole k-steps, users in pairs");
+    static_assert(L::kFits, "merge area within the operand regions");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBar);
+    uint64_t *a_full = bars, *full_b = bars + 1, *full_c = bars + 3, *conv = bars + 6, *mma_done = bars + 8,
+             *epi_done = bars + 10;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + L::kTmem);
+    float *sG = reinterpret_cast<float *>(smem + L::kC);
+    float *sN = reinterpret_cast<float *>(smem + L::kN);
+    float *sH = reinterpret_cast<float *>(smem + L::kH);
+    float *s_nqp = reinterpret_cast<float *>(smem + L::kQ);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int q0 = blockIdx.x * kTmaRows;
+    int n_ent = a.n_entries;
+    if (a.meta) n_ent = min(n_ent, max(__ldg(a.meta), 0));
+    const int n_tiles = (n_ent + E - 1) / E;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(a_full, 1);
+        for (int i = 0; i < 2; ++i) mbar_init(&full_b[i], 1);
+        for (int i = 0; i < 3; ++i) mbar_init(&full_c[i], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&conv[i], kTmaEpi);
+            mbar_init(&mma_done[i], 1);
+            mbar_init(&epi_done[i], kTmaEpi);
+        }
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    bool ok = true;
+
+    if (warp == 8) {
+        // ================= producer: TMA loads and MMAs (one thread) =================
+        if ((tid & 31) == 0) {
+            auto issue_b = [&](int t) {
+                const int s = t & 1;
+                unsigned char *dst = smem + L::kB + s * 2 * L::kBCopy;
+                mbar_arrive_expect_tx(&full_b[s], (uint32_t)L::kBCopy);
+#pragma unroll
+                for (int j = 0; j < CH; ++j) tma_load_2d(dst + j * E * 16, &a.tm_d, 4 * j, t * E, &full_b[s]);
+            };
+            auto issue_c = [&](int t) {
+                const int s = t % 3;
+                mbar_arrive_expect_tx(&full_c[s], (uint32_t)(L::kCStage + E * 4));
+                tma_load_2d(smem + L::kC + s * L::kCStage, &a.tm_g, 0, t * E, &full_c[s]);
+                tma_load_1d(smem + L::kN + s * E * 4, &a.tm_n, t * E, &full_c[s]);
+            };
+            mbar_arrive_expect_tx(a_full, (uint32_t)L::kACopy);
+#pragma unroll
+            for (int j = 0; j < CH; ++j) tma_load_2d(smem + L::kA + j * kTmaRows * 16, &a.tm_q, 4 * j, q0, a_full);
+            int nb = 0, nc = 0;  // tiles whose entry / coefficient loads have been issued
+            for (; nb < 2 && nb < n_tiles; ++nb) issue_b(nb);
+            for (; nc < 2 && nc < n_tiles; ++nc) issue_c(nc);
+            // F32 accumulate, TF32 A and B, both K-major, N = 64, M = 128
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(E >> 3) << 17) |
+                                   ((uint32_t)(kTmaRows >> 4) << 24);
+            const uint32_t a0 = smem_u32(smem + L::kA);
+            int committed = -1;
+            for (int t = 0; t < n_tiles; ++t) {
+                const int s = t & 1;
+                // the epilogue threads converted tile t; the epilogue of tile t-2 freed TMEM stage s
+                if (!mbar_wait_bounded(&conv[s], (t >> 1) & 1) ||
+                    (t >= 2 && !mbar_wait_bounded(&epi_done[s], ((t - 2) >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_re = tmem + (uint32_t)(s * 2 * E), d_im = d_re + E;
+                const uint32_t b0 = smem_u32(smem + L::kB + s * 2 * L::kBCopy);
+#pragma unroll
+                for (int ks = 0; ks < kSteps; ++ks) {
+                    const uint32_t ao = a0 + ks * 2 * L::kALbo, bo = b0 + ks * 2 * L::kBLbo;
+                    const uint64_t are_h = umma_desc(ao, L::kALbo, 128), are_l = umma_desc(ao + L::kACopy, L::kALbo, 128);
+                    const uint64_t aim_h = umma_desc(ao + 2 * L::kACopy, L::kALbo, 128);
+                    const uint64_t aim_l = umma_desc(ao + 3 * L::kACopy, L::kALbo, 128);
+                    const uint64_t bh = umma_desc(bo, L::kBLbo, 128), bl = umma_desc(bo + L::kBCopy, L::kBLbo, 128);
+                    umma_tf32(d_re, are_l, bh, idesc, ks > 0);
+                    umma_tf32(d_re, are_h, bl, idesc, 1);
+                    umma_tf32(d_re, are_h, bh, idesc, 1);
+                    umma_tf32(d_im, aim_l, bh, idesc, ks > 0);
+                    umma_tf32(d_im, aim_h, bl, idesc, 1);
+                    umma_tf32(d_im, aim_h, bh, idesc, 1);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&mma_done[s]))
+                             : "memory");
+                committed = t;
+                if (t + 2 < n_tiles) {
+                    // entry stage s is free once these MMAs are done; coefficient stage (t+2) mod 3
+                    // once the epilogue of tile t-1 is
+                    if (!mbar_wait_bounded(&mma_done[s], (t >> 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    issue_b(t + 2);
+                    ++nb;
+                    if (t >= 1 && !mbar_wait_bounded(&epi_done[(t - 1) & 1], ((t - 1) >> 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    issue_c(t + 2);
+                    ++nc;
+                }
+            }
+            // every copy and MMA this thread issued has landed before the CTA may exit
+            mbar_wait_bounded(a_full, 0);
+            for (int t = max(0, nb - 2); t < nb; ++t) mbar_wait_bounded(&full_b[t & 1], (t >> 1) & 1);
+            for (int t = max(0, nc - 3); t < nc; ++t) mbar_wait_bounded(&full_c[t % 3], (t / 3) & 1);
+            if (committed >= 0) mbar_wait_bounded(&mma_done[committed & 1], (committed >> 1) & 1);
+        }
+    } else {
+        // ================= epilogue =================
+        const int row = tid & (kTmaRows - 1), hf = tid >> 7;
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        const int s_row = q0 + row;
+        // the query operand: raw rows -> [re_hi, re_lo, im_hi, im_lo]; partial squared norms
+        float nqp = 0.f;
+        const bool a_ok = __all_sync(0xffffffffu, mbar_wait_bounded(a_full, 0));
+        if (a_ok) {
+            float4 *q = reinterpret_cast<float4 *>(smem + L::kA);
+            constexpr int QV = L::kACopy / 16;
+#pragma unroll
+            for (int i = 0; i < CH / 2; ++i) {
+                const int f = tid + kTmaEpi * i;  // chunk f / 128 of row f mod 128 (= row)
+                const float4 x = q[f];
+                nqp = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, nqp))));
+                const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                const float4 l = make_float4(tf32_hi(x.x - h.x), tf32_hi(x.y - h.y), tf32_hi(x.z - h.z),
+                                             tf32_hi(x.w - h.w));
+                q[f] = h;
+                q[QV + f] = l;
+                q[2 * QV + f] = make_float4(h.y, -h.x, h.w, -h.z);  // (Im, -Re) pairs
+                q[3 * QV + f] = make_float4(l.y, -l.x, l.w, -l.z);
+            }
+        }
+        s_nqp[tid] = nqp;
+        // one tile's landed loads -> operand copies, -k2 n_t, zeros past the held entries
+        auto convert = [&](int t) -> bool {
+            const int sb = t & 1, sc = t % 3;
+            const bool w = mbar_wait_bounded(&full_b[sb], (t >> 1) & 1) && mbar_wait_bounded(&full_c[sc], (t / 3) & 1);
+            if (!__all_sync(0xffffffffu, w)) return false;
+            const int nvalid = n_ent - t * E;  // rows at or past it are not held entries
+            float4 *bh = reinterpret_cast<float4 *>(smem + L::kB + sb * 2 * L::kBCopy);
+            float4 *bl = bh + L::kBCopy / 16;
+            for (int f = tid; f < CH * E; f += kTmaEpi) {
+                const float4 x = bh[f];
+                float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+                if ((f & (E - 1)) < nvalid) {
+                    h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                    l = make_float4(tf32_hi(x.x - h.x), tf32_hi(x.y - h.y), tf32_hi(x.z - h.z), tf32_hi(x.w - h.w));
+                }
+                bh[f] = h;
+                bl[f] = l;
+            }
+            if (tid < E) sH[sc * E + tid] = tid < nvalid ? -a.k2 * sN[sc * E + tid] : -INFINITY;
+            if (nvalid < E)
+                for (int i = tid; i < E * 2 * KB; i += kTmaEpi)
+                    if (i / (2 * KB) >= nvalid) sG[sc * E * 2 * KB + i] = 0.f;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&conv[sb]);
+            return true;
+        };
+        if (n_tiles > 0) ok = convert(0) && a_ok;
+        else asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ok = epi_and(ok);  // also: every partial norm is written
+        const float nq = s_nqp[row] + s_nqp[row + 128];
+        const bool cta_in_range = epi_and(a.k2 * nq <= kFactorLimit);
+
+        float acc1[KB], acc2[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) acc1[k] = acc2[k] = 0.f;
+        const float g2 = 2.f * a.k2;
+        const float hq = cta_in_range ? 0.f : -a.k2 * nq;  // unfactored exponent when out of range
+        // direct-difference fallback (as in detect_tc.cuh), here for queries outside the factor
+        // range only: inside it the TF32 x3 Gram error is below 2^-21 S in the exponent
+        const float one_m_theta = 1.f - kGuardF32;
+        const float thr_q = one_m_theta * a.k2 * nq;
+        const float base_q = a.k2 * nq + hq;
+        auto exact_pair = [&](const float *g_tile, int e, int e0) {
+            const int t = e0 + e;
+            if (t >= n_ent || s_row >= a.N) return;
+            const float2 *rq = a.rx + (size_t)s_row * M;
+            const float2 *rt = a.dict + (size_t)t * M;
+            float dA = 0.f, dB = 0.f, dC = 0.f;
+#pragma unroll 4
+            for (int m = 0; m < M; ++m) {
+                const float2 q = __ldg(rq + m), d = __ldg(rt + m);
+                const float ax = d.x - q.x, ay = d.y - q.y;
+                const float bx = d.x - q.y, by = d.y + q.x;
+                const float cx = d.x + q.y, cy = d.y - q.x;
+                dA = fmaf(ax, ax, fmaf(ay, ay, dA));
+                dB = fmaf(bx, bx, fmaf(by, by, dB));
+                dC = fmaf(cx, cx, fmaf(cy, cy, dC));
+            }
+            const float eA = ex2(base_q - a.k2 * dA), eB = ex2(base_q - a.k2 * dB), eC = ex2(base_q - a.k2 * dC);
+            float g1[KB], gg[KB];
+            load_coef<KB>(g_tile + e * 2 * KB, g1, gg);
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                acc1[k] = fmaf(g1[k], eA, fmaf(gg[k], eC, acc1[k]));
+                acc2[k] = fmaf(g1[k], eB, fmaf(gg[k], eA, acc2[k]));
+            }
+        };
+        auto run_tiles = [&](auto guard_c) {
+            constexpr bool kGuard = decltype(guard_c)::value;
+            for (int t = 0; t < n_tiles; ++t) {
+                const int s = t & 1, sc = t % 3;
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(&mma_done[s], (t >> 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (t + 1 < n_tiles && !convert(t + 1)) {  // the MMAs of tile t+1 run beside this epilogue
+                    ok = false;
+                    break;
+                }
+                const float *g_tile = sG + sc * E * 2 * KB;
+                const float *g = g_tile + hf * 32 * 2 * KB;
+                const float *hh = sH + sc * E + hf * 32;
+#pragma unroll 1
+                for (int c = 0; c < 2; ++c) {
+                    uint32_t vr[16], vi[16];
+                    const uint32_t col = tmem + lane_base + (uint32_t)(s * 2 * E + hf * 32 + 16 * c);
+                    tmem_ld16_async(col, vr);
+                    tmem_ld16_async(col + E, vi);
+                    float hv[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4 *>(hv + 4 * q) = *reinterpret_cast<const float4 *>(hh + 16 * c + 4 * q);
+                    tmem_wait_ld();
+                    uint32_t fbits = 0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
+                        float h = hv[j];
+                        if constexpr (kGuard) {
+                            h += hq;
+                            // flagged: 2 k2 max(Re z, |Im z|) > (1 - theta) k2 (n_s + n_t)
+                            const bool f = g2 * fmaxf(re, fabsf(im)) > fmaf(-one_m_theta, hv[j], thr_q);
+                            h = f ? -INFINITY : h;
+                            fbits |= f ? (1u << j) : 0u;
+                        }
+                        float xA = re, xB = im;
+                        fma2_scale(xA, xB, g2, h);  // (2 k2 Re z + h, 2 k2 Im z + h)
+                        const float eA = ex2(xA), eB = ex2(xB), eC = ex2(fmaf(-g2, im, h));
+                        float g1[KB], gg[KB];
+                        load_coef<KB>(g + (16 * c + j) * 2 * KB, g1, gg);
+#pragma unroll
+                        for (int k = 0; k < KB; k += 2) {
+                            fma2_pair(acc1[k], acc1[k + 1], gg[k], gg[k + 1], eC);
+                            fma2_pair(acc1[k], acc1[k + 1], g1[k], g1[k + 1], eA);
+                            fma2_pair(acc2[k], acc2[k + 1], gg[k], gg[k + 1], eA);
+                            fma2_pair(acc2[k], acc2[k + 1], g1[k], g1[k + 1], eB);
+                        }
+                    }
+                    if constexpr (kGuard) {
+                        if (__any_sync(0xffffffffu, fbits != 0)) {
+#pragma unroll 1
+                            while (fbits) {
+                                const int j = __ffs(fbits) - 1;
+                                fbits &= fbits - 1;
+                                exact_pair(g_tile, hf * 32 + 16 * c + j, t * E);
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&epi_done[s]);
+            }
+        };
+        if (ok) {
+            if (cta_in_range) run_tiles(std::false_type{});
+            else run_tiles(std::true_type{});
+        }
+        // ---- merge the two halves of every row; the second half also forms the linear part -----
+        // (the operand regions are free: each thread has seen the last tile's MMAs complete)
+        float *s_part = reinterpret_cast<float *>(smem + L::kA) + row * 4 * KB;
+        if (hf == 1) {
+            float l1[KB], l2[KB];  // c_k^H r
+#pragma unroll
+            for (int k = 0; k < KB; ++k) l1[k] = l2[k] = 0.f;
+            if (s_row < a.N) {
+                const float2 *rq = a.rx + (size_t)s_row * M;
+                for (int m = 0; m < M; ++m) {
+                    const float2 r = __ldg(rq + m);
+#pragma unroll
+                    for (int k = 0; k < KB; ++k) {
+                        const float2 c = __ldg(a.clin + m * KB + k);
+                        l1[k] = fmaf(c.x, r.x, fmaf(c.y, r.y, l1[k]));
+                        l2[k] = fmaf(c.x, r.y, fmaf(-c.y, r.x, l2[k]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                s_part[k] = acc1[k];
+                s_part[KB + k] = acc2[k];
+                s_part[2 * KB + k] = l1[k];
+                s_part[3 * KB + k] = l2[k];
+            }
+        }
+        ok = epi_and(ok);  // also: every half-sum is written
+        if (ok && hf == 0 && s_row < a.N) {
+            const float fq = cta_in_range ? ex2(-a.k2 * nq) : 1.f;  // query factor
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                const float y1 = fmaf(a.wL, s_part[2 * KB + k], a.wG * fq * (acc1[k] + s_part[k]));
+                const float y2 = fmaf(a.wL, s_part[3 * KB + k], a.wG * fq * (acc2[k] + s_part[KB + k]));
+                a.soft[(size_t)s_row * KB + k] = make_float2(y1, y2);
+                if (a.hard) a.hard[(size_t)s_row * KB + k] = (uint8_t)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
+            }
+        }
+    }
+    if (!ok && (tid == 0 || tid == 256)) report(a.status, APSM_ERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+}
+
+// ---- host side: tensor maps and launch ------------------------------------------------------
+
+using TmaEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmaEncodeFn tma_encode_fn();  // the driver's tiled tensor-map encoder (detect_dispatch.cu); null if absent
+
+// FP32 tensor map over `rows` rows of `inner` floats (row pitch row_bytes), box box_inner x
+// box_rows (rank 1 when rows == 0: `inner` floats, box box_inner).  Out-of-range boxes read zero.
+inline bool tma_map_f32(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+                        uint32_t box_inner, uint32_t box_rows) {
+    const TmaEncodeFn enc = tma_encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {inner, rows};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rows ? 2 : 1, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launches the kernel for (M, KB).  Returns 0 when launched, 1 when this form does not apply
+// (user count not its own bucket, unaligned arrays, no tensor-map encoder: use detect_tc.cuh),
+// -1 on a CUDA error.
+template <int M, int KB>
+int launch_detect_tma(const TcArgs &in, cudaStream_t stream) {
+    using L = TmaSmem<M, KB>;
+    if (in.K != KB || in.N <= 0 || in.n_entries <= 0) return 1;
+    auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+    if (!al16(in.rx) || !al16(in.dict) || !al16(in.gamma) || !al16(in.dict_norm)) return 1;
+    TmaArgs a{};
+    const uint64_t D = (uint64_t)in.n_entries;
+    if (!tma_map_f32(&a.tm_q, in.rx, 2 * M, (uint64_t)in.N, 8 * M, 4, kTmaRows) ||
+        !tma_map_f32(&a.tm_d, in.dict, 2 * M, D, 8 * M, 4, kTmaEntries) ||
+        !tma_map_f32(&a.tm_g, in.gamma, 2 * KB, D, 8 * KB, 2 * KB, kTmaEntries) ||
+        !tma_map_f32(&a.tm_n, in.dict_norm, D, 0, 0, kTmaEntries, 1))
+        return 1;
+    a.rx = in.rx;
+    a.N = in.N;
+    a.dict = in.dict;
+    a.clin = in.clin;
+    a.meta = in.meta;
+    a.n_entries = in.n_entries;
+    a.k2 = in.k2;
+    a.wL = in.wL;
+    a.wG = in.wG;
+    a.soft = in.soft;
+    a.hard = in.hard;
+    a.status = in.status;
+    auto fn = detect_tma_kernel<M, KB>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes) != cudaSuccess) return -1;
+    const int grid = (in.N + kTmaRows - 1) / kTmaRows;
+    // an ordinary launch: every read may take the L1 path (see launch_detect_tc)
+    fn<<<grid, kTmaThreads, L::kBytes, stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+using TmaLauncher = int (*)(const TcArgs &, cudaStream_t);
+
+}  // namespace apsm

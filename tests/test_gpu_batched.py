@@ -12,6 +12,17 @@ from parity import assert_hard_match, assert_soft_close, gpu_params, load_state,
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(autouse=True)
+def _converter_form():
+    """The persistent batched kernel forms its Gram like the converter form of single-instance
+    detection; bit-for-bit comparisons run the single-instance calls in that form too (the
+    TMA-staged form differs from it by FP32 rounding order only, and is checked against the
+    oracle in test_gpu_parity.py)."""
+    apsm.set_option("detect_tma", 0)
+    yield
+    apsm.set_option("detect_tma", 1)
+
 SHAPES = [  # M, K, P, D, N  (P > D: eviction; ragged sizes)
     (8, 2, 300, 128, 1000),
     (16, 6, 200, 512, 3000),

@@ -108,8 +108,14 @@ def test_violated_weights_training(M, K, P, W, D):
     cl = torch.full((2 * P, W, K), 127, dtype=torch.int8, device="cuda")
     apsm.train(gp, to_dev(inst.rx_pilot), to_dev(inst.sym_pilot), st, case_log=cl)
     fst, cases, margins = oracle.train(op, inst.rx_pilot, inst.sym_pilot, log_cases=True)
-    diff = (cl.cpu().numpy() != cases) & (cases != 127)
-    assert np.all(margins[diff] < 1e-4)
+    gcl = cl.cpu().numpy()
+    diff = (gcl != cases) & (cases != 127)
+    if diff.any():
+        # a branch may differ only at a near-tie; then the oracle replays the GPU's branches
+        assert np.all(margins[diff] < 1e-5) and diff.sum() <= 4, (margins[diff].max(), diff.sum())
+        forced = np.full(cases.shape, 127, dtype=np.int8)
+        forced[diff] = gcl[diff]
+        fst = oracle.train(op, inst.rx_pilot, inst.sym_pilot, forced=forced)
     _, dg, dc = _coef_errors(op, st, fst)
     assert dg <= 1e-4 and dc <= 1e-4, (dg, dc)
     soft, _ = apsm.detect(gp, st, to_dev(inst.rx_data))
