@@ -62,6 +62,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// The same wait for a thread whose wait is not on the critical path (a producer that runs a
+// tile or more ahead): it sleeps between polls so that its spinning takes no issue slots from
+// the warps that share its scheduler.
+__device__ __forceinline__ bool mbar_wait_sleepy(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        __nanosleep(200);
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
 // 1-D bulk copy global -> shared; both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_g2s(void *smem_dst, const void *gmem_src, uint32_t bytes, uint64_t *bar) {
     asm volatile(

@@ -15,11 +15,13 @@
 // factor range).
 //
 // Staging: the query tile, each entry tile, its coefficients and its norms are tiled TMA loads
-// (2-D tensor maps, boxes of 16-byte k-chunks x rows, so that every chunk lands as the
-// core matrices of the no-swizzle K-major operand layout; rows past the tensor read as zero).
-// A short shared-memory pass by the epilogue threads splits each landed tile into its TF32 hi
+// of whole rows (one box per tile; rows past the tensor read as zero).  Query and entry rows
+// land in the swizzled K-major operand layout whose swizzle width is the row (8M bytes: 128-,
+// 64- or 32-byte swizzle for 16, 8 or 4 antennas), which the MMA reads directly.  A short
+// shared-memory pass by the epilogue threads splits each landed tile in place into its TF32 hi
 // and lo copies (zeroing rows past the held entries), turns the entry norms into -k2 n_t and
-// builds the rotated query operand.
+// builds the rotated query operand; every step of it is per element or per 16-byte chunk, so
+// the swizzle (a permutation of a row's chunks) does not matter to it.
 //
 // Roles (288 threads): warps 0-7 = epilogue; warp w reads TMEM lanes 32 (w mod 4) .. and the
 // entries 32 (w / 4) .. 32 (w / 4) + 31 of each tile, so two threads share every query row and
@@ -44,10 +46,11 @@ constexpr int kTmaRows = 128;        // queries per CTA (MMA M)
 constexpr int kTmaEntries = 64;      // entries per tile (MMA N of each accumulator)
 constexpr int kTmaEpi = 256;         // epilogue threads
 constexpr int kTmaThreads = 288;     // + one producer warp
+constexpr int kTmaChunk = 16;        // entries read from TMEM at a time (8 or 16)
 
 struct TmaArgs {
-    CUtensorMap tm_q;   // queries   [N][2M] float, box {4, 128}
-    CUtensorMap tm_d;   // entries   [D][2M] float, box {4, 64}
+    CUtensorMap tm_q;   // queries   [N][2M] float, box {2M, 128}, row swizzle
+    CUtensorMap tm_d;   // entries   [D][2M] float, box {2M, 64}, row swizzle
     CUtensorMap tm_g;   // coefficients [D][2K] float, box {2K, 64}
     CUtensorMap tm_n;   // entry norms [D] float, box {64}
     const float2 *rx;   // [N][M] (exact fallback, linear part)
@@ -67,16 +70,16 @@ struct TmaSmem {
     static constexpr int kRow = 8 * M;                    // bytes of one stored row (2M floats)
     static constexpr int kACopy = kTmaRows * kRow;        // one query operand copy
     static constexpr int kBCopy = kTmaEntries * kRow;     // one entry operand copy
-    static constexpr int kALbo = kTmaRows * 16;           // bytes between k-adjacent core matrices
-    static constexpr int kBLbo = kTmaEntries * 16;
+    static constexpr int kSbo = 8 * kRow;                 // bytes between 8-row groups (swizzle atom)
     static constexpr int kCStage = kTmaEntries * 2 * KB * 4;
     static constexpr int kA = 0;                          // [re_hi, re_lo, im_hi, im_lo]
     static constexpr int kB = kA + 4 * kACopy;            // 2 stages x [hi, lo]
     static constexpr int kC = kB + 4 * kBCopy;            // 3 stages of coefficients [E][2K]
     static constexpr int kN = kC + 3 * kCStage;           // 3 stages of norms [E]
     static constexpr int kH = kN + 3 * kTmaEntries * 4;   // 3 stages of -k2 n_t [E]
-    static constexpr int kQ = kH + 3 * kTmaEntries * 4;   // partial query norms [256]
-    static constexpr int kBar = kQ + kTmaEpi * 4;         // 12 mbarriers
+    static constexpr int kQ = kH + 3 * kTmaEntries * 4;   // query norms [128], partial linear parts
+    static constexpr int kL = kQ + kTmaRows * 4;          // the linear filter [M][K]
+    static constexpr int kBar = kL + M * KB * 8;          // 12 mbarriers
     static constexpr int kTmem = kBar + 12 * 8;
     static constexpr int kBytes = kTmem + 16;
     static_assert(kRow % 16 == 0, "rows of whole 16-byte chunks");
@@ -88,14 +91,19 @@ struct TmaSmem {
 template <int M, int KB>
 constexpr int tma_min_blocks() { return TmaSmem<M, KB>::kBytes <= 113 * 1024 ? 2 : 1; }
 
-// Shared-memory matrix descriptor, K-major, no swizzle: lbo = bytes between k-adjacent core
-// matrices, sbo = bytes between 8-row groups.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor, K-major, rows of `row` bytes swizzled over the row (row =
+// 128, 64 or 32 bytes: swizzle modes 2, 4, 6); sbo = bytes between 8-row groups.  A k-step
+// inside the row advances the start address (the swizzle is applied to the full address).
+template <int kRowBytes>
+__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t addr) {
+    static_assert(kRowBytes == 128 || kRowBytes == 64 || kRowBytes == 32, "swizzle width = row");
+    constexpr uint64_t mode = kRowBytes == 128 ? 2 : (kRowBytes == 64 ? 4 : 6);
     uint64_t d = 0;
     d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 16;                                   // leading offset: unused here
+    d |= (uint64_t)(((8 * kRowBytes) >> 4) & 0x3FFF) << 32;  // 8-row groups
     d |= (uint64_t)1 << 46;
+    d |= mode << 61;
     return d;
 }
 
@@ -115,14 +123,20 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const CUtensorMap *tm, in
         : "memory");
 }
 
-// 16 columns of this warp's TMEM lanes, without waiting (tmem_wait_ld completes the loads).
-__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+// 16 (8) columns of this warp's TMEM lanes, without waiting (tmem_wait_ld completes the loads).
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
+}
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -155,6 +169,7 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
     using L = TmaSmem<M, KB>;
     constexpr int E = kTmaEntries, CH = M / 2;  // 16-byte k-chunks per row
     constexpr int kSteps = M / 4;               // MMA k-steps of 8 TF32 elements
+    constexpr int CE = kTmaChunk;               // entries per TMEM read
     static_assert(M % 4 == 0 && KB % 2 == 0, "whole k-steps, users in pairs");
     static_assert(L::kFits, "merge area within the operand regions");
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -201,10 +216,8 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
         if ((tid & 31) == 0) {
             auto issue_b = [&](int t) {
                 const int s = t & 1;
-                unsigned char *dst = smem + L::kB + s * 2 * L::kBCopy;
                 mbar_arrive_expect_tx(&full_b[s], (uint32_t)L::kBCopy);
-#pragma unroll
-                for (int j = 0; j < CH; ++j) tma_load_2d(dst + j * E * 16, &a.tm_d, 4 * j, t * E, &full_b[s]);
+                tma_load_2d(smem + L::kB + s * 2 * L::kBCopy, &a.tm_d, 0, t * E, &full_b[s]);
             };
             auto issue_c = [&](int t) {
                 const int s = t % 3;
@@ -213,8 +226,7 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                 tma_load_1d(smem + L::kN + s * E * 4, &a.tm_n, t * E, &full_c[s]);
             };
             mbar_arrive_expect_tx(a_full, (uint32_t)L::kACopy);
-#pragma unroll
-            for (int j = 0; j < CH; ++j) tma_load_2d(smem + L::kA + j * kTmaRows * 16, &a.tm_q, 4 * j, q0, a_full);
+            tma_load_2d(smem + L::kA, &a.tm_q, 0, q0, a_full);
             int nb = 0, nc = 0;  // tiles whose entry / coefficient loads have been issued
             for (; nb < 2 && nb < n_tiles; ++nb) issue_b(nb);
             for (; nc < 2 && nc < n_tiles; ++nc) issue_c(nc);
@@ -226,8 +238,8 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
             for (int t = 0; t < n_tiles; ++t) {
                 const int s = t & 1;
                 // the epilogue threads converted tile t; the epilogue of tile t-2 freed TMEM stage s
-                if (!mbar_wait_bounded(&conv[s], (t >> 1) & 1) ||
-                    (t >= 2 && !mbar_wait_bounded(&epi_done[s], ((t - 2) >> 1) & 1))) {
+                if (!mbar_wait_sleepy(&conv[s], (t >> 1) & 1) ||
+                    (t >= 2 && !mbar_wait_sleepy(&epi_done[s], ((t - 2) >> 1) & 1))) {
                     ok = false;
                     break;
                 }
@@ -236,11 +248,11 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                 const uint32_t b0 = smem_u32(smem + L::kB + s * 2 * L::kBCopy);
 #pragma unroll
                 for (int ks = 0; ks < kSteps; ++ks) {
-                    const uint32_t ao = a0 + ks * 2 * L::kALbo, bo = b0 + ks * 2 * L::kBLbo;
-                    const uint64_t are_h = umma_desc(ao, L::kALbo, 128), are_l = umma_desc(ao + L::kACopy, L::kALbo, 128);
-                    const uint64_t aim_h = umma_desc(ao + 2 * L::kACopy, L::kALbo, 128);
-                    const uint64_t aim_l = umma_desc(ao + 3 * L::kACopy, L::kALbo, 128);
-                    const uint64_t bh = umma_desc(bo, L::kBLbo, 128), bl = umma_desc(bo + L::kBCopy, L::kBLbo, 128);
+                    const uint32_t ao = a0 + ks * 32, bo = b0 + ks * 32;  // 8 TF32 = 32 bytes per k-step
+                    const uint64_t are_h = umma_desc_sw<L::kRow>(ao), are_l = umma_desc_sw<L::kRow>(ao + L::kACopy);
+                    const uint64_t aim_h = umma_desc_sw<L::kRow>(ao + 2 * L::kACopy);
+                    const uint64_t aim_l = umma_desc_sw<L::kRow>(ao + 3 * L::kACopy);
+                    const uint64_t bh = umma_desc_sw<L::kRow>(bo), bl = umma_desc_sw<L::kRow>(bo + L::kBCopy);
                     umma_tf32(d_re, are_l, bh, idesc, ks > 0);
                     umma_tf32(d_re, are_h, bl, idesc, 1);
                     umma_tf32(d_re, are_h, bh, idesc, 1);
@@ -255,13 +267,13 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                 if (t + 2 < n_tiles) {
                     // entry stage s is free once these MMAs are done; coefficient stage (t+2) mod 3
                     // once the epilogue of tile t-1 is
-                    if (!mbar_wait_bounded(&mma_done[s], (t >> 1) & 1)) {
+                    if (!mbar_wait_sleepy(&mma_done[s], (t >> 1) & 1)) {
                         ok = false;
                         break;
                     }
                     issue_b(t + 2);
                     ++nb;
-                    if (t >= 1 && !mbar_wait_bounded(&epi_done[(t - 1) & 1], ((t - 1) >> 1) & 1)) {
+                    if (t >= 1 && !mbar_wait_sleepy(&epi_done[(t - 1) & 1], ((t - 1) >> 1) & 1)) {
                         ok = false;
                         break;
                     }
@@ -270,27 +282,34 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                 }
             }
             // every copy and MMA this thread issued has landed before the CTA may exit
-            mbar_wait_bounded(a_full, 0);
-            for (int t = max(0, nb - 2); t < nb; ++t) mbar_wait_bounded(&full_b[t & 1], (t >> 1) & 1);
-            for (int t = max(0, nc - 3); t < nc; ++t) mbar_wait_bounded(&full_c[t % 3], (t / 3) & 1);
-            if (committed >= 0) mbar_wait_bounded(&mma_done[committed & 1], (committed >> 1) & 1);
+            mbar_wait_sleepy(a_full, 0);
+            for (int t = max(0, nb - 2); t < nb; ++t) mbar_wait_sleepy(&full_b[t & 1], (t >> 1) & 1);
+            for (int t = max(0, nc - 3); t < nc; ++t) mbar_wait_sleepy(&full_c[t % 3], (t / 3) & 1);
+            if (committed >= 0) mbar_wait_sleepy(&mma_done[committed & 1], (committed >> 1) & 1);
         }
     } else {
         // ================= epilogue =================
         const int row = tid & (kTmaRows - 1), hf = tid >> 7;
         const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
         const int s_row = q0 + row;
-        // the query operand: raw rows -> [re_hi, re_lo, im_hi, im_lo]; partial squared norms
-        float nqp = 0.f;
+        // the linear filter, for the linear part at the end
+        for (int i = tid; i < M * KB; i += kTmaEpi)
+            reinterpret_cast<float2 *>(smem + L::kL)[i] = __ldg(a.clin + i);
+        // the query operand: raw rows -> [re_hi, re_lo, im_hi, im_lo] (in place, per 16-byte
+        // chunk: chunk f is one of the CH chunks of row f / CH); squared norms by row
         const bool a_ok = __all_sync(0xffffffffu, mbar_wait_bounded(a_full, 0));
-        if (a_ok) {
+        float *s_nq = s_nqp;
+        {
             float4 *q = reinterpret_cast<float4 *>(smem + L::kA);
             constexpr int QV = L::kACopy / 16;
 #pragma unroll
             for (int i = 0; i < CH / 2; ++i) {
-                const int f = tid + kTmaEpi * i;  // chunk f / 128 of row f mod 128 (= row)
-                const float4 x = q[f];
-                nqp = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, fmaf(x.w, x.w, nqp))));
+                const int f = tid + kTmaEpi * i;
+                const float4 x = a_ok ? q[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float nqp = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w)));
+#pragma unroll
+                for (int o = 1; o < CH; o <<= 1) nqp += __shfl_xor_sync(0xffffffffu, nqp, o);
+                if ((f & (CH - 1)) == 0) s_nq[f / CH] = nqp;
                 const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
                 const float4 l = make_float4(tf32_hi(x.x - h.x), tf32_hi(x.y - h.y), tf32_hi(x.z - h.z),
                                              tf32_hi(x.w - h.w));
@@ -300,7 +319,6 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                 q[3 * QV + f] = make_float4(l.y, -l.x, l.w, -l.z);
             }
         }
-        s_nqp[tid] = nqp;
         // one tile's landed loads -> operand copies, -k2 n_t, zeros past the held entries
         auto convert = [&](int t) -> bool {
             const int sb = t & 1, sc = t % 3;
@@ -312,7 +330,7 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
             for (int f = tid; f < CH * E; f += kTmaEpi) {
                 const float4 x = bh[f];
                 float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-                if ((f & (E - 1)) < nvalid) {
+                if (f / CH < nvalid) {
                     h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
                     l = make_float4(tf32_hi(x.x - h.x), tf32_hi(x.y - h.y), tf32_hi(x.z - h.z), tf32_hi(x.w - h.w));
                 }
@@ -329,8 +347,8 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
         };
         if (n_tiles > 0) ok = convert(0) && a_ok;
         else asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        ok = epi_and(ok);  // also: every partial norm is written
-        const float nq = s_nqp[row] + s_nqp[row + 128];
+        ok = epi_and(ok);  // also: every query norm and the filter are written
+        const float nq = s_nq[row];
         const bool cta_in_range = epi_and(a.k2 * nq <= kFactorLimit);
 
         float acc1[KB], acc2[KB];
@@ -385,19 +403,19 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                 const float *g = g_tile + hf * 32 * 2 * KB;
                 const float *hh = sH + sc * E + hf * 32;
 #pragma unroll 1
-                for (int c = 0; c < 2; ++c) {
-                    uint32_t vr[16], vi[16];
-                    const uint32_t col = tmem + lane_base + (uint32_t)(s * 2 * E + hf * 32 + 16 * c);
-                    tmem_ld16_async(col, vr);
-                    tmem_ld16_async(col + E, vi);
-                    float hv[16];
+                for (int c = 0; c < 32 / CE; ++c) {
+                    uint32_t vr[CE], vi[CE];
+                    const uint32_t col = tmem + lane_base + (uint32_t)(s * 2 * E + hf * 32 + CE * c);
+                    tmem_ld_async(col, vr);
+                    tmem_ld_async(col + E, vi);
+                    float hv[CE];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        *reinterpret_cast<float4 *>(hv + 4 * q) = *reinterpret_cast<const float4 *>(hh + 16 * c + 4 * q);
+                    for (int q = 0; q < CE / 4; ++q)
+                        *reinterpret_cast<float4 *>(hv + 4 * q) = *reinterpret_cast<const float4 *>(hh + CE * c + 4 * q);
                     tmem_wait_ld();
                     uint32_t fbits = 0;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                    for (int j = 0; j < CE; ++j) {
                         const float re = __uint_as_float(vr[j]), im = __uint_as_float(vi[j]);
                         float h = hv[j];
                         if constexpr (kGuard) {
@@ -411,7 +429,7 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                         fma2_scale(xA, xB, g2, h);  // (2 k2 Re z + h, 2 k2 Im z + h)
                         const float eA = ex2(xA), eB = ex2(xB), eC = ex2(fmaf(-g2, im, h));
                         float g1[KB], gg[KB];
-                        load_coef<KB>(g + (16 * c + j) * 2 * KB, g1, gg);
+                        load_coef<KB>(g + (CE * c + j) * 2 * KB, g1, gg);
 #pragma unroll
                         for (int k = 0; k < KB; k += 2) {
                             fma2_pair(acc1[k], acc1[k + 1], gg[k], gg[k + 1], eC);
@@ -426,7 +444,7 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                             while (fbits) {
                                 const int j = __ffs(fbits) - 1;
                                 fbits &= fbits - 1;
-                                exact_pair(g_tile, hf * 32 + 16 * c + j, t * E);
+                                exact_pair(g_tile, hf * 32 + CE * c + j, t * E);
                             }
                         }
                     }
@@ -439,25 +457,29 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
             if (cta_in_range) run_tiles(std::false_type{});
             else run_tiles(std::true_type{});
         }
-        // ---- merge the two halves of every row; the second half also forms the linear part -----
-        // (the operand regions are free: each thread has seen the last tile's MMAs complete)
-        float *s_part = reinterpret_cast<float *>(smem + L::kA) + row * 4 * KB;
-        if (hf == 1) {
-            float l1[KB], l2[KB];  // c_k^H r
+        // ---- merge the two halves of every row -----------------------------------------------
+        // The linear part c_k^H r is split the same way (half hf over antennas [hf M/2, (hf+1) M/2));
+        // the operand regions hold the second halves' sums (each thread has seen the last tile's
+        // MMAs complete, so nothing reads them any more).
+        float l1[KB], l2[KB];
 #pragma unroll
-            for (int k = 0; k < KB; ++k) l1[k] = l2[k] = 0.f;
-            if (s_row < a.N) {
-                const float2 *rq = a.rx + (size_t)s_row * M;
-                for (int m = 0; m < M; ++m) {
-                    const float2 r = __ldg(rq + m);
+        for (int k = 0; k < KB; ++k) l1[k] = l2[k] = 0.f;
+        if (s_row < a.N) {
+            const float2 *rq = a.rx + (size_t)s_row * M;
+            const float2 *s_clin = reinterpret_cast<const float2 *>(smem + L::kL);
+#pragma unroll 2
+            for (int m = hf * (M / 2); m < (hf + 1) * (M / 2); ++m) {
+                const float2 r = __ldg(rq + m);
 #pragma unroll
-                    for (int k = 0; k < KB; ++k) {
-                        const float2 c = __ldg(a.clin + m * KB + k);
-                        l1[k] = fmaf(c.x, r.x, fmaf(c.y, r.y, l1[k]));
-                        l2[k] = fmaf(c.x, r.y, fmaf(-c.y, r.x, l2[k]));
-                    }
+                for (int k = 0; k < KB; ++k) {
+                    const float2 c = s_clin[m * KB + k];
+                    l1[k] = fmaf(c.x, r.x, fmaf(c.y, r.y, l1[k]));
+                    l2[k] = fmaf(c.x, r.y, fmaf(-c.y, r.x, l2[k]));
                 }
             }
+        }
+        float *s_part = reinterpret_cast<float *>(smem + L::kA) + row * 4 * KB;
+        if (hf == 1) {
 #pragma unroll
             for (int k = 0; k < KB; ++k) {
                 s_part[k] = acc1[k];
@@ -471,8 +493,8 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
             const float fq = cta_in_range ? ex2(-a.k2 * nq) : 1.f;  // query factor
 #pragma unroll
             for (int k = 0; k < KB; ++k) {
-                const float y1 = fmaf(a.wL, s_part[2 * KB + k], a.wG * fq * (acc1[k] + s_part[k]));
-                const float y2 = fmaf(a.wL, s_part[3 * KB + k], a.wG * fq * (acc2[k] + s_part[KB + k]));
+                const float y1 = fmaf(a.wL, l1[k] + s_part[2 * KB + k], a.wG * fq * (acc1[k] + s_part[k]));
+                const float y2 = fmaf(a.wL, l2[k] + s_part[3 * KB + k], a.wG * fq * (acc2[k] + s_part[KB + k]));
                 a.soft[(size_t)s_row * KB + k] = make_float2(y1, y2);
                 if (a.hard) a.hard[(size_t)s_row * KB + k] = (uint8_t)((y1 < 0.f ? 1 : 0) | (y2 < 0.f ? 2 : 0));
             }
@@ -496,7 +518,8 @@ TmaEncodeFn tma_encode_fn();  // the driver's tiled tensor-map encoder (detect_d
 // FP32 tensor map over `rows` rows of `inner` floats (row pitch row_bytes), box box_inner x
 // box_rows (rank 1 when rows == 0: `inner` floats, box box_inner).  Out-of-range boxes read zero.
 inline bool tma_map_f32(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
-                        uint32_t box_inner, uint32_t box_rows) {
+                        uint32_t box_inner, uint32_t box_rows,
+                        CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_NONE) {
     const TmaEncodeFn enc = tma_encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[2] = {inner, rows};
@@ -504,7 +527,7 @@ inline bool tma_map_f32(CUtensorMap *m, const void *base, uint64_t inner, uint64
     const cuuint32_t box[2] = {box_inner, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rows ? 2 : 1, const_cast<void *>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -519,8 +542,10 @@ int launch_detect_tma(const TcArgs &in, cudaStream_t stream) {
     if (!al16(in.rx) || !al16(in.dict) || !al16(in.gamma) || !al16(in.dict_norm)) return 1;
     TmaArgs a{};
     const uint64_t D = (uint64_t)in.n_entries;
-    if (!tma_map_f32(&a.tm_q, in.rx, 2 * M, (uint64_t)in.N, 8 * M, 4, kTmaRows) ||
-        !tma_map_f32(&a.tm_d, in.dict, 2 * M, D, 8 * M, 4, kTmaEntries) ||
+    constexpr CUtensorMapSwizzle swz = M == 16 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                       : (M == 8 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    if (!tma_map_f32(&a.tm_q, in.rx, 2 * M, (uint64_t)in.N, 8 * M, 2 * M, kTmaRows, swz) ||
+        !tma_map_f32(&a.tm_d, in.dict, 2 * M, D, 8 * M, 2 * M, kTmaEntries, swz) ||
         !tma_map_f32(&a.tm_g, in.gamma, 2 * KB, D, 8 * KB, 2 * KB, kTmaEntries) ||
         !tma_map_f32(&a.tm_n, in.dict_norm, D, 0, 0, kTmaEntries, 1))
         return 1;
