@@ -104,7 +104,7 @@ def code_digest(texts):
 
 def kernel_digest():
     texts = []
-    for f in ("detect_tc.cuh", "detect_f32.cuh", "apsm_common.cuh"):
+    for f in ("detect_tma.cuh", "detect_tc.cuh", "detect_f32.cuh", "apsm_common.cuh"):
         with open(os.path.join(ROOT, "paper_2201_05024_gb300", "csrc", f)) as fh:
             texts.append(fh.read())
     return code_digest(texts)
@@ -554,13 +554,14 @@ def main():
     ws = torch.empty((max(apsm.train_workspace_bytes(gp, w["P"]), 1),), dtype=torch.uint8, device=dev)
     soft = torch.empty((w["N"], w["K"]), dtype=torch.complex64, device=dev)
     hard = torch.empty((w["N"], w["K"]), dtype=torch.uint8, device=dev)
+    dws = apsm.detect_workspace(gp, w["N"], device=dev)  # balanced detection form
     flush = torch.empty((max(args.flush_mb, 1) << 18,), dtype=torch.float32, device=dev)
     do_flush = args.flush_mb > 0
     stream = torch.cuda.current_stream()
 
     def step():
         apsm.train(gp, rp, sp, st, workspace=ws)
-        apsm.detect(gp, st, rd, soft=soft, hard=hard)
+        apsm.detect(gp, st, rd, soft=soft, hard=hard, workspace=dws)
 
     for _ in range(max(args.warmup, 3)):
         if do_flush:
@@ -584,7 +585,7 @@ def main():
         ev[i][0].record(stream)
         apsm.train(gp, rp, sp, st, workspace=ws)
         ev[i][1].record(stream)
-        apsm.detect(gp, st, rd, soft=soft, hard=hard)
+        apsm.detect(gp, st, rd, soft=soft, hard=hard, workspace=dws)
         ev[i][2].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -609,14 +610,14 @@ def main():
         hs = torch.from_numpy(inst.sym_pilot).pin_memory()
         hd = torch.from_numpy(inst.rx_data).pin_memory()
         for _ in range(2):
-            apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
+            apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev, workspace=dws)
         e2e_times = []
         for _ in range(max(3, min(args.steps, 10))):
             if do_flush:
                 flush.fill_(0.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            soft_h, hard_h = apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev)
+            soft_h, hard_h = apsm.train_detect_host(gp, hp, hs, hd, state=st, device=dev, workspace=dws)
             e2e_times.append(time.perf_counter() - t0)
         e2e_step = sum(e2e_times) / len(e2e_times)
         e2e_step = reduce_max(dist, [e2e_step], dev)[0]
@@ -644,7 +645,7 @@ def main():
                    "ms": mean_detect},
         "train": {"value": world * w["P"] * w["K"] / (mean_train / 1e3), "unit": "pilot-updates/s",
                   "ms": mean_train, "us_per_pilot": mean_train * 1e3 / w["P"]},
-        "roofline": {"kernel": "detect_tc_kernel<16,6,TF32x3>", **roof},
+        "roofline": {"kernel": "detect_tma_kernel<16,6> (TF32 x3 Gram, balanced form)", **roof},
         "gpu_launches": int(launches),
         "wall_s_timed": wall,
         "e2e": e2e,

@@ -252,6 +252,27 @@ apsm_status apsm_train_noalloc(const apsm_params *p, const float *rx_pilot, cons
 apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
                         uint8_t *hard, void *stream);
 
+/*
+ * Detection balanced over the SMs (the same results as apsm_detect up to FP32 rounding order;
+ * Sec. III-B detection).  FP32 detection with 4, 8 or 16 antennas and an even user count in
+ * {2, 4, 6, 8, 12, 16} splits its (query tile, dictionary tile) work evenly over a persistent
+ * grid; a query tile split between CTAs leaves each part's sums in the workspace and the CTA
+ * that brings its last part adds the parts in a fixed order (results do not depend on timing).
+ *   apsm_detect_workspace_bytes: bytes for N data vectors on the current device; 0 where the
+ *     balanced form does not apply (apsm_detect_ws then runs apsm_detect).
+ *   workspace  device, 256-byte aligned, at least that many bytes, ZERO-FILLED before its first
+ *     use.  It starts with one arrival counter per 128 data vectors (int32); every call that
+ *     completes without a status error leaves them at zero again (the rest is scratch).  After
+ *     a status error, fill the workspace with zeros again before the next call.  One workspace
+ *     per call in flight (calls that overlap on different streams need different workspaces).
+ *     NULL: apsm_detect.
+ * Other arguments and errors as for apsm_detect; APSM_ERR_INVALID_ARG for an unaligned
+ * workspace.  A workspace smaller than the balanced form needs runs apsm_detect.
+ */
+apsm_status apsm_detect_workspace_bytes(const apsm_params *p, int32_t N, size_t *bytes);
+apsm_status apsm_detect_ws(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
+                           uint8_t *hard, void *workspace, size_t workspace_bytes, void *stream);
+
 /* Bytes of device workspace apsm_detect_backward needs for N data vectors. */
 apsm_status apsm_detect_backward_workspace_bytes(const apsm_params *p, int32_t N, size_t *bytes);
 

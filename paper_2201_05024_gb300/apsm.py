@@ -70,6 +70,8 @@ def load_library(path: str | None = None):
         lib.apsm_train_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_train.argtypes = [P, vp, vp, ctypes.c_int32, vp, S, vp, ctypes.c_size_t, vp, vp]
         lib.apsm_detect.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp]
+        lib.apsm_detect_ws.argtypes = [P, S, vp, ctypes.c_int32, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.apsm_detect_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_read_status.argtypes = [S, ctypes.POINTER(ctypes.c_int32), vp]
         lib.apsm_check_wait_timeout.argtypes = [S, vp]
         lib.apsm_state_set.argtypes = [P, vp, vp, vp, vp, ctypes.c_int32, S, vp]
@@ -94,7 +96,8 @@ def load_library(path: str | None = None):
         lib.apsm_status_string.argtypes = [ctypes.c_int]
         lib.apsm_status_string.restype = ctypes.c_char_p
         lib.apsm_launch_count.restype = ctypes.c_int64
-        for f in ("apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_train", "apsm_detect",
+        for f in ("apsm_dict_alloc", "apsm_train_workspace_bytes", "apsm_train", "apsm_detect", "apsm_detect_ws",
+                  "apsm_detect_workspace_bytes",
                   "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
                   "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
                   "apsm_train_backward_workspace_bytes", "apsm_train_backward",
@@ -284,9 +287,24 @@ def set_option(name: str, value: int):
     _check(load_library().apsm_set_option(_OPTIONS[name], int(value)), "apsm_set_option")
 
 
+def detect_workspace_bytes(p: Params, N: int) -> int:
+    """apsm_detect_workspace_bytes: bytes of the balanced detection form's workspace (0: none)."""
+    nb = ctypes.c_size_t()
+    _check(load_library().apsm_detect_workspace_bytes(ctypes.byref(p.c()), int(N), ctypes.byref(nb)),
+           "apsm_detect_workspace_bytes")
+    return nb.value
+
+
+def detect_workspace(p: Params, N: int, device="cuda") -> torch.Tensor | None:
+    """A zero-filled workspace for apsm_detect_ws on N vectors (None where the form does not apply)."""
+    nb = detect_workspace_bytes(p, N)
+    return torch.zeros((nb,), dtype=torch.uint8, device=device) if nb else None
+
+
 def detect(p: Params, state: State, rx: torch.Tensor, *, soft: torch.Tensor | None = None,
-           hard: torch.Tensor | None = None, want_hard: bool = True):
-    """apsm_detect: soft [N][K] complex64 estimates and Gray QPSK decisions [N][K] uint8."""
+           hard: torch.Tensor | None = None, want_hard: bool = True, workspace: torch.Tensor | None = None):
+    """apsm_detect (apsm_detect_ws with a workspace from detect_workspace): soft [N][K] complex64
+    estimates and Gray decisions [N][K] uint8."""
     lib = load_library()
     N = int(rx.shape[0])
     _dev(rx, torch.complex64, (N, p.M), "rx")
@@ -298,8 +316,12 @@ def detect(p: Params, state: State, rx: torch.Tensor, *, soft: torch.Tensor | No
     if hard is not None:
         _dev(hard, torch.uint8, (N, p.K), "hard")
     st = state.c()
-    _check(lib.apsm_detect(ctypes.byref(p.c()), ctypes.byref(st), _ptr(rx), N, _ptr(soft), _ptr(hard), _stream()),
-           "apsm_detect")
+    if workspace is not None:
+        _check(lib.apsm_detect_ws(ctypes.byref(p.c()), ctypes.byref(st), _ptr(rx), N, _ptr(soft), _ptr(hard),
+                                  _ptr(workspace), workspace.numel(), _stream()), "apsm_detect_ws")
+    else:
+        _check(lib.apsm_detect(ctypes.byref(p.c()), ctypes.byref(st), _ptr(rx), N, _ptr(soft), _ptr(hard),
+                               _stream()), "apsm_detect")
     return soft, hard
 
 
@@ -542,17 +564,18 @@ def launch_count() -> int:
 
 
 def train_detect_host(p: Params, rx_pilot, sym_pilot, rx_data, *, state: State | None = None,
-                      device="cuda"):
+                      device="cuda", workspace: torch.Tensor | None = None):
     """End-to-end call on HOST tensors: copy pilots, symbols and data vectors to the device,
-    train, detect, and copy the soft and hard outputs back.  Host inputs should be pinned for
-    asynchronous copies.  Returns (soft, hard) as host tensors."""
+    train, detect (balanced form with `workspace`, see detect_workspace), and copy the soft and
+    hard outputs back.  Host inputs should be pinned for asynchronous copies.  Returns (soft,
+    hard) as host tensors."""
     dev = torch.device(device)
     rp = rx_pilot.to(dev, non_blocking=True)
     sp = sym_pilot.to(dev, non_blocking=True)
     rd = rx_data.to(dev, non_blocking=True)
     st = state if state is not None else State(p, device=dev)
     train(p, rp, sp, st)
-    soft, hard = detect(p, st, rd)
+    soft, hard = detect(p, st, rd, workspace=workspace)
     soft_h = torch.empty(soft.shape, dtype=soft.dtype, pin_memory=True)
     hard_h = torch.empty(hard.shape, dtype=hard.dtype, pin_memory=True)
     soft_h.copy_(soft, non_blocking=True)

@@ -62,6 +62,11 @@ apsm_status check_state(const apsm_state *st) {
     return APSM_OK;
 }
 
+int current_device() {
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess ? dev : 0;
+}
+
 // sm_103 check, cached per device.
 apsm_status check_device() {
     static std::mutex mu;
@@ -614,13 +619,14 @@ apsm_status apsm_train_continue(const apsm_params *p, const float *rx, const flo
                      static_cast<cudaStream_t>(stream));
 }
 
-apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
-                        uint8_t *hard, void *stream) {
+apsm_status apsm_detect_ws(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
+                           uint8_t *hard, void *workspace, size_t workspace_bytes, void *stream) {
     apsm_status s = check_params(p);
     if (s != APSM_OK) return s;
     if ((s = check_state(st)) != APSM_OK) return s;
     if (N < 0 || (N > 0 && (!rx || !soft))) return APSM_ERR_INVALID_ARG;
     if (N > 0 && (!aligned16(rx) || (reinterpret_cast<uintptr_t>(soft) & 7))) return APSM_ERR_INVALID_ARG;
+    if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return APSM_ERR_INVALID_ARG;
     if ((s = check_device()) != APSM_OK) return s;
     if (N == 0) return APSM_OK;
     cudaStream_t strm = static_cast<cudaStream_t>(stream);
@@ -654,8 +660,12 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
             ta.hard = hard;
             ta.status = st->meta + 3;
             if (qam_pass) ta.hard = nullptr;
-            // the TMA-staged form where it applies (shape, alignment), else the converter form
-            const int r = tma ? tma(ta, strm) : 1;
+            // the TMA-staged form where it applies (shape, alignment; balanced over the SMs with a
+            // workspace), else the converter form
+            int sms = 0;
+            if (tma && workspace && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, current_device()) != cudaSuccess)
+                return APSM_ERR_CUDA;
+            const int r = tma ? tma(ta, workspace, workspace_bytes, sms, strm) : 1;
             if (r < 0) return APSM_ERR_CUDA;
             if (r > 0 && (!tc || tc(ta, strm) != cudaSuccess)) return tc ? APSM_ERR_CUDA : APSM_ERR_UNSUPPORTED;
             g_launches++;
@@ -687,6 +697,26 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
     if (det(da, 1, sh, strm) != cudaSuccess) return APSM_ERR_CUDA;
     g_launches++;
     return qam_pass ? qam_labels(soft, hard, N, p, strm) : APSM_OK;
+}
+
+apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float *rx, int32_t N, float *soft,
+                        uint8_t *hard, void *stream) {
+    return apsm_detect_ws(p, st, rx, N, soft, hard, nullptr, 0, stream);
+}
+
+apsm_status apsm_detect_workspace_bytes(const apsm_params *p, int32_t N, size_t *bytes) {
+    if (!bytes) return APSM_ERR_INVALID_ARG;
+    *bytes = 0;
+    apsm_status s = check_params(p);
+    if (s != APSM_OK) return s;
+    if (N < 0) return APSM_ERR_INVALID_ARG;
+    if (N == 0 || p->dtype != APSM_FP32 || !detect_tma_launcher(p->M, p->K)) return APSM_OK;
+    if ((s = check_device()) != APSM_OK) return s;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, current_device()) != cudaSuccess)
+        return APSM_ERR_CUDA;
+    *bytes = tma_workspace(N, p->K, 2 * sms).total;
+    return APSM_OK;
 }
 
 apsm_status apsm_state_set(const apsm_params *p, const float *entries, const float *gamma, const float *clin,

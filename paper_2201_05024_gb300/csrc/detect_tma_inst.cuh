@@ -17,9 +17,7 @@ TmaLauncher APSM_TMA_CAT(detect_tma_launcher_m, APSM_TMA_M)(int K) {
         case 6: return launch_detect_tma<M, 6>;
         case 8: return launch_detect_tma<M, 8>;
         case 12: return launch_detect_tma<M, 12>;
-        case 16:
-            if constexpr (TmaSmem<M, 16>::kFits) return launch_detect_tma<M, 16>;
-            return nullptr;
+        case 16: return launch_detect_tma<M, 16>;
         default: return nullptr;
     }
 }

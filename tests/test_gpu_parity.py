@@ -98,6 +98,88 @@ def test_detect_ignores_slots_past_the_held_entries(M, K, engine):
     assert apsm.read_status(st) == 0
 
 
+BALANCED_CASES = [
+    # M, K, D entries, N queries
+    (16, 6, 1024, 8192),      # 64 query tiles x 16 entry tiles over the SMs: tiles split between CTAs
+    (16, 6, 1000, 3001),      # ragged entry tile and query tail
+    (8, 4, 300, 1000),        # 40 units: fewer than the CTAs (CTAs with one unit or none)
+    (4, 2, 64, 129),          # one entry tile
+    (16, 12, 700, 5000),      # one CTA per SM (12 users)
+    (16, 2, 1, 200),          # a single entry
+    (8, 16, 2000, 777),       # 32 entry tiles over 7 query tiles
+]
+
+
+@pytest.mark.parametrize("M,K,D,N", BALANCED_CASES)
+def test_balanced_detection(M, K, D, N):
+    """apsm_detect_ws: the work split evenly over the SMs, split query tiles merged through the
+    workspace.  Against the FP64 oracle; bit-identical on a second call; the workspace's arrival
+    counters are left at zero; the same soft outputs as the plain form up to FP32 rounding order."""
+    ent, gam, clin = synth.random_state(M, K, D, instance=3 * D + M + K)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=N + M)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.5, w_L=0.5)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    ws = apsm.detect_workspace(gp, N)
+    assert ws is not None and ws.numel() > 0
+    rx = to_dev(inst.rx_data)
+    soft, hard = apsm.detect(gp, st, rx, workspace=ws)
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
+    assert_soft_close(soft.cpu().numpy(), ref)
+    assert_hard_match(hard.cpu().numpy(), ref)
+    assert apsm.read_status(st) == 0
+    assert torch.count_nonzero(ws[:4 * ((N + 127) // 128)]) == 0
+    soft2, hard2 = apsm.detect(gp, st, rx, workspace=ws)
+    assert torch.equal(soft, soft2) and torch.equal(hard, hard2)
+    plain, _ = apsm.detect(gp, st, rx)
+    assert_soft_close(soft.cpu().numpy(), plain.cpu().numpy().astype(np.complex128), tol=1e-5, what="plain form")
+
+
+def test_balanced_detection_ignores_slots_past_the_held_entries():
+    M, K, D, n, N = 16, 6, 1000, 333, 4000
+    ent, gam, clin = synth.random_state(M, K, n, instance=77)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=78)
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.5, w_L=0.5)
+    gp = gpu_params(op)
+    st = apsm.State(gp)
+    st.dict.fill_(complex(float("nan"), float("nan")))
+    st.dict_norm.fill_(float("nan"))
+    st.gamma.fill_(float("nan"))
+    apsm.state_set(gp, st, to_dev(np.asarray(ent, np.complex64)), to_dev(np.asarray(gam, np.float32)),
+                   to_dev(np.asarray(clin, np.complex64)))
+    ws = apsm.detect_workspace(gp, N)
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data), workspace=ws)
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
+    assert_soft_close(soft.cpu().numpy(), ref)
+    assert_hard_match(hard.cpu().numpy(), ref)
+    assert torch.count_nonzero(ws[:4 * ((N + 127) // 128)]) == 0
+
+
+@pytest.mark.parametrize("case", ["offset", "mixed_queries"])
+def test_balanced_detection_unnormalised_inputs(case):
+    """Query tiles outside the factor range take the guarded form in the balanced kernel too."""
+    M, K, D, N = 16, 6, 200, 1500
+    rng = np.random.default_rng(12)
+    ent, gam, clin = synth.random_state(M, K, D, instance=5)
+    inst = synth.make_instance(M, K, 4, N, 10.0, instance=6)
+    rx = inst.rx_data.copy()
+    sigma = 0.5
+    if case == "offset":
+        base = (rng.standard_normal(M) + 1j * rng.standard_normal(M)) * 1.6
+        ent = (ent + base).astype(np.complex64)
+        rx = (rx * 0.5 + base).astype(np.complex64)
+        sigma = 0.8
+    else:
+        rx[::97] *= 5.0
+    op = oracle.Params(M=M, K=K, W=1, D=D, sigma=sigma, w_L=0.5)
+    gp = gpu_params(op)
+    st = load_state(gp, ent, gam, clin)
+    soft, hard = apsm.detect(gp, st, to_dev(rx), workspace=apsm.detect_workspace(gp, N))
+    ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), rx)
+    assert_soft_close(soft.cpu().numpy(), ref)
+    assert_hard_match(hard.cpu().numpy(), ref)
+
+
 @pytest.mark.parametrize("M,K", [(16, 6), (64, 5)])
 @pytest.mark.parametrize("case", ["offset", "mixed_entries", "mixed_queries"])
 def test_detect_unnormalised_inputs(case, M, K, engine):
