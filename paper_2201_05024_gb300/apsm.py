@@ -453,6 +453,104 @@ def train_detect_autograd(p: Params, rx_pilot, sym_pilot, rx, clin0, sigma, mu, 
     return TrainDetectFunction.apply(clin0, sigma, mu, eps, w_L, p, rx_pilot, sym_pilot, rx)
 
 
+class GradBatch:
+    """Batched differentiation form: forward (train from c_0, detect) and backward (loss gradient
+    dsoft = 2 (soft - target), apsm_detect_backward, apsm_train_backward) of many independent
+    instances with the same parameters, on `lanes` CUDA streams with no host synchronisation
+    between instances; with graph=True the whole pass is captured once and replayed as one CUDA
+    graph.  Every buffer is allocated here, once.  Per-instance results stay on the device:
+    loss [n] (sum |soft - target|^2), dscalars [n][4] (d sigma, d mu, d eps, d w_L) and
+    dclin0 [n][M][K]; grads() sums them over the instances in instance order.  Each instance's
+    results equal those of the same calls made one instance at a time, bit for bit.
+    backward=False: the forward pass alone (soft outputs in buf[i]["soft"])."""
+
+    def __init__(self, p: Params, instances, clin0: torch.Tensor, *, lanes: int = 16, graph: bool = False,
+                 backward: bool = True):
+        lib = load_library()
+        self.p, self.lanes, self.backward = p, max(1, int(lanes)), backward
+        self.inst = [tuple(t.contiguous() for t in x) for x in instances]  # (rx_pilot, sym_pilot, rx, target)
+        n = len(self.inst)
+        dev = self.inst[0][0].device
+        _dev(clin0, torch.complex64, (p.M, p.K), "clin0")
+        self.clin0 = clin0
+        self.states, self.buf = [], []
+        for rp, sp, rd, sd in self.inst:
+            P, N = int(rp.shape[0]), int(rd.shape[0])
+            nb_t, nb_d, nb_b = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+            _check(lib.apsm_train_workspace_bytes(ctypes.byref(p.c()), P, ctypes.byref(nb_t)), "apsm_train_workspace_bytes")
+            _check(lib.apsm_detect_backward_workspace_bytes(ctypes.byref(p.c()), N, ctypes.byref(nb_d)),
+                   "apsm_detect_backward_workspace_bytes")
+            _check(lib.apsm_train_backward_workspace_bytes(ctypes.byref(p.c()), P, ctypes.byref(nb_b)),
+                   "apsm_train_backward_workspace_bytes")
+            st = State(p, device=dev)
+            self.states.append(st)
+            self.buf.append(dict(
+                ws_t=torch.empty((max(nb_t.value, 1),), dtype=torch.uint8, device=dev),
+                ws_d=torch.empty((max(nb_d.value, 1),), dtype=torch.uint8, device=dev),
+                ws_b=torch.empty((max(nb_b.value, 1),), dtype=torch.uint8, device=dev),
+                soft=torch.empty((N, p.K), dtype=torch.complex64, device=dev),
+                dsoft=torch.empty((N, p.K), dtype=torch.complex64, device=dev),
+                dgamma=torch.empty_like(st.gamma), dclin=torch.empty_like(st.clin),
+                dsd=torch.empty((2,), dtype=torch.float32, device=dev)))
+        self.loss = torch.zeros((n,), dtype=torch.float32, device=dev)
+        self.dst = torch.zeros((n, 4), dtype=torch.float32, device=dev)
+        self.dclin0 = torch.zeros((n, p.M, p.K), dtype=torch.complex64, device=dev)
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(self.lanes)]
+        self.graph = None
+        if graph:
+            self._run()                                  # warm-up outside the capture
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._run()
+            self.graph = g
+
+    def _instance(self, i):
+        lib = load_library()
+        p, (rp, sp, rd, sd), st, b = self.p, self.inst[i], self.states[i], self.buf[i]
+        P, N = int(rp.shape[0]), int(rd.shape[0])
+        c, strm = st.c(), _stream()
+        _check(lib.apsm_train(ctypes.byref(p.c()), _ptr(rp), _ptr(sp), P, _ptr(self.clin0), ctypes.byref(c),
+                              _ptr(b["ws_t"]), b["ws_t"].numel(), None, strm), "apsm_train")
+        _check(lib.apsm_detect(ctypes.byref(p.c()), ctypes.byref(c), _ptr(rd), N, _ptr(b["soft"]), None, strm),
+               "apsm_detect")
+        if not self.backward:
+            return
+        torch.sub(b["soft"], sd, out=b["dsoft"])
+        self.loss[i] = b["dsoft"].abs().square().sum()
+        b["dsoft"].mul_(2.0)
+        _check(lib.apsm_detect_backward(ctypes.byref(p.c()), ctypes.byref(c), _ptr(rd), N, _ptr(b["dsoft"]),
+                                        _ptr(b["dgamma"]), _ptr(b["dclin"]), _ptr(b["dsd"]), _ptr(b["ws_d"]),
+                                        b["ws_d"].numel(), strm), "apsm_detect_backward")
+        _check(lib.apsm_train_backward(ctypes.byref(p.c()), _ptr(rp), _ptr(sp), P, _ptr(self.clin0),
+                                       _ptr(b["dgamma"]), _ptr(b["dclin"]), _ptr(self.dst[i]), _ptr(self.dclin0[i]),
+                                       _ptr(b["ws_b"]), b["ws_b"].numel(), strm), "apsm_train_backward")
+        # sigma and w_L also enter through the detection
+        self.dst[i, 0] += b["dsd"][0]
+        self.dst[i, 3] += b["dsd"][1]
+
+    def _run(self):
+        main = torch.cuda.current_stream()
+        for s in self.streams:
+            s.wait_stream(main)
+        for i in range(len(self.inst)):
+            with torch.cuda.stream(self.streams[i % self.lanes]):
+                self._instance(i)
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def run(self):
+        """One forward + backward pass over every instance (no host synchronisation)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._run()
+
+    def grads(self):
+        """(sum of losses, d sigma, d mu, d eps, d w_L, dclin0 [M][K]) summed in instance order."""
+        return self.loss.sum(), self.dst.sum(0), self.dclin0.sum(0)
+
+
 ENGINES = {"tensor": 0, "ffma": 1}
 
 

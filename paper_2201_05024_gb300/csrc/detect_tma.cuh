@@ -35,11 +35,11 @@
 // Roles (288 threads): warps 0-7 = epilogue; warp w reads TMEM lanes 32 (w mod 4) .. and the
 // entries 32 (w / 4) .. 32 (w / 4) + 31 of each tile, so two threads share every query row; at
 // the end of a segment the second half passes its sums through TMEM to the first, which adds
-// them in a fixed order.  The epilogue threads convert entry tile j+1 at the start of tile j.
-// Warp 8 = producer: lane 0 issues the TMA loads and the MMAs; the warp builds the next
-// segment's query operand as soon as the MMAs of the current segment are done.  Entry operand
-// (hi, lo) two stages, coefficients and norms three, TMEM two accumulator pairs.  All waits are
-// bounded.
+// them in a fixed order.  The epilogue threads build a segment's query operand at its start
+// (its rows were loaded as soon as the previous segment's MMAs were done) and convert entry
+// tile j+1 at the start of tile j.  Warp 8, lane 0 = producer: issues the TMA loads and the
+// MMAs.  Entry operand (hi, lo) two stages, coefficients and norms three, TMEM two accumulator
+// pairs.  All waits are bounded.
 //
 // Used for FP32 detection with 4, 8 or 16 antennas and an even user count that is its own
 // bucket (2, 4, 6, 8, 12, 16), where the state's arrays are 16-byte aligned.
@@ -88,9 +88,9 @@ struct TmaSmem {
     static constexpr int kB = kA + 4 * kACopy;            // 2 stages x [hi, lo]
     static constexpr int kC = kB + 4 * kBCopy;            // 3 stages of coefficients [E][2K]
     static constexpr int kN = kC + 3 * kCStage;           // 3 stages of norms [E], then -k2 n_t
-    static constexpr int kQ = kN + 3 * kTmaEntries * 4;   // 2 x query norms [128], 2 range flags, flag
-    static constexpr int kBar = kQ + 2 * kTmaRows * 4 + 16;  // 15 mbarriers
-    static constexpr int kTmem = kBar + 15 * 8;
+    static constexpr int kQ = kN + 3 * kTmaEntries * 4;   // query norms [128], a flag
+    static constexpr int kBar = kQ + kTmaRows * 4 + 16;   // 13 mbarriers
+    static constexpr int kTmem = kBar + 13 * 8;
     static constexpr int kBytes = kTmem + 16;
     static_assert(kRow % 16 == 0, "rows of whole 16-byte chunks");
     static_assert(kC % 1024 == 0 && kCStage % 128 == 0, "TMA destinations 128-byte aligned");
@@ -207,12 +207,12 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kBar);
     uint64_t *a_full = bars, *full_b = bars + 1, *full_c = bars + 3, *conv = bars + 6, *a_ready = bars + 8,
-             *nq_read = bars + 9, *mma_done = bars + 11, *epi_done = bars + 13;
+             *mma_done = bars + 9, *epi_done = bars + 11;
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + L::kTmem);
     float *sG = reinterpret_cast<float *>(smem + L::kC);
     float *sH = reinterpret_cast<float *>(smem + L::kN);  // norms as landed, then -k2 n_t
-    float *s_nq = reinterpret_cast<float *>(smem + L::kQ);  // [2][128]
-    int *s_flag = reinterpret_cast<int *>(smem + L::kQ + 2 * kTmaRows * 4);  // [2] range, [2] last part
+    float *s_nq = reinterpret_cast<float *>(smem + L::kQ);                 // [128]
+    int *s_last = reinterpret_cast<int *>(smem + L::kQ + kTmaRows * 4);    // a split tile's last part
 
     const int tid = threadIdx.x, warp = tid >> 5;
     int n_ent = a.n_entries;
@@ -232,12 +232,11 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
     }
     if (tid == 0) {
         mbar_init(a_full, 1);
-        mbar_init(a_ready, 1);
+        mbar_init(a_ready, kTmaEpi);
         for (int i = 0; i < 3; ++i) mbar_init(&full_c[i], 1);
         for (int i = 0; i < 2; ++i) {
             mbar_init(&full_b[i], 1);
             mbar_init(&conv[i], kTmaEpi);
-            mbar_init(&nq_read[i], kTmaEpi);
             mbar_init(&mma_done[i], 1);
             mbar_init(&epi_done[i], kTmaEpi);
         }
@@ -276,11 +275,9 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
         int j = 0;
         for (int u = u_lo, k = 0; u < u_hi && pok; ++k) {
             const int q = u / NT, u_end = min(u_hi, (q + 1) * NT), j_end = j + (u_end - u);
-            // ---- this segment's query operand: the previous segment's MMAs are done with A, and
-            // the epilogue has read the query norms of segment k-2 (same buffer)
+            // ---- this segment's query rows: the previous segment's MMAs are done with A
             if (lane == 0) {
                 if (k > 0) pok = mbar_wait_sleepy(&mma_done[(j - 1) & 1], ((j - 1) >> 1) & 1);
-                if (pok && k >= 2) pok = mbar_wait_sleepy(&nq_read[k & 1], ((k - 2) >> 1) & 1);
                 if (pok) {
                     mbar_arrive_expect_tx(a_full, (uint32_t)L::kACopy);
                     tma_load_2d(smem + L::kA, &a.tm_q, 0, q * kTmaRows, a_full);
@@ -289,44 +286,14 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
             }
             pok = __shfl_sync(0xffffffffu, pok, 0);
             if (!pok) break;
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(a_full, k & 1))) {
-                pok = false;
-                break;
-            }
-            {
-                // raw rows -> [re_hi, re_lo, im_hi, im_lo] in place per 16-byte chunk (chunk f is
-                // one of the CH chunks of row f / CH; CH consecutive lanes hold one row)
-                float4 *qv = reinterpret_cast<float4 *>(smem + L::kA);
-                constexpr int QV = L::kACopy / 16;
-                bool in_range = true;
-#pragma unroll 4
-                for (int f = lane; f < QV; f += 32) {
-                    const float4 x = qv[f];
-                    float nq = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w)));
-#pragma unroll
-                    for (int o = 1; o < CH; o <<= 1) nq += __shfl_xor_sync(0xffffffffu, nq, o);
-                    if ((f & (CH - 1)) == 0) s_nq[(k & 1) * kTmaRows + f / CH] = nq;
-                    in_range = in_range && a.k2 * nq <= kFactorLimit;
-                    const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-                    const float4 l = make_float4(tf32_hi(x.x - h.x), tf32_hi(x.y - h.y), tf32_hi(x.z - h.z),
-                                                 tf32_hi(x.w - h.w));
-                    qv[f] = h;
-                    qv[QV + f] = l;
-                    qv[2 * QV + f] = make_float4(h.y, -h.x, h.w, -h.z);  // (Im, -Re) pairs
-                    qv[3 * QV + f] = make_float4(l.y, -l.x, l.w, -l.z);
-                }
-                in_range = __all_sync(0xffffffffu, in_range);
-                if (lane == 0) s_flag[k & 1] = in_range ? 1 : 0;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(a_ready);  // releases the norms and the range flag
-            }
             // ---- the segment's tiles (lane 0)
             if (lane == 0) {
+                const int j0 = j;
                 for (; j < j_end && pok; ++j) {
                     const int s = j & 1;
-                    // the epilogue converted tile j; the epilogue of tile j-2 freed TMEM stage s
-                    if (!mbar_wait_sleepy(&conv[s], (j >> 1) & 1) ||
+                    // the epilogue converted tile j (and, before the segment's first tile, built
+                    // the query operand); the epilogue of tile j-2 freed TMEM stage s
+                    if ((j == j0 && !mbar_wait_sleepy(a_ready, k & 1)) || !mbar_wait_sleepy(&conv[s], (j >> 1) & 1) ||
                         (j >= 2 && !mbar_wait_sleepy(&epi_done[s], ((j - 2) >> 1) & 1))) {
                         pok = false;
                         break;
@@ -421,11 +388,36 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
             const int q = u / NT, u_end = min(u_hi, (q + 1) * NT), j_end = j + (u_end - u);
             const bool whole = u == q * NT && u_end == (q + 1) * NT;
             const int s_row = q * kTmaRows + row;
-            // the segment's query norms and range flag (built by the producer)
-            if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(a_ready, k & 1));
-            const float nq = s_nq[(k & 1) * kTmaRows + row];
-            const bool in_range = s_flag[k & 1] != 0;
-            mbar_arrive(&nq_read[k & 1]);
+            // ---- the segment's query operand: raw rows -> [re_hi, re_lo, im_hi, im_lo] in place
+            // per 16-byte chunk (chunk f is one of the CH chunks of row f / CH; CH consecutive
+            // lanes hold one row), squared norms by row
+            if (ok) ok = __all_sync(0xffffffffu, mbar_wait_bounded(a_full, k & 1));
+            bool rows_in_range = true;
+            {
+                float4 *qv = reinterpret_cast<float4 *>(smem + L::kA);
+                constexpr int QV = L::kACopy / 16;
+#pragma unroll
+                for (int i = 0; i < CH / 2; ++i) {
+                    const int f = tid + kTmaEpi * i;
+                    const float4 x = ok ? qv[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float nqf = fmaf(x.x, x.x, fmaf(x.y, x.y, fmaf(x.z, x.z, x.w * x.w)));
+#pragma unroll
+                    for (int o = 1; o < CH; o <<= 1) nqf += __shfl_xor_sync(0xffffffffu, nqf, o);
+                    if ((f & (CH - 1)) == 0) s_nq[f / CH] = nqf;
+                    rows_in_range = rows_in_range && a.k2 * nqf <= kFactorLimit;
+                    const float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                    const float4 l = make_float4(tf32_hi(x.x - h.x), tf32_hi(x.y - h.y), tf32_hi(x.z - h.z),
+                                                 tf32_hi(x.w - h.w));
+                    qv[f] = h;
+                    qv[QV + f] = l;
+                    qv[2 * QV + f] = make_float4(h.y, -h.x, h.w, -h.z);  // (Im, -Re) pairs
+                    qv[3 * QV + f] = make_float4(l.y, -l.x, l.w, -l.z);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(a_ready);
+            const bool in_range = epi_and(rows_in_range);  // also: every query norm is written
+            const float nq = s_nq[row];
 #pragma unroll
             for (int kk = 0; kk < KB; ++kk) acc1[kk] = acc2[kk] = 0.f;
             const float hq = in_range ? 0.f : -a.k2 * nq;  // unfactored exponent when out of range
@@ -609,9 +601,9 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                         n_parts += o != prev;
                         prev = o;
                     }
-                    if (row == 0) s_flag[2] = atomicAdd(a.counters + q, 1) == n_parts - 1;
+                    if (row == 0) *s_last = atomicAdd(a.counters + q, 1) == n_parts - 1;
                     asm volatile("bar.sync 3, 128;" ::: "memory");
-                    fin = s_flag[2] != 0;
+                    fin = *s_last != 0;
                     if (fin) {
                         __threadfence();
 #pragma unroll
@@ -631,7 +623,7 @@ __global__ void __launch_bounds__(kTmaThreads, (tma_min_blocks<M, KB>()))
                         }
                         if (row == 0) a.counters[q] = 0;  // the workspace is left as it was found
                     }
-                    asm volatile("bar.sync 3, 128;" ::: "memory");  // (s_flag[2] is reused)
+                    asm volatile("bar.sync 3, 128;" ::: "memory");  // (*s_last is reused)
                 }
                 if (fin && s_row < a.N) {
                     const float fq = in_range ? ex2(-a.k2 * nq) : 1.f;  // query factor

@@ -86,3 +86,35 @@ def test_train_and_detect_gradients_match_finite_differences(M, K, P, W, D, N, s
             assert got == pytest.approx(ref, rel=3e-3, abs=1e-5 * scale), (m, k, unit)
             checked += 1
     assert checked >= 8
+
+
+def test_grad_batch_equals_instances_one_at_a_time():
+    """apsm.GradBatch (forward + backward of many instances on parallel streams, optionally one
+    CUDA graph): each instance's loss and gradients equal those of the single-stream run bit for
+    bit, and match the instance-at-a-time autograd path."""
+    M, K, P, W, D, N = 8, 3, 70, 6, 64, 300
+    xs = [synth.make_instance(M, K, P, N, 10.0, instance=900 + i) for i in range(6)]
+    data = [(to_dev(x.rx_pilot), to_dev(x.sym_pilot), to_dev(x.rx_data), to_dev(x.sym_data)) for x in xs]
+    p = apsm.Params(M=M, K=K, window=W, dict_cap=D, sigma=0.6, mu=0.7, eps=0.02, w_L=0.4)
+    rng = np.random.default_rng(3)
+    c0 = to_dev((0.05 * (rng.standard_normal((M, K)) + 1j * rng.standard_normal((M, K)))).astype(np.complex64))
+    one = apsm.GradBatch(p, data, c0, lanes=1)
+    one.run()
+    many = apsm.GradBatch(p, data, c0, lanes=4)
+    many.run()
+    graph = apsm.GradBatch(p, data, c0, lanes=3, graph=True)
+    graph.run()
+    graph.run()
+    torch.cuda.synchronize()
+    for b in (many, graph):
+        assert torch.equal(b.loss, one.loss) and torch.equal(b.dst, one.dst) and torch.equal(b.dclin0, one.dclin0)
+    for i, (rp, sp, rd, sd) in enumerate(data):
+        cg = c0.clone().requires_grad_(True)
+        th = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (p.sigma, p.mu, p.eps, p.w_L)]
+        soft = apsm.train_detect_autograd(p, rp, sp, rd, cg, *th)
+        (soft - sd).abs().pow(2).sum().backward()
+        ref = np.array([float(t.grad) for t in th])
+        got = one.dst[i].double().cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max()), (got, ref)
+        dc = (one.dclin0[i] - cg.grad).abs().max().item()
+        assert dc <= 1e-4 * max(1.0, cg.grad.abs().max().item())
