@@ -71,6 +71,12 @@ def detect_roofline(w, n_entries, seconds, engine="tf32x3"):
     gram = 2 * (2 * w["M"]) * 2 * pairs
     if engine == "ffma":
         res = {"alu": (2 * (4 * w["M"] + 4 * w["K"] + 3) * pairs, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s")}
+    elif engine == "half-tc":
+        # both contractions on the tensor pipe: the Gram (one BF16/FP16 product) and the
+        # coefficient GEMM (3 exponentials x 2K outputs, G as a BF16 hi + lo pair: 2 products);
+        # the FP32 pipe forms the 3 exponent arguments
+        res = {"tensor": (gram + 2 * 2 * 3 * (2 * w["K"]) * pairs, bf16 * 1e12, "TFLOP/s"),
+               "alu": (2 * 3 * pairs, FP32_PEAK_TFLOPS * 1e12, "TFLOP/s")}
     else:
         tensor = ((3 * gram, bf16 * (1.1 / 2.25) * 1e12, "TFLOP/s") if engine == "tf32x3" else
                   (gram, bf16 * 1e12, "TFLOP/s"))
@@ -422,17 +428,19 @@ def run_precision(args):
         q = apsm.Params(**base, dtype=dt)
         s_ = torch.empty((N, K), dtype=torch.complex64, device="cuda")
         h_ = torch.empty((N, K), dtype=torch.uint8, device="cuda")
-        ms = _time_events(lambda: apsm.detect(q, st, rd, soft=s_, hard=h_), args.steps, args.warmup)
+        dw = apsm.detect_workspace(q, N)
+        ms = _time_events(lambda: apsm.detect(q, st, rd, soft=s_, hard=h_, workspace=dw), args.steps, args.warmup)
         soft[dt] = s_
         pairs = N * D
         # FP32 has no tensor-core kernel above 32 antennas (its TF32 hi/lo operands would not fit
-        # shared memory), so it runs on the FMA engine here; BF16/FP16 take one tensor product.
-        engine = "half" if dt != "fp32" else ("ffma" if M > 32 else "tf32x3")
+        # shared memory), so it runs on the FMA engine here; BF16/FP16 form the Gram and the
+        # coefficient sums on the tensor cores.
+        engine = "half-tc" if dt != "fp32" else ("ffma" if M > 32 else "tf32x3")
         out[dt] = {"value": N / (ms / 1e3), "ms": ms, "pairs_per_s": pairs / (ms / 1e3), "engine": engine,
                    "roofline": detect_roofline(dict(M=M, K=K, N=N), D, ms / 1e3, engine),
                    "ser": float((h_.cpu().numpy() != x.idx_data).mean())}
     out["value"], out["ms_per_step"], out["dtype"] = out["bf16"]["value"], out["bf16"]["ms"], "bf16"
-    out["roofline"] = {"kernel": "detect_tc_kernel<64,16,half> (BF16)", **out["bf16"]["roofline"],
+    out["roofline"] = {"kernel": "detect_tcc_kernel<64,16> (BF16 Gram and coefficient GEMM)", **out["bf16"]["roofline"],
                        "traffic": None}
     sample = np.random.default_rng(0).choice(N, 512, replace=False)
     ent, gam = st.entries()

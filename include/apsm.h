@@ -253,11 +253,15 @@ apsm_status apsm_detect(const apsm_params *p, const apsm_state *st, const float 
                         uint8_t *hard, void *stream);
 
 /*
- * Detection balanced over the SMs (the same results as apsm_detect up to FP32 rounding order;
- * Sec. III-B detection).  FP32 detection with 4, 8 or 16 antennas and an even user count in
+ * Detection with a workspace (the same results as apsm_detect up to rounding order; Sec. III-B
+ * detection).  FP32 detection with 4, 8 or 16 antennas and an even user count in
  * {2, 4, 6, 8, 12, 16} splits its (query tile, dictionary tile) work evenly over a persistent
  * grid; a query tile split between CTAs leaves each part's sums in the workspace and the CTA
  * that brings its last part adds the parts in a fixed order (results do not depend on timing).
+ * BF16/FP16 detection with 16, 32 or 64 antennas packs the dictionary's operands into the
+ * workspace once per call and forms the coefficient sums on the tensor cores too (see
+ * APSM_OPT_HALF_TC_COEF): the exponentials rounded to BF16 against the coefficients as a BF16
+ * hi + lo pair, accumulated in FP32.
  *   apsm_detect_workspace_bytes: bytes for N data vectors on the current device; 0 where the
  *     balanced form does not apply (apsm_detect_ws then runs apsm_detect).
  *   workspace  device, 256-byte aligned, at least that many bytes, ZERO-FILLED before its first
@@ -418,9 +422,18 @@ apsm_status apsm_check_wait_timeout(const apsm_state *st, void *stream);
  *                         count in {2, 4, 6, 8, 12, 16} stages every operand by TMA (entry rows
  *                         as stored, the real split's rotation on the query side); 0: the
  *                         tensor-core form that converts entry rows in shared memory
+ *   APSM_OPT_HALF_TC_COEF 1 (default): BF16/FP16 detection with 16, 32 or 64 antennas forms the
+ *                         coefficient sums on the tensor cores too (the exponentials rounded to
+ *                         BF16, the coefficients as a BF16 hi + lo pair, FP32 accumulation);
+ *                         0: coefficient sums in FP32 on the FMA pipe
  * Returns APSM_ERR_INVALID_ARG for an unknown option or a value out of range.
  */
-typedef enum { APSM_OPT_TRAIN_CHUNK = 0, APSM_OPT_TRAIN_TRACK = 1, APSM_OPT_DETECT_TMA = 2 } apsm_option;
+typedef enum {
+    APSM_OPT_TRAIN_CHUNK = 0,
+    APSM_OPT_TRAIN_TRACK = 1,
+    APSM_OPT_DETECT_TMA = 2,
+    APSM_OPT_HALF_TC_COEF = 3
+} apsm_option;
 apsm_status apsm_set_option(int32_t option, int32_t value);
 
 /* Static description of a status code. */

@@ -23,7 +23,7 @@ APSM_FP32, APSM_BF16, APSM_FP16 = 0, 1, 2
 _DTYPES = {"fp32": APSM_FP32, "bf16": APSM_BF16, "fp16": APSM_FP16}
 APSM_Q_UNIFORM, APSM_Q_VIOLATED = 0, 1
 _WEIGHTS = {"uniform": APSM_Q_UNIFORM, "violated": APSM_Q_VIOLATED}
-_OPTIONS = {"train_chunk": 0, "train_track": 1, "detect_tma": 2}
+_OPTIONS = {"train_chunk": 0, "train_track": 1, "detect_tma": 2, "half_tc_coef": 3}
 
 
 class ApsmError(RuntimeError):
@@ -283,7 +283,8 @@ def linear_init(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, nois
 
 
 def set_option(name: str, value: int):
-    """apsm_set_option: process-wide launch options ("train_chunk", "train_track", "detect_tma")."""
+    """apsm_set_option: process-wide launch options ("train_chunk", "train_track", "detect_tma",
+    "half_tc_coef")."""
     _check(load_library().apsm_set_option(_OPTIONS[name], int(value)), "apsm_set_option")
 
 

@@ -13,6 +13,7 @@
 #include "detect_bwd.cuh"
 #include "detect_f32.cuh"
 #include "detect_tc.cuh"
+#include "detect_tcc.cuh"
 #include "detect_tma.cuh"
 #include "train_f32.cuh"
 
@@ -24,6 +25,8 @@ DetectLauncher detect_f32_launcher(int M, int K);  // detect_f32_m*.cu
 DetectBwdLauncher detect_bwd_launcher(int M, int K);  // detect_f32_m*.cu
 TcLauncher detect_tc_launcher(int M, int K, int prec);  // detect_tc_m*.cu
 TmaLauncher detect_tma_launcher(int M, int K);         // detect_tma_m*.cu
+TccLauncher detect_tcc_launcher(int M, int K);         // detect_tc_m*.cu (BF16/FP16, coefficient sums on tcgen05)
+size_t detect_tcc_workspace(int M, int K, int D);
 using ChunkLauncher = cudaError_t (*)(const ChunkArgs &, int, cudaStream_t);
 ChunkLauncher chunk_launcher(int S, int WP, bool ext);  // train_chunk.cu
 int padded_window(int W);                           // train_chunk.cu
@@ -107,6 +110,7 @@ constexpr int kMaxSmemBytes = 227 * 1024;  // opt-in shared memory per CTA
 std::atomic<int> g_opt_train_chunk{64};  // pilots per training chunk
 std::atomic<int> g_opt_train_track{1};   // next-chunk tracking form (1) or sequential form (0)
 std::atomic<int> g_opt_detect_tma{1};     // TMA-staged FP32 detection where it applies (1) or not (0)
+std::atomic<int> g_opt_half_tc_coef{1};   // BF16/FP16: coefficient sums on the tensor cores (1) or FP32 pipe (0)
 
 inline apsm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? APSM_OK : APSM_ERR_CUDA; }
 
@@ -640,6 +644,9 @@ apsm_status apsm_detect_ws(const apsm_params *p, const apsm_state *st, const flo
     if (p->dtype != APSM_FP32 || !force_ffma) {
         const int prec = p->dtype == APSM_FP32 ? kTF32x3 : kHalf;
         TcLauncher tc = detect_tc_launcher(p->M, p->K, prec);
+        // BF16/FP16 with a workspace: the coefficient sums on the tensor cores too
+        TccLauncher tcc = (prec == kHalf && workspace && g_opt_half_tc_coef.load()) ? detect_tcc_launcher(p->M, p->K)
+                                                                                     : nullptr;
         TmaLauncher tma = (p->dtype == APSM_FP32 && g_opt_detect_tma.load()) ? detect_tma_launcher(p->M, p->K) : nullptr;
         if (tc || tma) {
             TcArgs ta{};
@@ -667,7 +674,12 @@ apsm_status apsm_detect_ws(const apsm_params *p, const apsm_state *st, const flo
                 return APSM_ERR_CUDA;
             const int r = tma ? tma(ta, workspace, workspace_bytes, sms, strm) : 1;
             if (r < 0) return APSM_ERR_CUDA;
-            if (r > 0 && (!tc || tc(ta, strm) != cudaSuccess)) return tc ? APSM_ERR_CUDA : APSM_ERR_UNSUPPORTED;
+            if (r > 0 && tcc) {
+                if (tcc(ta, workspace, workspace_bytes, strm) != cudaSuccess) return APSM_ERR_CUDA;
+                g_launches++;  // (the packing launch)
+            } else if (r > 0 && (!tc || tc(ta, strm) != cudaSuccess)) {
+                return tc ? APSM_ERR_CUDA : APSM_ERR_UNSUPPORTED;
+            }
             g_launches++;
             return qam_pass ? qam_labels(soft, hard, N, p, strm) : APSM_OK;
         }
@@ -710,7 +722,12 @@ apsm_status apsm_detect_workspace_bytes(const apsm_params *p, int32_t N, size_t 
     apsm_status s = check_params(p);
     if (s != APSM_OK) return s;
     if (N < 0) return APSM_ERR_INVALID_ARG;
-    if (N == 0 || p->dtype != APSM_FP32 || !detect_tma_launcher(p->M, p->K)) return APSM_OK;
+    if (N == 0) return APSM_OK;
+    if (p->dtype != APSM_FP32) {  // the packed operands of the reduced-precision form
+        if (g_opt_half_tc_coef.load()) *bytes = detect_tcc_workspace(p->M, p->K, p->dict_cap);
+        return APSM_OK;
+    }
+    if (!detect_tma_launcher(p->M, p->K)) return APSM_OK;
     if ((s = check_device()) != APSM_OK) return s;
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, current_device()) != cudaSuccess)
@@ -818,6 +835,10 @@ apsm_status apsm_set_option(int32_t option, int32_t value) {
         case APSM_OPT_DETECT_TMA:
             if (value != 0 && value != 1) return APSM_ERR_INVALID_ARG;
             g_opt_detect_tma.store(value);
+            return APSM_OK;
+        case APSM_OPT_HALF_TC_COEF:
+            if (value != 0 && value != 1) return APSM_ERR_INVALID_ARG;
+            g_opt_half_tc_coef.store(value);
             return APSM_OK;
         default: return APSM_ERR_INVALID_ARG;
     }

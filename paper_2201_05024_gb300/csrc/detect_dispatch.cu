@@ -6,6 +6,7 @@
 #include "detect_tc.cuh"
 #include "detect_tc_batch.cuh"
 #include "detect_tma.cuh"
+#include "detect_tcc.cuh"
 
 namespace apsm {
 
@@ -29,6 +30,13 @@ TcLauncher detect_tc_launcher_m8(int kb, int prec);
 TcLauncher detect_tc_launcher_m16(int kb, int prec);
 TcLauncher detect_tc_launcher_m32(int kb, int prec);
 TcLauncher detect_tc_launcher_m64(int kb, int prec);
+
+TccLauncher detect_tcc_launcher_m16(int kb);
+TccLauncher detect_tcc_launcher_m32(int kb);
+TccLauncher detect_tcc_launcher_m64(int kb);
+size_t detect_tcc_workspace_m16(int kb, int D);
+size_t detect_tcc_workspace_m32(int kb, int D);
+size_t detect_tcc_workspace_m64(int kb, int D);
 
 TcBatchLauncher detect_tc_batch_launcher_m2(int kb, int *ctas_per_sm);
 TcBatchLauncher detect_tc_batch_launcher_m4(int kb, int *ctas_per_sm);
@@ -88,6 +96,28 @@ TcLauncher detect_tc_launcher(int M, int K, int prec) {
         case 32: return detect_tc_launcher_m32(kb, prec);
         case 64: return detect_tc_launcher_m64(kb, prec);
         default: return nullptr;
+    }
+}
+
+// BF16/FP16 detection with the coefficient sums on the tensor cores; nullptr if none.
+TccLauncher detect_tcc_launcher(int M, int K) {
+    const int kb = tc_user_bucket(K);
+    if (!kb) return nullptr;
+    switch (M) {
+        case 16: return detect_tcc_launcher_m16(kb);
+        case 32: return detect_tcc_launcher_m32(kb);
+        case 64: return detect_tcc_launcher_m64(kb);
+        default: return nullptr;
+    }
+}
+size_t detect_tcc_workspace(int M, int K, int D) {
+    const int kb = tc_user_bucket(K);
+    if (!kb) return 0;
+    switch (M) {
+        case 16: return detect_tcc_workspace_m16(kb, D);
+        case 32: return detect_tcc_workspace_m32(kb, D);
+        case 64: return detect_tcc_workspace_m64(kb, D);
+        default: return 0;
     }
 }
 

@@ -230,12 +230,12 @@ constexpr bool tc_core_rows() {
 // halves), i.e. eight consecutive B rows, so their 16-byte stores hit all 32 banks once.
 // The first PF tasks' global loads can be issued ahead (prefetch), before the converters wait
 // for the stage they will write, so that their L2 latency overlaps the wait.
-template <int M, int kPrec>
+template <int M, int kPrec, int kMaxPf = 8>
 struct EntryRows {
     using Sh = TcShape<M, kPrec>;
     // (instantiated for every M; used only where tc_core_rows<M, kPrec>() holds, so that P >= 1)
     static constexpr int C = Sh::kCoreK, P = M / C > 0 ? M / C : 1, V = C / 2;  // float4 loads per task
-    static constexpr int PF = P * V <= 8 ? P : 8 / V;                          // prefetched tasks (<= 8 float4)
+    static constexpr int PF = P * V <= kMaxPf ? P : kMaxPf / V;                // prefetched tasks (<= kMaxPf float4)
     float4 pf[PF][V];
 
     // task i of thread ct: 64 entries x 2 halves x P pieces over 128 threads

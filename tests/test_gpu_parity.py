@@ -224,8 +224,15 @@ HALF_CASES = [
 TOL_HALF = 2e-2
 
 
+@pytest.fixture(params=["tc-coef", "fma-coef"])
+def half_coef(request):
+    """Where the reduced-precision form forms its coefficient sums: on the tensor cores (with a
+    workspace, for 16, 32 and 64 antennas) or on the FP32 FMA pipe (no workspace)."""
+    yield request.param
+
+
 @pytest.mark.parametrize("M,K,D,N,dtype", HALF_CASES)
-def test_detect_reduced_precision_matches_oracle(M, K, D, N, dtype):
+def test_detect_reduced_precision_matches_oracle(M, K, D, N, dtype, half_coef):
     """BF16 / FP16 Gram on the tensor cores with FP32 accumulation, exponentials and sums:
     soft outputs within 2e-2 (scaled) of the FP64 oracle, decisions identical away from a
     boundary; the error against the FP32 path is reported by the benchmark."""
@@ -234,7 +241,8 @@ def test_detect_reduced_precision_matches_oracle(M, K, D, N, dtype):
     op = oracle.Params(M=M, K=K, W=1, D=D, sigma=0.5, w_L=0.5)
     gp = gpu_params(op, dtype=dtype)
     st = load_state(gp, ent, gam, clin)
-    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data))
+    ws = apsm.detect_workspace(gp, N) if half_coef == "tc-coef" else None
+    soft, hard = apsm.detect(gp, st, to_dev(inst.rx_data), workspace=ws)
     ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), inst.rx_data)
     err = assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what=dtype)
     assert err > 1e-6  # really the reduced-precision path
@@ -292,7 +300,7 @@ def _unguarded_bf16_detect(M, K, ent, gam, clin, rx, sigma, w_L):
 @pytest.mark.parametrize("M,K", [(16, 6), (64, 5)])
 @pytest.mark.parametrize("case", ["offset", "mixed_entries", "mixed_queries"])
 @pytest.mark.parametrize("dtype", ["bf16", "fp16"])
-def test_detect_reduced_precision_unnormalised_inputs(case, M, K, dtype):
+def test_detect_reduced_precision_unnormalised_inputs(case, M, K, dtype, half_coef):
     """BF16/FP16 Gram on inputs outside the gain-controlled range: the pairs where the norm
     expansion cancels (smallest distance below 2^-4 k2 (||r||^2 + ||r_t||^2)) are recomputed by
     direct differences in FP32, so the result stays within 2e-2 of the FP64 oracle."""
@@ -300,7 +308,8 @@ def test_detect_reduced_precision_unnormalised_inputs(case, M, K, dtype):
     op = oracle.Params(M=M, K=K, W=1, D=ent.shape[0], sigma=sigma, w_L=0.5)
     gp = gpu_params(op, dtype=dtype)
     st = load_state(gp, ent, gam, clin)
-    soft, hard = apsm.detect(gp, st, to_dev(rx))
+    ws = apsm.detect_workspace(gp, rx.shape[0]) if half_coef == "tc-coef" else None
+    soft, hard = apsm.detect(gp, st, to_dev(rx), workspace=ws)
     ref = oracle.detect(op, oracle_state_fp32(M, ent, gam, clin), rx)
     assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what=f"{dtype} {case}")
     assert_hard_match(hard.cpu().numpy(), ref, tol=TOL_HALF)
@@ -324,12 +333,13 @@ def test_direct_difference_fallback_regression():
     assert_soft_close(soft.cpu().numpy(), ref, tol=TOL_HALF, what="guarded bf16")
 
 
-def test_detect_empty_dictionary_is_linear_filter():
+@pytest.mark.parametrize("dtype", ["fp32", "bf16"])
+def test_detect_empty_dictionary_is_linear_filter(dtype):
     M, K, N = 16, 6, 200
     ent, gam, clin = synth.random_state(M, K, 0)
     inst = synth.make_instance(M, K, 4, N, 10.0, instance=3)
     op = oracle.Params(M=M, K=K, W=1, D=8)
-    gp = gpu_params(op)
+    gp = gpu_params(op, dtype=dtype)
     st = load_state(gp, ent, gam, clin)
     soft, _ = apsm.detect(gp, st, to_dev(inst.rx_data))
     ref = 0.5 * (inst.rx_data.astype(np.complex128) @ np.conj(clin.astype(np.complex128)))
