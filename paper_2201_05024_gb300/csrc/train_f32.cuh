@@ -744,17 +744,18 @@ __global__ void __launch_bounds__(32 * S, 1) train_chunk_kernel(const ChunkArgs 
     }
 
     // ---- new dictionary entries of this chunk (slot (tb + t) % D), their norms, bookkeeping --
+    // (spread over the K user CTAs, which all hold the chunk's pilots)
+    for (int i = k * RS + u; i < Tc * M; i += K * RS) {
+        const int t = t0 + i / M, mm = i % M;
+        a.dict[(size_t)((tb + t) % D) * M + mm] = s_pil[(t - pa0) * M + mm];
+    }
+    for (int i = k * RS + u; i < Tc; i += K * RS) {
+        const float2 *rv = s_pil + (t0 + i - pa0) * M;
+        float nrm = 0.f;
+        for (int mm = 0; mm < M; ++mm) nrm = fmaf(rv[mm].x, rv[mm].x, fmaf(rv[mm].y, rv[mm].y, nrm));
+        a.dict_norm[(tb + t0 + i) % D] = nrm;
+    }
     if (k == 0) {
-        for (int i = u; i < Tc * M; i += RS) {
-            const int t = t0 + i / M, mm = i % M;
-            a.dict[(size_t)((tb + t) % D) * M + mm] = s_pil[(t - pa0) * M + mm];
-        }
-        for (int i = u; i < Tc; i += RS) {
-            const float2 *rv = s_pil + (t0 + i - pa0) * M;
-            float nrm = 0.f;
-            for (int mm = 0; mm < M; ++mm) nrm = fmaf(rv[mm].x, rv[mm].x, fmaf(rv[mm].y, rv[mm].y, nrm));
-            a.dict_norm[(tb + t0 + i) % D] = nrm;
-        }
         if (a.chunk == g.n_chunks - 1 && u == 0) {
             const int total = tb + g.P;  // vectors trained on since the state was emptied
             a.meta[0] = min(total, D);
