@@ -465,9 +465,10 @@ def run_precision(args):
 def run_grad(args):
     """Differentiation form: 256 instances of 16 antennas, 6 users, 256 pilots (W = 8, D = 256),
     4096 data vectors each; loss = sum |soft - transmitted symbol|^2; forward (train + detect) and
-    backward (loss gradient, detect adjoint, checkpointed training adjoint) of all instances as
-    one CUDA graph over 16 streams (apsm.GradBatch), against the forward alone batched the same
-    way and against the instance-at-a-time autograd path on a sample."""
+    backward (loss gradient, detect adjoint, training adjoint) of all instances as one CUDA graph
+    (apsm.GradBatch: per-instance work over 64 streams, the training adjoints of all instances in
+    one batched launch), against the forward alone batched the same way and against the
+    instance-at-a-time autograd path on a sample."""
     import torch
     from paper_2201_05024_gb300 import apsm, build, synth
     torch.cuda.set_device(0)
@@ -479,8 +480,8 @@ def run_grad(args):
         x = synth.make_instance(M, K, P, N, 10.0, instance=20000 + i)
         data.append(tuple(torch.from_numpy(a).cuda() for a in (x.rx_pilot, x.sym_pilot, x.rx_data, x.sym_data)))
     c0 = torch.zeros((M, K), dtype=torch.complex64, device="cuda")
-    fb = apsm.GradBatch(p, data, c0, lanes=16, graph=True)
-    fo = apsm.GradBatch(p, data, c0, lanes=16, graph=True, backward=False)
+    fb = apsm.GradBatch(p, data, c0, lanes=64, graph=True)
+    fo = apsm.GradBatch(p, data, c0, lanes=64, graph=True, backward=False)
     ms = _time_events(fb.run, args.steps, args.warmup)
     fwd = _time_events(fo.run, args.steps, args.warmup)
     loss, dscal, dclin0 = fb.grads()
@@ -501,8 +502,8 @@ def run_grad(args):
                       "serial_autograd_ms_extrapolated": ms_serial, "higher_is_better": True, "scaling": "weak",
                       "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"{n_inst} instances x (M={M}, K={K}, P={P}, W={W}, D={D}, N={N}); "
-                                             "gradients wrt sigma, mu, eps, w_L, c_0; checkpoint every 32 pilots; "
-                                             "one CUDA graph over 16 streams"},
+                                             "gradients wrt sigma, mu, eps, w_L, c_0; "
+                                             "one CUDA graph over 64 streams, batched training adjoint"},
                       "loss": float(loss), "grad_sample": [float(v) for v in dscal]}))
 
 

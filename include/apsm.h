@@ -313,7 +313,9 @@ apsm_status apsm_train_backward_workspace_bytes(const apsm_params *p, int32_t P,
  *   dclin0 [M][K] complex = dL/d(initial linear filter c_0).
  * The derivative of Eq. beta is taken piecewise: -1/kappa_jj with respect to the residual and
  * -+1/kappa_jj with respect to eps outside the slab, 0 inside it (and at |e| = eps exactly).
- * The forward recurrence is re-run from checkpoints taken every 32 pilots (64 steps).
+ * The forward recurrence is run once, carrying the window's predictions from step to step, and
+ * its per-step terms are kept in the workspace; the reverse sweep forms a centre's adjoint when
+ * the centre enters the window, so both passes cost O(W^2 + P) per step.
  *   rx_pilot, sym_pilot, P, clin0: as given to apsm_train (clin0 may be NULL for zero), P >= 1
  *   workspace: apsm_train_backward_workspace_bytes(p, P) bytes, 256-byte aligned
  * All pointers DEVICE.  Deterministic.  Errors as for apsm_train.
@@ -321,6 +323,24 @@ apsm_status apsm_train_backward_workspace_bytes(const apsm_params *p, int32_t P,
 apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
                                 const float *clin0, const float *dgamma, const float *dclin, float *dscalars,
                                 float *dclin0, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Bytes of device workspace apsm_train_backward_batched needs for n instances of P pilots. */
+apsm_status apsm_train_backward_batched_workspace_bytes(const apsm_params *p, int32_t P, int32_t n, size_t *bytes);
+
+/*
+ * apsm_train_backward for n independent instances with the same parameters and pilot count, in
+ * one launch per kernel (users x instances thread blocks).  Instance i's arrays follow instance
+ * i-1's, each in the layout of apsm_train_backward:
+ *   rx_pilot [n][P][M], sym_pilot [n][P][K] complex; clin0 [n][M][K] complex or NULL (zero);
+ *   dgamma [n][A][2][K]; dclin [n][M][K] complex; dscalars [n][4] out; dclin0 [n][M][K] out.
+ * Each instance's results equal those of its own apsm_train_backward call bit for bit.
+ *   n: 1..65535; workspace: apsm_train_backward_batched_workspace_bytes(p, P, n) bytes, 256-byte aligned.
+ * All pointers DEVICE.  Errors as for apsm_train_backward.
+ */
+apsm_status apsm_train_backward_batched(const apsm_params *p, int32_t n, const float *rx_pilot, const float *sym_pilot,
+                                        int32_t P, const float *clin0, const float *dgamma, const float *dclin,
+                                        float *dscalars, float *dclin0, void *workspace, size_t workspace_bytes,
+                                        void *stream);
 
 /*
  * Load a given filter into a state (detection with fixed, externally trained coefficients):

@@ -85,6 +85,8 @@ def load_library(path: str | None = None):
         i32 = ctypes.c_int32
         lib.apsm_train_backward_workspace_bytes.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_train_backward.argtypes = [P, vp, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.apsm_train_backward_batched_workspace_bytes.argtypes = [P, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+        lib.apsm_train_backward_batched.argtypes = [P, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.apsm_tune_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
         lib.apsm_tune_clear.argtypes = []
         lib.apsm_batch_workspace_bytes.argtypes = [ctypes.POINTER(_CInstance), i32, ctypes.POINTER(ctypes.c_size_t)]
@@ -101,6 +103,7 @@ def load_library(path: str | None = None):
                   "apsm_read_status", "apsm_state_set", "apsm_detect_backward_workspace_bytes",
                   "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
                   "apsm_train_backward_workspace_bytes", "apsm_train_backward",
+                  "apsm_train_backward_batched_workspace_bytes", "apsm_train_backward_batched",
                   "apsm_batch_launch", "apsm_batch_destroy", "apsm_check_wait_timeout",
                   "apsm_train_continue_workspace_bytes", "apsm_train_continue", "apsm_linear_init",
                   "apsm_set_option", "apsm_batch_workspace_bytes", "apsm_batch_launch_detect",
@@ -422,6 +425,38 @@ def train_backward(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, d
     return dscal, dclin0
 
 
+def train_backward_batched(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor, dgamma: torch.Tensor,
+                           dclin: torch.Tensor, *, clin0: torch.Tensor | None = None,
+                           workspace: torch.Tensor | None = None, dscalars: torch.Tensor | None = None,
+                           dclin0: torch.Tensor | None = None):
+    """apsm_train_backward_batched: train_backward of n instances in one launch per kernel.
+    rx_pilot [n][P][M], sym_pilot [n][P][K], dgamma [n][A][2][K], dclin [n][M][K], clin0 [n][M][K] or
+    None; returns (dscalars [n][4], dclin0 [n][M][K]) (written into the given tensors if passed)."""
+    lib = load_library()
+    n, P = int(rx_pilot.shape[0]), int(rx_pilot.shape[1])
+    _dev(rx_pilot, torch.complex64, (n, P, p.M), "rx_pilot")
+    _dev(sym_pilot, torch.complex64, (n, P, p.K), "sym_pilot")
+    _dev(dgamma, torch.float32, (n, dict_alloc(p), 2, p.K), "dgamma")
+    _dev(dclin, torch.complex64, (n, p.M, p.K), "dclin")
+    if clin0 is not None:
+        _dev(clin0, torch.complex64, (n, p.M, p.K), "clin0")
+    nb = ctypes.c_size_t()
+    _check(lib.apsm_train_backward_batched_workspace_bytes(ctypes.byref(p.c()), P, n, ctypes.byref(nb)),
+           "apsm_train_backward_batched_workspace_bytes")
+    if workspace is None:
+        workspace = torch.empty((max(nb.value, 1),), dtype=torch.uint8, device=rx_pilot.device)
+    if dscalars is None:
+        dscalars = torch.empty((n, 4), dtype=torch.float32, device=rx_pilot.device)
+    if dclin0 is None:
+        dclin0 = torch.empty((n, p.M, p.K), dtype=torch.complex64, device=rx_pilot.device)
+    _dev(dscalars, torch.float32, (n, 4), "dscalars")
+    _dev(dclin0, torch.complex64, (n, p.M, p.K), "dclin0")
+    _check(lib.apsm_train_backward_batched(ctypes.byref(p.c()), n, _ptr(rx_pilot), _ptr(sym_pilot), P, _ptr(clin0),
+                                           _ptr(dgamma), _ptr(dclin), _ptr(dscalars), _ptr(dclin0), _ptr(workspace),
+                                           workspace.numel(), _stream()), "apsm_train_backward_batched")
+    return dscalars, dclin0
+
+
 class TrainDetectFunction(torch.autograd.Function):
     """soft = detect(train(pilots; c_0, sigma, mu, eps, w_L), rx): the APSM recurrence unrolled over
     the pilots and the detection of the data vectors, differentiable with respect to the initial
@@ -459,14 +494,17 @@ class GradBatch:
     dsoft = 2 (soft - target), apsm_detect_backward, apsm_train_backward) of many independent
     instances with the same parameters, on `lanes` CUDA streams with no host synchronisation
     between instances; with graph=True the whole pass is captured once and replayed as one CUDA
-    graph.  Every buffer is allocated here, once.  Per-instance results stay on the device:
+    graph.  When every instance has the same pilot count, the training adjoints run as
+    apsm_train_backward_batched calls over chunks of `chunk` instances (default: all of them), each
+    on its own stream as soon as its instances' detection adjoints are done, so that they overlap
+    the per-instance work of the next chunks.  Every buffer is allocated here, once.  Per-instance results stay on the device:
     loss [n] (sum |soft - target|^2), dscalars [n][4] (d sigma, d mu, d eps, d w_L) and
     dclin0 [n][M][K]; grads() sums them over the instances in instance order.  Each instance's
     results equal those of the same calls made one instance at a time, bit for bit.
     backward=False: the forward pass alone (soft outputs in buf[i]["soft"])."""
 
     def __init__(self, p: Params, instances, clin0: torch.Tensor, *, lanes: int = 16, graph: bool = False,
-                 backward: bool = True):
+                 backward: bool = True, chunk: int | None = None):
         lib = load_library()
         self.p, self.lanes, self.backward = p, max(1, int(lanes)), backward
         self.inst = [tuple(t.contiguous() for t in x) for x in instances]  # (rx_pilot, sym_pilot, rx, target)
@@ -475,7 +513,23 @@ class GradBatch:
         _dev(clin0, torch.complex64, (p.M, p.K), "clin0")
         self.clin0 = clin0
         self.states, self.buf = [], []
-        for rp, sp, rd, sd in self.inst:
+        Ps = {int(x[0].shape[0]) for x in self.inst}
+        self.batched = backward and len(Ps) == 1
+        A = dict_alloc(p)
+        self.dgamma = torch.empty((n, A, 2, p.K), dtype=torch.float32, device=dev)
+        self.dclin = torch.empty((n, p.M, p.K), dtype=torch.complex64, device=dev)
+        self.dsd = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        if self.batched:
+            P0 = Ps.pop()
+            nb_bb = ctypes.c_size_t()
+            _check(lib.apsm_train_backward_batched_workspace_bytes(ctypes.byref(p.c()), P0, n, ctypes.byref(nb_bb)),
+                   "apsm_train_backward_batched_workspace_bytes")
+            self.ws_bb = torch.empty((max(nb_bb.value, 1),), dtype=torch.uint8, device=dev)
+            self.ws_per = nb_bb.value // n  # bytes per instance (a multiple of 256)
+            self.rxp_all = torch.empty((n, P0, p.M), dtype=torch.complex64, device=dev)
+            self.symp_all = torch.empty((n, P0, p.K), dtype=torch.complex64, device=dev)
+            self.clin0_all = torch.empty((n, p.M, p.K), dtype=torch.complex64, device=dev)
+        for i, (rp, sp, rd, sd) in enumerate(self.inst):
             P, N = int(rp.shape[0]), int(rd.shape[0])
             nb_t, nb_d, nb_b = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
             _check(lib.apsm_train_workspace_bytes(ctypes.byref(p.c()), P, ctypes.byref(nb_t)), "apsm_train_workspace_bytes")
@@ -488,15 +542,17 @@ class GradBatch:
             self.buf.append(dict(
                 ws_t=torch.empty((max(nb_t.value, 1),), dtype=torch.uint8, device=dev),
                 ws_d=torch.empty((max(nb_d.value, 1),), dtype=torch.uint8, device=dev),
-                ws_b=torch.empty((max(nb_b.value, 1),), dtype=torch.uint8, device=dev),
+                ws_b=None if self.batched else torch.empty((max(nb_b.value, 1),), dtype=torch.uint8, device=dev),
                 soft=torch.empty((N, p.K), dtype=torch.complex64, device=dev),
                 dsoft=torch.empty((N, p.K), dtype=torch.complex64, device=dev),
-                dgamma=torch.empty_like(st.gamma), dclin=torch.empty_like(st.clin),
-                dsd=torch.empty((2,), dtype=torch.float32, device=dev)))
+                dgamma=self.dgamma[i], dclin=self.dclin[i], dsd=self.dsd[i]))
         self.loss = torch.zeros((n,), dtype=torch.float32, device=dev)
         self.dst = torch.zeros((n, 4), dtype=torch.float32, device=dev)
         self.dclin0 = torch.zeros((n, p.M, p.K), dtype=torch.complex64, device=dev)
         self.streams = [torch.cuda.Stream(device=dev) for _ in range(self.lanes)]
+        cs = max(1, int(chunk)) if chunk else n
+        self.chunks = [(c, min(n, c + cs)) for c in range(0, n, cs)] if self.batched else []
+        self.bstreams = [torch.cuda.Stream(device=dev) for _ in self.chunks]
         self.graph = None
         if graph:
             self._run()                                  # warm-up outside the capture
@@ -523,6 +579,8 @@ class GradBatch:
         _check(lib.apsm_detect_backward(ctypes.byref(p.c()), ctypes.byref(c), _ptr(rd), N, _ptr(b["dsoft"]),
                                         _ptr(b["dgamma"]), _ptr(b["dclin"]), _ptr(b["dsd"]), _ptr(b["ws_d"]),
                                         b["ws_d"].numel(), strm), "apsm_detect_backward")
+        if self.batched:
+            return
         _check(lib.apsm_train_backward(ctypes.byref(p.c()), _ptr(rp), _ptr(sp), P, _ptr(self.clin0),
                                        _ptr(b["dgamma"]), _ptr(b["dclin"]), _ptr(self.dst[i]), _ptr(self.dclin0[i]),
                                        _ptr(b["ws_b"]), b["ws_b"].numel(), strm), "apsm_train_backward")
@@ -530,14 +588,36 @@ class GradBatch:
         self.dst[i, 0] += b["dsd"][0]
         self.dst[i, 3] += b["dsd"][1]
 
+    def _chunk_backward(self, lo, hi):
+        """Training adjoints of instances lo..hi-1 in one batched call (on the current stream)."""
+        sl = slice(lo, hi)
+        torch.stack([x[0] for x in self.inst[sl]], out=self.rxp_all[sl])
+        torch.stack([x[1] for x in self.inst[sl]], out=self.symp_all[sl])
+        self.clin0_all[sl].copy_(self.clin0.expand_as(self.clin0_all[sl]))
+        ws = self.ws_bb[lo * self.ws_per:hi * self.ws_per]
+        train_backward_batched(self.p, self.rxp_all[sl], self.symp_all[sl], self.dgamma[sl], self.dclin[sl],
+                               clin0=self.clin0_all[sl], workspace=ws, dscalars=self.dst[sl], dclin0=self.dclin0[sl])
+        self.dst[sl, 0] += self.dsd[sl, 0]  # sigma and w_L also enter through the detection
+        self.dst[sl, 3] += self.dsd[sl, 1]
+
     def _run(self):
         main = torch.cuda.current_stream()
-        for s in self.streams:
+        for s in self.streams + self.bstreams:
             s.wait_stream(main)
-        for i in range(len(self.inst)):
-            with torch.cuda.stream(self.streams[i % self.lanes]):
-                self._instance(i)
-        for s in self.streams:
+        if self.batched:
+            for (lo, hi), bs in zip(self.chunks, self.bstreams):
+                for i in range(lo, hi):
+                    with torch.cuda.stream(self.streams[i % self.lanes]):
+                        self._instance(i)
+                for i in range(lo, hi):
+                    bs.wait_stream(self.streams[i % self.lanes])
+                with torch.cuda.stream(bs):
+                    self._chunk_backward(lo, hi)
+        else:
+            for i in range(len(self.inst)):
+                with torch.cuda.stream(self.streams[i % self.lanes]):
+                    self._instance(i)
+        for s in self.streams + self.bstreams:
             main.wait_stream(s)
 
     def run(self):

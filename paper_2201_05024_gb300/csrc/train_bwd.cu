@@ -15,12 +15,21 @@
 //   gbar_i += ybar_j w_G kappa_G(x_i, x_j) for every alive centre i.
 // Inside the slab the derivative is taken as 0 (also at |e| = eps exactly).
 //
-// Checkpointing: a first forward pass stores (w, every gamma) at the start of every segment of
-// 32 pilots (64 steps); the reverse sweep restores each segment, re-runs its forward recording a
-// per-step tape (beta, branch, kappa, <w, x_j>, gauss_j, its sigma weight), then walks it back.
-// Kernel values between samples come from tables built once per call.  One CTA of 8 warps per
-// user: a warp per window slot for the inner products, a thread per centre for the state
-// adjoint's update, a thread per slot for the scalar terms (summed in slot order at the end).
+// Cost per step O(W^2 + S) instead of O(W S):
+//  * forward: the predictions of the window samples are carried from step to step (the W
+//    projections of a step change them by sum_o a_o kappa(x_{j_o}, x_j); an evicted centre's
+//    contribution is subtracted), and a sample's prediction is formed once, on arrival, from the
+//    live centres; every step's tape (beta, branch, kappa, <w, x_j>, gauss_j, its sigma weight)
+//    goes to the workspace, so nothing is re-run;
+//  * reverse: gbar_i is read only while centre i is in the window.  R_j, the sum of the cg terms
+//    of sample j over the steps swept so far, gives centre i's adjoint when it enters the window
+//    from below: gbar_i = final_i + sum_j R_j kappa_G(x_i, x_j) over the steps in which i is
+//    alive (for a centre evicted during the call, R at the eviction step is kept and subtracted);
+//    from then on it is pushed the W terms of each step like the forward predictions.
+// Kernel values between samples come from tables built once per call.  One CTA of 4 warps per
+// user: the threads split the O(S) sums of an arrival, a thread per window slot for the scalar
+// terms (summed in slot order at the end), a thread per component or window sample for the
+// O(W) updates.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -32,7 +41,9 @@ namespace apsm {
 
 extern std::atomic<long long> g_launches;  // apsm_api.cu
 
-constexpr int kBwdSeg = 64;  // steps per checkpoint segment (32 pilots)
+struct Tape {  // one window slot of one step
+    float beta, s, kappa, dotw, gauss, gd2;
+};
 
 struct TrainBwdArgs {
     int M, K, W, D, P;
@@ -44,22 +55,50 @@ struct TrainBwdArgs {
     const float2 *dclin;    // [M][K] adjoint of the final linear filter
     float *ltab;            // [2P][2P] x_i . x_j
     float *gtab;            // [2P][2P] kappa_G(x_i, x_j)
-    float *ckpt;            // [K][n_seg][2M + 2P]
+    float *gdtab;           // [2P][2P] kappa_G(x_i, x_j) ||x_i - x_j||^2
+    Tape *tape;             // [K][2P][W]
+    float *snap;            // [K][P - D][W] R at the eviction steps (P > D only)
     float *scal;            // [K][4] per-user sigma, mu, eps, w_L adjoints
     float2 *dclin0;         // [M][K] out
     float *dscalars;        // [4] out
-    int n_seg;
+    // instance i of a batch: the pointers above advanced by i times these (elements; ws_stride in
+    // bytes for the workspace regions ltab, gtab, gdtab, tape, snap, scal)
+    size_t st_rx, st_sym, st_clin0, st_dgamma, st_mk, ws_stride;
 };
 
-__global__ void train_bwd_tables_kernel(const TrainBwdArgs a) {
+// The arguments of instance i (blockIdx.y of every launch below).
+__device__ __forceinline__ TrainBwdArgs for_instance(const TrainBwdArgs &a0, int i) {
+    TrainBwdArgs a = a0;
+    auto adv = [&](auto *ptr) { return reinterpret_cast<decltype(ptr)>(reinterpret_cast<unsigned char *>(ptr) + i * a0.ws_stride); };
+    a.rx += i * a.st_rx;
+    a.sym += i * a.st_sym;
+    if (a.clin0) a.clin0 += i * a.st_clin0;
+    a.dgamma += i * a.st_dgamma;
+    a.dclin += i * a.st_mk;
+    a.dclin0 += i * a.st_mk;
+    a.dscalars += 4 * (size_t)i;
+    a.ltab = adv(a.ltab);
+    a.gtab = adv(a.gtab);
+    a.gdtab = adv(a.gdtab);
+    a.tape = adv(a.tape);
+    a.snap = adv(a.snap);
+    a.scal = adv(a.scal);
+    return a;
+}
+
+__global__ void train_bwd_tables_kernel(const TrainBwdArgs a0) {
+    const TrainBwdArgs a = for_instance(a0, blockIdx.y);
     const int S = 2 * a.P;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)S * S;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / S), j = (int)(idx % S);
+        const int i0 = (int)(idx / S), j0 = (int)(idx % S);
+        const int i = min(i0, j0), j = max(i0, j0);  // both halves from one ordering: exactly symmetric
         float dot, d2;
         sample_pair(a.rx + (size_t)(i >> 1) * a.M, a.rx + (size_t)(j >> 1) * a.M, a.M, i & 1, j & 1, dot, d2);
+        const float g = ex2(-a.k2 * d2);
         a.ltab[idx] = dot;
-        a.gtab[idx] = ex2(-a.k2 * d2);
+        a.gtab[idx] = g;
+        a.gdtab[idx] = g * d2;
     }
 }
 
@@ -80,175 +119,432 @@ __device__ __forceinline__ float xcomp(const float2 *rx, int M, int j, int m) {
     return (j & 1) ? -v.x : v.y;
 }
 
-struct Tape {  // one window slot of one step
-    float beta, s, kappa, dotw, gauss, gd2;
+// Slot of a sample in a ring of R slots from the slot b of a reference sample below it and the
+// offset off in [0, 3R] between the two (no integer division on the per-step path).
+__device__ __forceinline__ int ring_slot(int b, int off, int R) {
+    int x = b + off;
+    x -= x >= R ? R : 0;
+    x -= x >= R ? R : 0;
+    x -= x >= R ? R : 0;
+    return x;
+}
+
+// Loads issued a step ahead of their use: predicated rather than followed by a select, so that no
+// instruction waits on the data before it is used; volatile, so that they stay ahead of the barriers.
+__device__ __forceinline__ float ldg_if(bool c, const float *p) {  // read-only data of earlier kernels
+    float v = 0.f;
+    if (c) asm volatile("ld.global.nc.f32 %0, [%1];" : "+f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_if(bool c, const float *p) {  // data this kernel wrote
+    float v = 0.f;
+    if (c) asm volatile("ld.global.f32 %0, [%1];" : "+f"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr int kBwdThreads = 128;  // 4 warps per user
+constexpr int kWarpUsersMax = 16;  // users (warps) per CTA of train_bwd_warp_kernel
+constexpr int kPf = 4;            // entries of the next O(S) row a thread fetches a step ahead, per table
+
+// Entries lo + tid + q * kBwdThreads (q < kPf, below hi) of one or two table rows, a step early.
+struct RowPf {
+    float g[kPf], d[kPf];
 };
 
-constexpr int kBwdThreads = 256;  // 8 warps per user: one window slot per warp
-
-// smem: gamma [2P], gbar [2P], norms [2P], w [2M], wbar [2M], abar [W], cw [W], cg [W],
-//       tape [kBwdSeg][W]
-__global__ void __launch_bounds__(kBwdThreads) train_bwd_kernel(const TrainBwdArgs a) {
-    extern __shared__ __align__(16) float sm[];
-    const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = kBwdThreads / 32;
-    const int M = a.M, K = a.K, W = a.W, D = a.D, P = a.P, S = 2 * P, L2 = 2 * M;
-    float *gam = sm, *gbar = gam + S, *nrm = gbar + S, *w = nrm + S, *wbar = w + L2, *abar = wbar + L2;
-    float *cw = abar + W, *cg = cw + W;
-    Tape *tape = reinterpret_cast<Tape *>(cg + W);
-    const float inv_s3 = 1.f / (a.sigma * a.sigma * a.sigma);
-
-    auto target = [&](int j) {
-        const float2 b = __ldg(a.sym + (size_t)(j >> 1) * K + k);
-        return (j & 1) ? b.y : b.x;
-    };
-    auto first_centre = [&](int n) { return 2 * max(0, (n >> 1) - D + 1); };
-    for (int i = tid; i < S; i += kBwdThreads) nrm[i] = a.ltab[(size_t)i * S + i];  // ||x_i||^2
-
-    // ---- forward over one segment (warp o takes window slots o, o + 8, ...); records the tape --
-    auto forward = [&](int n0, int n1) {
-        for (int n = n0; n < n1; ++n) {
-            const int c_lo = first_centre(n), c_hi = 2 * (n >> 1) + 2;
-            const int jlo = max(0, n - W + 1), nJ = n - jlo + 1;
-            for (int o = warp; o < nJ; o += NW) {
-                const int j = jlo + o;
-                float dw = 0.f;
-                for (int m = lane; m < L2; m += 32) dw = fmaf(w[m], xcomp(a.rx, M, j, m), dw);
-                const float nj = nrm[j];
-                const float *grow = a.gtab + (size_t)j * S, *lrow = a.ltab + (size_t)j * S;
-                float gs[4] = {0.f, 0.f, 0.f, 0.f}, gd[4] = {0.f, 0.f, 0.f, 0.f};
-                int i = c_lo + lane;
-                for (; i + 96 < c_hi; i += 128) {  // four centres per lane in flight
+__device__ __forceinline__ void row_fetch(RowPf &f, const float *grow, const float *drow, int lo, int hi) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int ii = i + 32 * q;
-                        const float g = __ldg(grow + ii), lt = __ldg(lrow + ii), gi = gam[ii];
-                        gs[q] = fmaf(gi, g, gs[q]);
-                        gd[q] = fmaf(gi * g, fmaxf(nrm[ii] + nj - 2.f * lt, 0.f), gd[q]);
-                    }
-                }
-                for (; i < c_hi; i += 32) {
-                    const float g = __ldg(grow + i), lt = __ldg(lrow + i), gi = gam[i];
-                    gs[0] = fmaf(gi, g, gs[0]);
-                    gd[0] = fmaf(gi * g, fmaxf(nrm[i] + nj - 2.f * lt, 0.f), gd[0]);
-                }
-                dw = warp_sum(dw);
-                const float gsum = warp_sum((gs[0] + gs[1]) + (gs[2] + gs[3]));
-                const float gdsum = warp_sum((gd[0] + gd[1]) + (gd[2] + gd[3]));
-                const float y = fmaf(a.wL, dw, a.wG * gsum);
-                const float e = y - target(j);
-                const float kap = fmaf(a.wL, nj, a.wG);
-                float beta = 0.f, s = 0.f;
-                if (kap != 0.f) {
-                    if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
-                    else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
-                }
-                if (lane == 0) tape[(n - n0) * W + o] = Tape{beta, s, kap, dw, gsum, gdsum};
-            }
-            __syncthreads();
-            // all projections of the step from the same f_n (Eq. apsm), then applied together
-            const float mq = a.mu / (float)nJ;
-            if (tid < nJ) gam[jlo + tid] += mq * tape[(n - n0) * W + tid].beta;
-            for (int m = tid; m < L2; m += kBwdThreads) {
-                float acc = w[m];
-                for (int o = 0; o < nJ; ++o) acc = fmaf(mq * tape[(n - n0) * W + o].beta, xcomp(a.rx, M, jlo + o, m), acc);
-                w[m] = acc;
-            }
-            __syncthreads();
+    for (int q = 0; q < kPf; ++q) {
+        const int i = lo + (int)threadIdx.x + q * kBwdThreads;
+        f.g[q] = ldg_if(i < hi, grow + i);
+        f.d[q] = ldg_if(drow != nullptr && i < hi, drow + i);
+    }
+}
+
+// The band of row r that the window needs: entries s0 + t, t = 0..W (thread t holds one, thread 0
+// also t = W when W = kBwdThreads), inside [0, S).  Stored into the window rings kg, kd, kl
+// [(W+1)^2] (sample j in slot j mod (W+1)) at both (r, j) and (j, r): the tables are exactly
+// symmetric.
+struct BandPf {
+    float g[2], d[2], l[2];
+};
+
+__device__ __forceinline__ void band_fetch(BandPf &b, const TrainBwdArgs &a, int S, int W, int r, int s0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int t = (int)threadIdx.x + q * kBwdThreads, j = s0 + t;
+        const bool ok = r >= 0 && r < S && t <= W && j >= 0 && j < S;
+        const size_t x = ok ? (size_t)r * S + j : 0;
+        b.g[q] = ldg_if(ok, a.gtab + x);
+        b.d[q] = ldg_if(ok, a.gdtab + x);
+        b.l[q] = ldg_if(ok, a.ltab + x);
+    }
+}
+
+// (sr, s0r: the ring slots of r and s0)
+__device__ __forceinline__ void band_store(const BandPf &b, float *kg, float *kd, float *kl, int S, int W, int r,
+                                           int s0, int sr, int s0r) {
+    const int WR = W + 1;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int t = (int)threadIdx.x + q * kBwdThreads, j = s0 + t;
+        if (r >= 0 && r < S && t <= W && j >= 0 && j < S) {
+            const int sj = ring_slot(s0r, t, WR);
+            const int u = sr * WR + sj, v = sj * WR + sr;
+            kg[u] = b.g[q];
+            kg[v] = b.g[q];
+            kd[u] = b.d[q];
+            kd[v] = b.d[q];
+            kl[u] = b.l[q];
+            kl[v] = b.l[q];
+        }
+    }
+}
+
+// smem (floats): gamma (forward) / R (reverse) [2P], norms [2P], w / wbar [2M], window rings
+// py, pd, pw [W] (forward: gauss_j, its sigma weight, <w, x_j>; reverse: py = abar_j), ca, cb [W],
+// targets pb [W], warp partials [3 * 4], kg, kd, kl [(W+1)^2] (kappa_G, kappa_G d^2 and x_i . x_j
+// among the samples of the window and the one entering or leaving it), xw [(W+1)][2M] (their
+// components)
+__global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBwdArgs a0) {
+    extern __shared__ __align__(16) float sm[];
+    const TrainBwdArgs a = for_instance(a0, blockIdx.y);
+    constexpr int T = kBwdThreads, NW = T / 32;
+    const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int M = a.M, K = a.K, W = a.W, D = a.D, P = a.P, S = 2 * P, L2 = 2 * M, WR = W + 1;
+    float *gam = sm, *nrm = gam + S, *w = nrm + S, *py = w + L2, *pd = py + W, *pw = pd + W;
+    float *ca = pw + W, *cb = ca + W, *pb = cb + W, *part = pb + W, *kg = part + 3 * NW, *kd = kg + WR * WR;
+    float *kl = kd + WR * WR, *xw = kl + WR * WR;
+    Tape *tape = a.tape + (size_t)k * S * W;
+    float *snap = a.snap + (size_t)k * (P > D ? P - D : 0) * W;
+    const float inv_s3 = 1.f / (a.sigma * a.sigma * a.sigma);
+    const float mqW = a.mu / (float)W, qW = 1.f / (float)W;  // mu q and q of a full window
+    // ring slots relative to the reference sample n - W - 1 of the current step: sW, sR are its
+    // slots (mod W, mod W + 1), kept up to date as n moves (the samples used lie in [n - W - 1, n + 1])
+    auto pmod = [](int x, int R) { return ((x % R) + R) % R; };
+    int sW = 0, sR = 0;
+    auto slotW = [&](int n, int j) { return ring_slot(sW, j - (n - W - 1), W); };
+    auto slotR = [&](int n, int j) { return ring_slot(sR, j - (n - W - 1), WR); };
+
+    auto first_centre = [&](int n) { return 2 * max(0, (n >> 1) - D + 1); };
+    // centre i takes part in the steps n < evict_step(i) (its entry leaves at that step)
+    auto evict_step = [&](int i) { return 2 * ((i >> 1) + D); };
+    auto reduce3 = [&](float x, float y, float z) {  // per-warp partials, combined in warp order
+        x = warp_sum(x);
+        y = warp_sum(y);
+        z = warp_sum(z);
+        if (lane == 0) {
+            part[3 * warp] = x;
+            part[3 * warp + 1] = y;
+            part[3 * warp + 2] = z;
         }
     };
+    auto total = [&](int c) {
+        float s = 0.f;
+        for (int v = 0; v < NW; ++v) s += part[3 * v + c];
+        return s;
+    };
+    // component tid of sample j as stored (x_{2t+1}'s upper half is the negated real part: xsign)
+    auto xc = [&](int j) {
+        const bool ok = tid < L2 && j >= 0 && j < S;
+        const bool up = tid >= M, odd = j & 1;
+        const int mm = up ? tid - M : tid, comp = up ? (odd ? 0 : 1) : (odd ? 1 : 0);
+        return ldg_if(ok, reinterpret_cast<const float *>(a.rx + (ok ? (size_t)(j >> 1) * M + mm : 0)) + comp);
+    };
+    auto xsign = [&](int j, float v) { return (tid >= M && (j & 1)) ? -v : v; };
+    // target b_j of user k (real part for even j, imaginary for odd)
+    auto target_at = [&](bool ok, int j) {
+        return ldg_if(ok, reinterpret_cast<const float *>(a.sym + (ok ? (size_t)(j >> 1) * K + k : 0)) + (j & 1));
+    };
 
-    // ---- pass 1: forward, checkpoint at every segment start ------------------------------------------
-    for (int i = tid; i < S; i += kBwdThreads) gam[i] = 0.f;
-    for (int m = tid; m < M; m += kBwdThreads) {
+    for (int i = tid; i < S; i += T) {
+        gam[i] = 0.f;
+        nrm[i] = a.ltab[(size_t)i * S + i];  // ||x_i||^2
+    }
+    for (int m = tid; m < M; m += T) {
         const float2 c = a.clin0 ? a.clin0[m * K + k] : make_float2(0.f, 0.f);
-        w[m] = c.x;      // w = [Re c; Im c]
+        w[m] = c.x;  // w = [Re c; Im c]
         w[M + m] = c.y;
     }
+    RowPf pf;
+    BandPf bp;
+    sW = pmod(-W - 1, W);
+    sR = pmod(-W - 1, WR);
+    band_fetch(bp, a, S, W, 0, -W);
+    band_store(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W));
+    band_fetch(bp, a, S, W, 1, 1 - W);
+    if (S > 1) row_fetch(pf, a.gtab + S, a.gdtab + S, first_centre(1), 1);
+    if (tid < L2) xw[slotR(0, 0) * L2 + tid] = xcomp(a.rx, M, 0, tid);
+    float xn = xc(1);
+    float bn = target_at(tid == T - 1 && S > 1, 1);  // the target of the next arrival, a step early
+    if (tid == 0) pb[0] = target_at(true, 0);
     __syncthreads();
-    float *ck = a.ckpt + (size_t)k * a.n_seg * (L2 + S);
-    for (int sg = 0; sg < a.n_seg; ++sg) {
-        float *dst = ck + (size_t)sg * (L2 + S);
-        for (int m = tid; m < L2; m += kBwdThreads) dst[m] = w[m];
-        for (int i = tid; i < S; i += kBwdThreads) dst[L2 + i] = gam[i];
-        forward(sg * kBwdSeg, min(S, (sg + 1) * kBwdSeg));
+
+    // ---- forward: sample 0 arrives with no live centre --------------------------------------------
+    reduce3(0.f, 0.f, tid < L2 ? w[tid] * xw[slotR(0, 0) * L2 + tid] : 0.f);
+    __syncthreads();
+    if (tid == 0) {
+        py[0] = 0.f;
+        pd[0] = 0.f;
+        pw[0] = total(2);
+    }
+    __syncthreads();
+    for (int n = 0; n < S; ++n, sW = ring_slot(sW, 1, W), sR = ring_slot(sR, 1, WR)) {
+        const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, jn = n + 1;
+        const float mq = nJ == W ? mqW : a.mu / (float)nJ;
+        const float b_jn = bn;
+        if (warp == NW - 1) bn = target_at(tid == T - 1 && jn + 1 < S, jn + 1);
+        // the next sample's prediction from the live centres, before this step's update
+        if (jn < S) {
+            if (tid <= W) {
+                band_store(bp, kg, kd, kl, S, W, jn, jn - W, slotR(n, jn), slotR(n, jn - W));
+                band_fetch(bp, a, S, W, jn + 1, jn + 1 - W);
+            }
+            float ws = 0.f;
+            if (tid < L2) {
+                const float x = xsign(jn, xn);
+                xw[slotR(n, jn) * L2 + tid] = x;
+                ws = w[tid] * x;
+                xn = xc(jn + 1);
+            }
+            const int lo = first_centre(jn);
+            const float *grow = a.gtab + (size_t)jn * S, *drow = a.gdtab + (size_t)jn * S;
+            float ys = 0.f, ds = 0.f;
+#pragma unroll
+            for (int q = 0; q < kPf; ++q) {
+                const int i = lo + tid + q * T;
+                if (i < jn) {
+                    ys = fmaf(gam[i], pf.g[q], ys);
+                    ds = fmaf(gam[i], pf.d[q], ds);
+                }
+            }
+            for (int i = lo + tid + kPf * T; i < jn; i += T) {
+                ys = fmaf(gam[i], __ldg(grow + i), ys);
+                ds = fmaf(gam[i], __ldg(drow + i), ds);
+            }
+            reduce3(ys, ds, ws);
+            if (jn + 1 < S)
+                row_fetch(pf, a.gtab + (size_t)(jn + 1) * S, a.gdtab + (size_t)(jn + 1) * S, first_centre(jn + 1),
+                          jn + 1);
+        }
+        // the window's projections (Eq. beta), all from f_n
+        if (tid < nJ) {
+            const int j = jlo + tid, r = slotW(n, j);
+            const float dw = pw[r], yg = py[r], gd = pd[r];
+            const float y = fmaf(a.wL, dw, a.wG * yg);
+            const float e = y - pb[r];
+            const float kap = fmaf(a.wL, nrm[j], a.wG);
+            float beta = 0.f, s = 0.f;
+            if (kap != 0.f) {
+                if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
+                else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
+            }
+            tape[(size_t)n * W + tid] = Tape{beta, s, kap, dw, yg, gd};
+            ca[tid] = mq * beta;
+            cb[tid] = gam[j] + mq * beta;  // the coefficient after the step
+        }
+        __syncthreads();
+        // Eq. apsm: coefficients, linear part, and the carried predictions of J_{n+1}.  With
+        // 2D = W + 1 the oldest centre of J_n leaves before step n+1: the arrival jn takes no term
+        // of it, and the other samples drop its coefficient after this step's update.
+        if (tid < nJ) gam[jlo + tid] = cb[tid];
+        if (tid == T - 1 && jn < S) pb[slotW(n, jn)] = b_jn;
+        const int t_lo = max(0, n - W + 2), n_t = jn < S ? jn - t_lo + 1 : 0;
+        const int e_lo = first_centre(n), e_hi = jn < S ? first_centre(jn) : e_lo;  // leave before step n+1
+        const int s_lo = slotR(n, jlo);
+        for (int u = tid; u < L2 + n_t; u += T) {
+            if (u < L2) {
+                float acc = w[u];
+                int si = s_lo;
+#pragma unroll 4
+                for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) acc = fmaf(ca[o], xw[si * L2 + u], acc);
+                w[u] = acc;
+            } else {
+                const int j = t_lo + (u - L2), r = slotW(n, j), sj = slotR(n, j) * WR;
+                float ay, ad, aw;
+                if (j == jn) {
+                    ay = total(0);
+                    ad = total(1);
+                    aw = total(2);
+                } else {
+                    ay = py[r];
+                    ad = pd[r];
+                    aw = pw[r];
+                }
+                const int o_lo = j == jn ? max(0, e_hi - jlo) : 0;  // sources still live at jn
+                int si = s_lo;
+#pragma unroll 4
+                for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) {
+                    const float c = ca[o];
+                    aw = fmaf(c, kl[sj + si], aw);
+                    if (o >= o_lo) {
+                        ay = fmaf(c, kg[sj + si], ay);
+                        ad = fmaf(c, kd[sj + si], ad);
+                    }
+                }
+                if (j != jn) {
+                    const float *grow = a.gtab + (size_t)j * S, *drow = a.gdtab + (size_t)j * S;
+                    for (int i = e_lo; i < e_hi; ++i) {  // centres leaving before step n+1
+                        const float gi = i >= jlo ? cb[i - jlo] : gam[i];
+                        ay = fmaf(-gi, __ldg(grow + i), ay);
+                        ad = fmaf(-gi, __ldg(drow + i), ad);
+                    }
+                }
+                py[r] = ay;
+                pd[r] = ad;
+                pw[r] = aw;
+            }
+        }
+        __syncthreads();
     }
 
-    // ---- initial adjoint: the final coefficients and linear filter --------------------------------
-    for (int i = tid; i < S; i += kBwdThreads) {
-        const int t = i >> 1;
-        const bool alive = P > 0 && t >= max(0, P - D);
-        gbar[i] = alive ? a.dgamma[((size_t)(t % D) * 2 + (i & 1)) * K + k] : 0.f;
-    }
-    for (int m = tid; m < M; m += kBwdThreads) {
+    // ---- reverse sweep: R = 0, wbar = dL/dw of the final state ------------------------------------
+    // (kg, kl and xw still hold the last W + 1 samples)
+    for (int i = tid; i < S; i += T) gam[i] = 0.f;
+    for (int m = tid; m < M; m += T) {
         const float2 d = a.dclin[m * K + k];
-        wbar[m] = d.x;
-        wbar[M + m] = d.y;
+        w[m] = d.x;
+        w[M + m] = d.y;
     }
+    const int alive0 = max(0, P - D);  // first pilot whose entry is held at the end
+    auto final_at = [&](int j) {       // adjoint of the final coefficient of sample j (0 if evicted)
+        const bool ok = j >= 0 && (j >> 1) >= alive0;
+        return ldg_if(ok, a.dgamma + (ok ? ((size_t)((j >> 1) % D) * 2 + (j & 1)) * K + k : 0));
+    };
+    // centres with a nonzero R when the entrant n - W is pulled at step n (none when it is not alive
+    // in any step after n)
+    auto pull_hi = [&](int n) {
+        const int e = evict_step(n - W);
+        return e > n + 1 ? min(e, S) : n - W + 2;
+    };
+    __syncthreads();
+    for (int j = max(0, S - W) + tid; j < S; j += T) {  // abar of the last window
+        float d = 0.f;
+        for (int m = 0; m < L2; ++m) d = fmaf(w[m], xcomp(a.rx, M, j, m), d);
+        py[j % W] = d + final_at(j);
+    }
+    const int je0 = S - 1 - W;  // the first entrant
+    if (je0 >= 0) row_fetch(pf, a.gtab + (size_t)je0 * S, nullptr, je0 + 2, pull_hi(S - 1));
+    band_fetch(bp, a, S, W, je0, je0);
+    xn = xc(je0);
+    const int t_fa = L2 % T;  // the thread that updates the entrant's abar
+    float fa = tid == t_fa ? final_at(je0) : 0.f;  // the entrant's final adjoint, a step early
+    Tape tnext;
+    auto tape_at = [&](Tape &t, bool ok, int n) {
+        const float *f = reinterpret_cast<const float *>(tape + (ok ? (size_t)n * W + tid : 0));
+        t.beta = ld_if(ok, f);
+        t.s = ld_if(ok, f + 1);
+        t.kappa = ld_if(ok, f + 2);
+        t.dotw = ld_if(ok, f + 3);
+        t.gauss = ld_if(ok, f + 4);
+        t.gd2 = ld_if(ok, f + 5);
+    };
+    if (tid < W) tape_at(tnext, tid < S - max(0, S - W), S - 1);
+    sW = pmod(S - 1 - W - 1, W);
+    sR = pmod(S - 1 - W - 1, WR);
     __syncthreads();
     // scalar adjoints: thread o sums the terms of window slot o over all steps (fixed order)
     float sig_bar = 0.f, mu_bar = 0.f, eps_bar = 0.f, wl_bar = 0.f;
-
-    // ---- reverse sweep, one segment at a time -------------------------------------------------------
-    for (int sg = a.n_seg - 1; sg >= 0; --sg) {
-        const int n0 = sg * kBwdSeg, n1 = min(S, (sg + 1) * kBwdSeg);
-        const float *src = ck + (size_t)sg * (L2 + S);
-        for (int m = tid; m < L2; m += kBwdThreads) w[m] = src[m];
-        for (int i = tid; i < S; i += kBwdThreads) gam[i] = src[L2 + i];
-        __syncthreads();
-        forward(n0, n1);
-        for (int n = n1 - 1; n >= n0; --n) {
-            const int c_lo = first_centre(n), c_hi = 2 * (n >> 1) + 2;
-            const int jlo = max(0, n - W + 1), nJ = n - jlo + 1;
-            const float q = 1.f / (float)nJ;
-            // abar_j from the adjoint of S_{n+1}, for every j, before any update
-            for (int o = warp; o < nJ; o += NW) {
-                const int j = jlo + o;
-                float d = 0.f;
-                for (int m = lane; m < L2; m += 32) d = fmaf(wbar[m], xcomp(a.rx, M, j, m), d);
-                d = warp_sum(d) + gbar[j];
-                if (lane == 0) abar[o] = d;
-            }
-            __syncthreads();
-            if (tid < nJ) {  // slot tid: its scalar terms and its coefficients for the state adjoint
-                const int o = tid, j = jlo + o;
-                const float ab = abar[o];
-                const Tape tp = tape[(n - n0) * W + o];
-                mu_bar += q * tp.beta * ab;
-                const float bbar = a.mu * q * ab;
-                float cwo = 0.f, cgo = 0.f;
-                if (tp.s != 0.f) {  // inside the slab beta does not depend on the state
-                    const float ybar = -bbar / tp.kappa;
-                    eps_bar += -tp.s * bbar / tp.kappa;
-                    wl_bar += (-bbar * tp.beta / tp.kappa) * (nrm[j] - 1.f);
-                    wl_bar += ybar * (tp.dotw - tp.gauss);
-                    sig_bar += ybar * a.wG * tp.gd2 * inv_s3;
-                    cwo = ybar * a.wL;
-                    cgo = ybar * a.wG;
-                }
-                cw[o] = cwo;
-                cg[o] = cgo;
-            }
-            __syncthreads();
-            for (int m = tid; m < L2; m += kBwdThreads) {
-                float acc = wbar[m];
-                for (int o = 0; o < nJ; ++o) acc = fmaf(cw[o], xcomp(a.rx, M, jlo + o, m), acc);
-                wbar[m] = acc;
-            }
-            for (int i = c_lo + tid; i < c_hi; i += kBwdThreads) {
-                float acc = gbar[i];
-                for (int o = 0; o < nJ; ++o) acc = fmaf(cg[o], __ldg(a.gtab + (size_t)(jlo + o) * S + i), acc);
-                gbar[i] = acc;
-            }
-            __syncthreads();
+    for (int n = S - 1; n >= 0; --n, sW = ring_slot(sW, W - 1, W), sR = ring_slot(sR, WR - 1, WR)) {
+        const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, je = n - W;
+        const float q = nJ == W ? qW : 1.f / (float)nJ;
+        float fa_je = 0.f;
+        if (tid == t_fa) {
+            fa_je = fa;
+            fa = final_at(je - 1);
         }
+        // R after the steps >= e, kept for the centres whose entry leaves at step e = n + 1
+        if (((n + 1) & 1) == 0 && n + 1 <= S - 1 && ((n + 1) >> 1) >= D && tid < W - 1) {
+            const int e = n + 1;
+            snap[(size_t)((e >> 1) - D) * W + tid] = gam[e - W + 1 + tid];
+        }
+        // the entrant's pull: sum_j R_j kappa_G(x_je, x_j) over the steps after n in which it is alive,
+        // and <wbar, x_je>, both before this step's terms
+        if (je >= 0) {
+            if (tid <= W) {
+                band_store(bp, kg, kd, kl, S, W, je, je, slotR(n, je), slotR(n, je));
+                band_fetch(bp, a, S, W, je - 1, je - 1);
+            }
+            float ls = 0.f;
+            if (tid < L2) {
+                const float x = xsign(je, xn);
+                xw[slotR(n, je) * L2 + tid] = x;
+                ls = w[tid] * x;
+                xn = xc(je - 1);
+            }
+            const int lo = je + 2, hi = pull_hi(n), e = evict_step(je);
+            const int s_lo = e <= S - 1 ? e - W + 1 : S;  // centres whose R holds steps >= e
+            const float *sv = snap + (size_t)((e >> 1) - D) * W;
+            const float *grow = a.gtab + (size_t)je * S;
+            float gs = 0.f;
+#pragma unroll
+            for (int qq = 0; qq < kPf; ++qq) {
+                const int i = lo + tid + qq * T;
+                if (i < hi) gs = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], pf.g[qq], gs);
+            }
+            for (int i = lo + tid + kPf * T; i < hi; i += T)
+                gs = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], __ldg(grow + i), gs);
+            reduce3(gs, ls, 0.f);
+            if (je - 1 >= 0) row_fetch(pf, a.gtab + (size_t)(je - 1) * S, nullptr, je + 1, pull_hi(n - 1));
+        }
+        if (tid < nJ) {  // slot tid: its scalar terms and its coefficients for the state adjoint
+            const Tape tp = tnext;
+            tape_at(tnext, n > 0 && tid < n - max(0, n - W), n - 1);
+            const int o = tid, j = jlo + o;
+            const float ab = py[slotW(n, j)];
+            mu_bar += q * tp.beta * ab;
+            const float bbar = a.mu * q * ab;
+            float cwo = 0.f, cgo = 0.f;
+            if (tp.s != 0.f) {  // inside the slab beta does not depend on the state
+                const float ybar = -bbar / tp.kappa;
+                eps_bar += tp.s * ybar;
+                wl_bar += (ybar * tp.beta) * (nrm[j] - 1.f);
+                wl_bar += ybar * (tp.dotw - tp.gauss);
+                sig_bar += ybar * a.wG * tp.gd2 * inv_s3;
+                cwo = ybar * a.wL;
+                cgo = ybar * a.wG;
+            }
+            ca[o] = cwo;
+            cb[o] = cgo;
+        } else if (tid < W) {
+            tape_at(tnext, n > 0 && tid < n - max(0, n - W), n - 1);
+        }
+        __syncthreads();
+        // adjoint of S_n: R, wbar, and abar of the samples of J_{n-1}
+        if (tid < nJ) gam[jlo + tid] += cb[tid];
+        const int t_lo = max(0, n - W), n_t = n - t_lo;
+        const int s_lo = slotR(n, jlo);
+        for (int u = tid; u < L2 + n_t; u += T) {
+            if (u < L2) {
+                float acc = w[u];
+                int si = s_lo;
+#pragma unroll 4
+                for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) acc = fmaf(ca[o], xw[si * L2 + u], acc);
+                w[u] = acc;
+            } else {
+                const int j = t_lo + (u - L2), r = slotW(n, j), sj = slotR(n, j) * WR;
+                float acc;
+                bool alive = true;  // centres of J_{n-1} other than the entrant are alive at step n
+                if (j == je) {
+                    acc = fa_je + total(0) + total(1);
+                    alive = n < evict_step(j);
+                } else {
+                    acc = py[r];
+                }
+                int si = s_lo;
+#pragma unroll 4
+                for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) {
+                    acc = fmaf(ca[o], kl[sj + si], acc);
+                    if (alive) acc = fmaf(cb[o], kg[sj + si], acc);
+                }
+                py[r] = acc;
+            }
+        }
+        __syncthreads();
     }
 
     // ---- results -------------------------------------------------------------------------------------
-    for (int m = tid; m < M; m += kBwdThreads) a.dclin0[m * K + k] = make_float2(wbar[m], wbar[M + m]);
-    // per-slot partial sums, combined in slot order
-    __syncthreads();
-    float *red = reinterpret_cast<float *>(tape);  // free now (kBwdSeg * W tapes >= 4 W floats)
+    for (int m = tid; m < M; m += T) a.dclin0[m * K + k] = make_float2(w[m], w[M + m]);
+    float *red = py;  // py, pd, pw, ca: 4 W floats, free now
     if (tid < W) {
         red[4 * tid + 0] = sig_bar;
         red[4 * tid + 1] = mu_bar;
@@ -263,7 +559,414 @@ __global__ void __launch_bounds__(kBwdThreads) train_bwd_kernel(const TrainBwdAr
     }
 }
 
-__global__ void train_bwd_sum_kernel(const TrainBwdArgs a) {
+// ---- one warp per user -------------------------------------------------------------------------
+// The same recurrence and adjoint as train_bwd_kernel, for windows of at most 32 slots: one warp
+// per user (lane o = window slot o), the users of one instance in one CTA, and no block barrier
+// inside the step loop -- each step synchronises one warp only.  The O(S) sums of a step take
+// kPfW entries per lane from registers loaded a step ahead (the rest directly).
+constexpr int kPfW = 16;
+
+struct RowPfW {
+    float g[kPfW], d[kPfW];
+};
+
+__device__ __forceinline__ void row_fetch_w(RowPfW &f, const float *grow, const float *drow, int lo, int hi, int lane) {
+#pragma unroll
+    for (int q = 0; q < kPfW; ++q) {
+        const int i = lo + lane + 32 * q;
+        f.g[q] = ldg_if(i < hi, grow + i);
+        f.d[q] = ldg_if(drow != nullptr && i < hi, drow + i);
+    }
+}
+
+// band of row r, entries s0 + t for t = lane (and lane + 32 when W = 32), inside [0, S)
+template <int NQ>
+__device__ __forceinline__ void band_fetch_w(BandPf &b, const TrainBwdArgs &a, int S, int W, int r, int s0, int lane) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int t = lane + 32 * q, j = s0 + t;
+        const bool ok = r >= 0 && r < S && t <= W && j >= 0 && j < S;
+        const size_t x = ok ? (size_t)r * S + j : 0;
+        b.g[q] = ldg_if(ok, a.gtab + x);
+        b.d[q] = ldg_if(ok, a.gdtab + x);
+        b.l[q] = ldg_if(ok, a.ltab + x);
+    }
+}
+
+template <int NQ>
+__device__ __forceinline__ void band_store_w(const BandPf &b, float *kg, float *kd, float *kl, int S, int W, int r,
+                                             int s0, int sr, int s0r, int lane) {
+    const int WR = W + 1;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int t = lane + 32 * q, j = s0 + t;
+        if (r >= 0 && r < S && t <= W && j >= 0 && j < S) {
+            const int sj = ring_slot(s0r, t, WR);
+            const int u = sr * WR + sj, v = sj * WR + sr;
+            kg[u] = b.g[q];
+            kg[v] = b.g[q];
+            kd[u] = b.d[q];
+            kd[v] = b.d[q];
+            kl[u] = b.l[q];
+            kl[v] = b.l[q];
+        }
+    }
+}
+
+// floats of one warp's region: gamma / R [S], kg, kd, kl [(W+1)^2], xw [(W+1)][2M], py, pd, pw,
+// pb, ca, cb [W], w / wbar [2M]
+__host__ __device__ inline int bwd_warp_floats(int S, int W, int L2) {
+    const int WR = W + 1;
+    return (S + 3 * WR * WR + WR * L2 + 6 * W + L2 + 3) & ~3;
+}
+
+// WM: a bound on the window (8, 16 or 32) over which the O(W) loops are unrolled, so that their
+// shared-memory loads are independent of one another.
+template <int WM>
+__global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(const TrainBwdArgs a0) {
+    extern __shared__ __align__(16) float sm[];
+    const TrainBwdArgs a = for_instance(a0, blockIdx.y);
+    constexpr int NQ = WM >= 32 ? 2 : 1;  // band entries per lane (W + 1 <= 32 NQ)
+    const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
+    const int M = a.M, K = a.K, W = a.W, D = a.D, P = a.P, S = 2 * P, L2 = 2 * M, WR = W + 1;
+    float *nrm = sm;
+    float *gam = nrm + ((S + 3) & ~3) + k * bwd_warp_floats(S, W, L2);
+    float *kg = gam + S, *kd = kg + WR * WR, *kl = kd + WR * WR, *xw = kl + WR * WR;
+    float *py = xw + WR * L2, *pd = py + W, *pw = pd + W, *pb = pw + W, *ca = pb + W, *cb = ca + W, *w = cb + W;
+    Tape *tape = a.tape + (size_t)k * S * W;
+    float *snap = a.snap + (size_t)k * (P > D ? P - D : 0) * W;
+    const float inv_s3 = 1.f / (a.sigma * a.sigma * a.sigma);
+    const float mqW = a.mu / (float)W, qW = 1.f / (float)W;
+    auto pmod = [](int x, int R) { return ((x % R) + R) % R; };
+    int sW = 0, sR = 0;  // slots of the reference sample n - W - 1 (mod W, mod W + 1)
+    auto slotW = [&](int n, int j) { return ring_slot(sW, j - (n - W - 1), W); };
+    auto slotR = [&](int n, int j) { return ring_slot(sR, j - (n - W - 1), WR); };
+    auto first_centre = [&](int n) { return 2 * max(0, (n >> 1) - D + 1); };
+    auto evict_step = [&](int i) { return 2 * ((i >> 1) + D); };
+    // component m of sample j as stored, and its sign (x_{2t+1}'s upper half is -Re r)
+    auto xc = [&](int j, int m) {
+        const bool ok = m < L2 && j >= 0 && j < S;
+        const bool up = m >= M, odd = j & 1;
+        const int mm = up ? m - M : m, comp = up ? (odd ? 0 : 1) : (odd ? 1 : 0);
+        return ldg_if(ok, reinterpret_cast<const float *>(a.rx + (ok ? (size_t)(j >> 1) * M + mm : 0)) + comp);
+    };
+    auto xsign = [&](int j, int m, float v) { return (m >= M && (j & 1)) ? -v : v; };
+    auto wrap = [&](int x) { return x >= WR ? x - WR : x; };  // x < 2 (W + 1)
+    auto target_at = [&](bool ok, int j) {
+        return ldg_if(ok, reinterpret_cast<const float *>(a.sym + (ok ? (size_t)(j >> 1) * K + k : 0)) + (j & 1));
+    };
+
+    for (int i = threadIdx.x; i < S; i += blockDim.x) nrm[i] = a.ltab[(size_t)i * S + i];  // ||x_i||^2
+    __syncthreads();  // the only block barrier: nrm is shared by the users
+    for (int i = lane; i < S; i += 32) gam[i] = 0.f;
+    for (int m = lane; m < M; m += 32) {
+        const float2 c = a.clin0 ? a.clin0[m * K + k] : make_float2(0.f, 0.f);
+        w[m] = c.x;
+        w[M + m] = c.y;
+    }
+    RowPfW pf;
+    BandPf bp;
+    float xn[4];
+    sW = pmod(-W - 1, W);
+    sR = pmod(-W - 1, WR);
+    band_fetch_w<NQ>(bp, a, S, W, 0, -W, lane);
+    band_store_w<NQ>(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W), lane);
+    band_fetch_w<NQ>(bp, a, S, W, 1, 1 - W, lane);
+    if (S > 1) row_fetch_w(pf, a.gtab + S, a.gdtab + S, first_centre(1), 1, lane);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int m = lane + 32 * c;
+        if (m < L2) xw[slotR(0, 0) * L2 + m] = xcomp(a.rx, M, 0, m);
+        xn[c] = xc(1, m);
+    }
+    float bn = target_at(lane == 0 && S > 1, 1);  // the next arrival's target, a step early
+    if (lane == 0) pb[0] = target_at(true, 0);
+    __syncwarp();
+    {
+        float ws = 0.f;
+        for (int m = lane; m < L2; m += 32) ws = fmaf(w[m], xw[slotR(0, 0) * L2 + m], ws);
+        ws = warp_sum(ws);
+        if (lane == 0) {
+            py[0] = 0.f;
+            pd[0] = 0.f;
+            pw[0] = ws;
+        }
+    }
+    __syncwarp();
+
+    // ---- forward ---------------------------------------------------------------------------------------
+    for (int n = 0; n < S; ++n, sW = ring_slot(sW, 1, W), sR = ring_slot(sR, 1, WR)) {
+        const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, jn = n + 1;
+        const float mq = nJ == W ? mqW : a.mu / (float)nJ;
+        const float b_jn = bn;
+        bn = target_at(lane == 0 && jn + 1 < S, jn + 1);
+        float ys = 0.f, ds = 0.f, ws = 0.f;  // the arrival's sums from the state before this step
+        if (jn < S) {
+            band_store_w<NQ>(bp, kg, kd, kl, S, W, jn, jn - W, slotR(n, jn), slotR(n, jn - W), lane);
+            band_fetch_w<NQ>(bp, a, S, W, jn + 1, jn + 1 - W, lane);
+            const int sx = slotR(n, jn) * L2;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int m = lane + 32 * c;
+                if (m < L2) {
+                    const float x = xsign(jn, m, xn[c]);
+                    xw[sx + m] = x;
+                    ws = fmaf(w[m], x, ws);
+                    xn[c] = xc(jn + 1, m);
+                }
+            }
+            const int lo = first_centre(jn);
+            float y2[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // two chains of sums
+#pragma unroll
+            for (int q = 0; q < kPfW; ++q) {
+                const int i = lo + lane + 32 * q;
+                if (i < jn) {
+                    y2[q & 1] = fmaf(gam[i], pf.g[q], y2[q & 1]);
+                    d2[q & 1] = fmaf(gam[i], pf.d[q], d2[q & 1]);
+                }
+            }
+            const float *grow = a.gtab + (size_t)jn * S, *drow = a.gdtab + (size_t)jn * S;
+            for (int i = lo + lane + 32 * kPfW; i < jn; i += 32) {
+                y2[0] = fmaf(gam[i], __ldg(grow + i), y2[0]);
+                d2[0] = fmaf(gam[i], __ldg(drow + i), d2[0]);
+            }
+            ys = y2[0] + y2[1];
+            ds = d2[0] + d2[1];
+            if (jn + 1 < S)
+                row_fetch_w(pf, a.gtab + (size_t)(jn + 1) * S, a.gdtab + (size_t)(jn + 1) * S, first_centre(jn + 1),
+                            jn + 1, lane);
+            ys = warp_sum(ys);
+            ds = warp_sum(ds);
+            ws = warp_sum(ws);
+        }
+        if (lane < nJ) {  // the window's projections (Eq. beta), all from f_n
+            const int j = jlo + lane, r = slotW(n, j);
+            const float dw = pw[r], yg = py[r], gd = pd[r];
+            const float y = fmaf(a.wL, dw, a.wG * yg);
+            const float e = y - pb[r];
+            const float kap = fmaf(a.wL, nrm[j], a.wG);
+            float beta = 0.f, s = 0.f;
+            if (kap != 0.f) {
+                if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
+                else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
+            }
+            tape[(size_t)n * W + lane] = Tape{beta, s, kap, dw, yg, gd};
+            ca[lane] = mq * beta;
+            cb[lane] = gam[j] + mq * beta;  // the coefficient after the step
+        }
+        __syncwarp();
+        // Eq. apsm: coefficients, linear part, carried predictions of J_{n+1} (2D = W + 1: the oldest
+        // centre of J_n leaves before step n+1)
+        if (lane < nJ) gam[jlo + lane] = cb[lane];
+        if (lane == 0 && jn < S) pb[slotW(n, jn)] = b_jn;
+        const int s_lo = slotR(n, jlo);
+        for (int m = lane; m < L2; m += 32) {
+            float acc = w[m];
+#pragma unroll
+            for (int o = 0; o < WM; ++o)
+                if (o < nJ) acc = fmaf(ca[o], xw[wrap(s_lo + o) * L2 + m], acc);
+            w[m] = acc;
+        }
+        const int t_lo = max(0, n - W + 2), n_t = jn < S ? jn - t_lo + 1 : 0;
+        const int e_lo = first_centre(n), e_hi = jn < S ? first_centre(jn) : e_lo;
+        if (lane < n_t) {
+            const int j = t_lo + lane, r = slotW(n, j), sj = slotR(n, j) * WR;
+            float ay, ad, aw;
+            if (j == jn) {
+                ay = ys;
+                ad = ds;
+                aw = ws;
+            } else {
+                ay = py[r];
+                ad = pd[r];
+                aw = pw[r];
+            }
+            const int o_lo = j == jn ? max(0, e_hi - jlo) : 0;
+#pragma unroll
+            for (int o = 0; o < WM; ++o) {
+                if (o < nJ) {
+                    const int si = sj + wrap(s_lo + o);
+                    const float c = ca[o];
+                    aw = fmaf(c, kl[si], aw);
+                    if (o >= o_lo) {
+                        ay = fmaf(c, kg[si], ay);
+                        ad = fmaf(c, kd[si], ad);
+                    }
+                }
+            }
+            if (j != jn) {
+                const float *grow = a.gtab + (size_t)j * S, *drow = a.gdtab + (size_t)j * S;
+                for (int i = e_lo; i < e_hi; ++i) {
+                    const float gi = i >= jlo ? cb[i - jlo] : gam[i];
+                    ay = fmaf(-gi, __ldg(grow + i), ay);
+                    ad = fmaf(-gi, __ldg(drow + i), ad);
+                }
+            }
+            py[r] = ay;
+            pd[r] = ad;
+            pw[r] = aw;
+        }
+        __syncwarp();
+    }
+
+    // ---- reverse sweep ---------------------------------------------------------------------------------
+    for (int i = lane; i < S; i += 32) gam[i] = 0.f;  // R
+    for (int m = lane; m < M; m += 32) {
+        const float2 d = a.dclin[m * K + k];
+        w[m] = d.x;
+        w[M + m] = d.y;
+    }
+    const int alive0 = max(0, P - D);
+    auto final_at = [&](int j) {
+        const bool ok = j >= 0 && (j >> 1) >= alive0;
+        return ldg_if(ok, a.dgamma + (ok ? ((size_t)((j >> 1) % D) * 2 + (j & 1)) * K + k : 0));
+    };
+    auto pull_hi = [&](int n) {
+        const int e = evict_step(n - W);
+        return e > n + 1 ? min(e, S) : n - W + 2;
+    };
+    __syncwarp();
+    for (int j = max(0, S - W) + lane; j < S; j += 32) {  // abar of the last window (xw holds them)
+        float d = 0.f;
+        const int sx = pmod(j, WR) * L2;
+        for (int m = 0; m < L2; ++m) d = fmaf(w[m], xw[sx + m], d);
+        py[j % W] = d + final_at(j);
+    }
+    const int je0 = S - 1 - W;
+    if (je0 >= 0) row_fetch_w(pf, a.gtab + (size_t)je0 * S, nullptr, je0 + 2, pull_hi(S - 1), lane);
+    band_fetch_w<NQ>(bp, a, S, W, je0, je0, lane);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) xn[c] = xc(je0, lane + 32 * c);
+    float fa = final_at(je0);  // every lane: the entrant's final adjoint, a step early
+    Tape tnext;
+    auto tape_at = [&](Tape &t, bool ok, int n) {
+        const float *f = reinterpret_cast<const float *>(tape + (ok ? (size_t)n * W + lane : 0));
+        t.beta = ld_if(ok, f);
+        t.s = ld_if(ok, f + 1);
+        t.kappa = ld_if(ok, f + 2);
+        t.dotw = ld_if(ok, f + 3);
+        t.gauss = ld_if(ok, f + 4);
+        t.gd2 = ld_if(ok, f + 5);
+    };
+    tape_at(tnext, lane < S - max(0, S - W), S - 1);
+    sW = pmod(S - 1 - W - 1, W);
+    sR = pmod(S - 1 - W - 1, WR);
+    __syncwarp();
+    float sig_bar = 0.f, mu_bar = 0.f, eps_bar = 0.f, wl_bar = 0.f;  // lane o: window slot o's terms
+    for (int n = S - 1; n >= 0; --n, sW = ring_slot(sW, W - 1, W), sR = ring_slot(sR, WR - 1, WR)) {
+        const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, je = n - W;
+        const float q = nJ == W ? qW : 1.f / (float)nJ;
+        const float fa_je = fa;
+        fa = final_at(je - 1);
+        if (((n + 1) & 1) == 0 && n + 1 <= S - 1 && ((n + 1) >> 1) >= D && lane < W - 1) {
+            const int e = n + 1;  // R after the steps >= e, for the centres whose entry leaves at e
+            snap[(size_t)((e >> 1) - D) * W + lane] = gam[e - W + 1 + lane];
+        }
+        float gs = 0.f, ls = 0.f;
+        if (je >= 0) {
+            band_store_w<NQ>(bp, kg, kd, kl, S, W, je, je, slotR(n, je), slotR(n, je), lane);
+            band_fetch_w<NQ>(bp, a, S, W, je - 1, je - 1, lane);
+            const int sx = slotR(n, je) * L2;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int m = lane + 32 * c;
+                if (m < L2) {
+                    const float x = xsign(je, m, xn[c]);
+                    xw[sx + m] = x;
+                    ls = fmaf(w[m], x, ls);
+                    xn[c] = xc(je - 1, m);
+                }
+            }
+            const int lo = je + 2, hi = pull_hi(n), e = evict_step(je);
+            const int s_lo = e <= S - 1 ? e - W + 1 : S;
+            const float *sv = snap + (size_t)((e >> 1) - D) * W;
+            const float *grow = a.gtab + (size_t)je * S;
+            float g2[2] = {0.f, 0.f};
+#pragma unroll
+            for (int qq = 0; qq < kPfW; ++qq) {
+                const int i = lo + lane + 32 * qq;
+                if (i < hi) g2[qq & 1] = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], pf.g[qq], g2[qq & 1]);
+            }
+            for (int i = lo + lane + 32 * kPfW; i < hi; i += 32)
+                g2[0] = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], __ldg(grow + i), g2[0]);
+            gs = g2[0] + g2[1];
+            if (je - 1 >= 0) row_fetch_w(pf, a.gtab + (size_t)(je - 1) * S, nullptr, je + 1, pull_hi(n - 1), lane);
+            gs = warp_sum(gs);
+            ls = warp_sum(ls);
+        }
+        if (lane < nJ) {
+            const Tape tp = tnext;
+            tape_at(tnext, n > 0 && lane < n - max(0, n - W), n - 1);
+            const int j = jlo + lane;
+            const float ab = py[slotW(n, j)];
+            mu_bar += q * tp.beta * ab;
+            const float bbar = a.mu * q * ab;
+            float cwo = 0.f, cgo = 0.f;
+            if (tp.s != 0.f) {
+                const float ybar = -bbar / tp.kappa;
+                eps_bar += tp.s * ybar;
+                wl_bar += (ybar * tp.beta) * (nrm[j] - 1.f);
+                wl_bar += ybar * (tp.dotw - tp.gauss);
+                sig_bar += ybar * a.wG * tp.gd2 * inv_s3;
+                cwo = ybar * a.wL;
+                cgo = ybar * a.wG;
+            }
+            ca[lane] = cwo;
+            cb[lane] = cgo;
+        }
+        __syncwarp();
+        if (lane < nJ) gam[jlo + lane] += cb[lane];
+        const int s_lo = slotR(n, jlo);
+        for (int m = lane; m < L2; m += 32) {
+            float acc = w[m];
+#pragma unroll
+            for (int o = 0; o < WM; ++o)
+                if (o < nJ) acc = fmaf(ca[o], xw[wrap(s_lo + o) * L2 + m], acc);
+            w[m] = acc;
+        }
+        const int t_lo = max(0, n - W), n_t = n - t_lo;
+        if (lane < n_t) {
+            const int j = t_lo + lane, r = slotW(n, j), sj = slotR(n, j) * WR;
+            float acc;
+            bool alive = true;
+            if (j == je) {
+                acc = fa_je + gs + ls;
+                alive = n < evict_step(j);
+            } else {
+                acc = py[r];
+            }
+#pragma unroll
+            for (int o = 0; o < WM; ++o) {
+                if (o < nJ) {
+                    const int si = sj + wrap(s_lo + o);
+                    acc = fmaf(ca[o], kl[si], acc);
+                    if (alive) acc = fmaf(cb[o], kg[si], acc);
+                }
+            }
+            py[r] = acc;
+        }
+        __syncwarp();
+    }
+
+    for (int m = lane; m < M; m += 32) a.dclin0[m * K + k] = make_float2(w[m], w[M + m]);
+    // slot partials combined in slot order
+    float *red = py;  // py, pd, pw, pb: 4 W floats
+    if (lane < W) {
+        red[4 * lane + 0] = sig_bar;
+        red[4 * lane + 1] = mu_bar;
+        red[4 * lane + 2] = eps_bar;
+        red[4 * lane + 3] = wl_bar;
+    }
+    __syncwarp();
+    if (lane < 4) {
+        float s = 0.f;
+        for (int o = 0; o < W; ++o) s += red[4 * o + lane];
+        a.scal[k * 4 + lane] = s;
+    }
+}
+
+__global__ void train_bwd_sum_kernel(const TrainBwdArgs a0) {
+    const TrainBwdArgs a = for_instance(a0, blockIdx.y);
     if (threadIdx.x < 4) {
         float s = 0.f;
         for (int k = 0; k < a.K; ++k) s += a.scal[k * 4 + threadIdx.x];  // users in order
@@ -272,7 +975,8 @@ __global__ void train_bwd_sum_kernel(const TrainBwdArgs a) {
 }
 
 size_t train_bwd_smem(int M, int W, int P) {
-    return sizeof(float) * (size_t)(3 * 2 * P + 2 * 2 * M + 3 * W) + sizeof(Tape) * (size_t)kBwdSeg * W;
+    return sizeof(float) * (size_t)(2 * 2 * P + 2 * M + 6 * W + 3 * (kBwdThreads / 32) + 3 * (W + 1) * (W + 1) +
+                                    (W + 1) * 2 * M);
 }
 
 }  // namespace apsm
@@ -282,22 +986,24 @@ using namespace apsm;
 namespace {
 
 struct BwdLayout {
-    size_t ltab, gtab, ckpt, scal, total;
-    int n_seg;
+    size_t ltab, gtab, gdtab, tape, snap, scal, total;
 };
 
 BwdLayout bwd_layout(const apsm_params *p, int P) {
     BwdLayout b;
     const size_t S = 2 * (size_t)P;
-    b.n_seg = P > 0 ? (int)((S + kBwdSeg - 1) / kBwdSeg) : 0;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     b.ltab = off;
     off = al(off + sizeof(float) * S * S);
     b.gtab = off;
     off = al(off + sizeof(float) * S * S);
-    b.ckpt = off;
-    off = al(off + sizeof(float) * (size_t)p->K * b.n_seg * (2 * p->M + S));
+    b.gdtab = off;
+    off = al(off + sizeof(float) * S * S);
+    b.tape = off;
+    off = al(off + sizeof(Tape) * (size_t)p->K * S * p->window);
+    b.snap = off;
+    off = al(off + sizeof(float) * (size_t)p->K * (size_t)std::max(0, P - p->dict_cap) * p->window);
     b.scal = off;
     off = al(off + sizeof(float) * 4 * (size_t)p->K);
     b.total = off;
@@ -306,31 +1012,28 @@ BwdLayout bwd_layout(const apsm_params *p, int P) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-apsm_status apsm_train_backward_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes) {
-    size_t dummy = 0;
-    apsm_status s = apsm_train_workspace_bytes(p, 0, &dummy);  // parameter validation
-    if (s != APSM_OK) return s;
-    if (!bytes || P < 0) return APSM_ERR_INVALID_ARG;
-    *bytes = bwd_layout(p, P).total;
-    return APSM_OK;
-}
-
-apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
-                                const float *clin0, const float *dgamma, const float *dclin, float *dscalars,
-                                float *dclin0, void *workspace, size_t workspace_bytes, void *stream) {
+// The calls of one batch of n instances (n = 1 for apsm_train_backward).
+apsm_status train_bwd_run(const apsm_params *p, int n, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                          const float *clin0, const float *dgamma, const float *dclin, float *dscalars, float *dclin0,
+                          void *workspace, size_t workspace_bytes, void *stream) {
     size_t dummy = 0;
     apsm_status s = apsm_train_workspace_bytes(p, 0, &dummy);
     if (s != APSM_OK) return s;
-    if (P < 1 || !rx_pilot || !sym_pilot || !dgamma || !dclin || !dscalars || !dclin0) return APSM_ERR_INVALID_ARG;
+    if (n < 1 || n > 65535 || P < 1 || !rx_pilot || !sym_pilot || !dgamma || !dclin || !dscalars || !dclin0)
+        return APSM_ERR_INVALID_ARG;
     if (P > 8192) return APSM_ERR_UNSUPPORTED;
     if (p->weights != APSM_Q_UNIFORM) return APSM_ERR_UNSUPPORTED;  // the adjoint of q = 1/|J_n| only
     const BwdLayout b = bwd_layout(p, P);
-    if (!workspace || workspace_bytes < b.total) return APSM_ERR_WORKSPACE;
+    if (!workspace || workspace_bytes < b.total * (size_t)n) return APSM_ERR_WORKSPACE;
     if (reinterpret_cast<uintptr_t>(workspace) & 255) return APSM_ERR_INVALID_ARG;
     const size_t smem = train_bwd_smem(p->M, p->window, P);
-    if (smem > 227 * 1024) return APSM_ERR_UNSUPPORTED;
+    // one warp per user when the window fits the lanes and every user's rings fit one CTA
+    const size_t smem_w =
+        sizeof(float) * ((size_t)((2 * P + 3) & ~3) + (size_t)p->K * bwd_warp_floats(2 * P, p->window, 2 * p->M));
+    const bool warp_form = p->window <= 32 && smem_w <= 227 * 1024;
+    if (!warp_form && smem > 227 * 1024) return APSM_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -361,20 +1064,68 @@ apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, con
     a.dclin = reinterpret_cast<const float2 *>(dclin);
     a.ltab = reinterpret_cast<float *>(ws + b.ltab);
     a.gtab = reinterpret_cast<float *>(ws + b.gtab);
-    a.ckpt = reinterpret_cast<float *>(ws + b.ckpt);
+    a.gdtab = reinterpret_cast<float *>(ws + b.gdtab);
+    a.tape = reinterpret_cast<Tape *>(ws + b.tape);
+    a.snap = reinterpret_cast<float *>(ws + b.snap);
     a.scal = reinterpret_cast<float *>(ws + b.scal);
     a.dclin0 = reinterpret_cast<float2 *>(dclin0);
     a.dscalars = dscalars;
-    a.n_seg = b.n_seg;
+    a.st_rx = (size_t)P * p->M;
+    a.st_sym = (size_t)P * p->K;
+    a.st_clin0 = (size_t)p->M * p->K;
+    a.st_dgamma = (size_t)round_up(p->dict_cap, kTileEntries) * 2 * p->K;
+    a.st_mk = (size_t)p->M * p->K;
+    a.ws_stride = b.total;
     const long long pairs = 4LL * P * P;
-    const int blocks = (int)std::min<long long>(4096, (pairs + 255) / 256);
-    train_bwd_tables_kernel<<<blocks, 256, 0, strm>>>(a);
-    if (cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return APSM_ERR_CUDA;
-    train_bwd_kernel<<<p->K, kBwdThreads, smem, strm>>>(a);
-    train_bwd_sum_kernel<<<1, 32, 0, strm>>>(a);
+    const int blocks = (int)std::min<long long>(std::max(1, 4096 / n), (pairs + 255) / 256);
+    train_bwd_tables_kernel<<<dim3(blocks, n), 256, 0, strm>>>(a);
+    if (warp_form) {
+        auto kern = p->window <= 8 ? train_bwd_warp_kernel<8>
+                    : p->window <= 16 ? train_bwd_warp_kernel<16> : train_bwd_warp_kernel<32>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_w) != cudaSuccess)
+            return APSM_ERR_CUDA;
+        kern<<<dim3(1, n), 32 * p->K, smem_w, strm>>>(a);
+    } else {
+        if (cudaFuncSetAttribute(train_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return APSM_ERR_CUDA;
+        train_bwd_kernel<<<dim3(p->K, n), kBwdThreads, smem, strm>>>(a);
+    }
+    train_bwd_sum_kernel<<<dim3(1, n), 32, 0, strm>>>(a);
     g_launches += 3;
     return cudaGetLastError() == cudaSuccess ? APSM_OK : APSM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+apsm_status apsm_train_backward_workspace_bytes(const apsm_params *p, int32_t P, size_t *bytes) {
+    return apsm_train_backward_batched_workspace_bytes(p, P, 1, bytes);
+}
+
+apsm_status apsm_train_backward_batched_workspace_bytes(const apsm_params *p, int32_t P, int32_t n, size_t *bytes) {
+    size_t dummy = 0;
+    apsm_status s = apsm_train_workspace_bytes(p, 0, &dummy);  // parameter validation
+    if (s != APSM_OK) return s;
+    if (!bytes || P < 0 || n < 1) return APSM_ERR_INVALID_ARG;
+    *bytes = bwd_layout(p, P).total * (size_t)n;
+    return APSM_OK;
+}
+
+apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, const float *sym_pilot, int32_t P,
+                                const float *clin0, const float *dgamma, const float *dclin, float *dscalars,
+                                float *dclin0, void *workspace, size_t workspace_bytes, void *stream) {
+    return train_bwd_run(p, 1, rx_pilot, sym_pilot, P, clin0, dgamma, dclin, dscalars, dclin0, workspace,
+                         workspace_bytes, stream);
+}
+
+apsm_status apsm_train_backward_batched(const apsm_params *p, int32_t n, const float *rx_pilot, const float *sym_pilot,
+                                        int32_t P, const float *clin0, const float *dgamma, const float *dclin,
+                                        float *dscalars, float *dclin0, void *workspace, size_t workspace_bytes,
+                                        void *stream) {
+    return train_bwd_run(p, n, rx_pilot, sym_pilot, P, clin0, dgamma, dclin, dscalars, dclin0, workspace,
+                         workspace_bytes, stream);
 }
 
 }  // extern "C"

@@ -1,5 +1,5 @@
 """Adjoint of the training recurrence: gradients of an MSE detection loss with respect to sigma,
-mu, eps, w_L and the initial linear filter, through training (checkpointed reverse sweep) and
+mu, eps, w_L and the initial linear filter, through training (reverse sweep of the recurrence) and
 detection, against FP64 central finite differences of the oracle.  A finite difference is used
 only where no branch of Eq. beta flips between the two perturbed runs (the loss has kinks
 there); the number of usable checks is asserted."""
@@ -16,11 +16,11 @@ pytestmark = pytest.mark.gpu
 
 CASES = [
     # M, K, P, W, D, N, sigma, mu, eps, w_L
-    (4, 2, 40, 4, 40, 150, 0.6, 0.5, 0.05, 0.5),     # no eviction, two checkpoint segments
+    (4, 2, 40, 4, 40, 150, 0.6, 0.5, 0.05, 0.5),     # no eviction
     (4, 2, 70, 6, 12, 150, 0.6, 0.7, 0.05, 0.4),     # FIFO eviction
     (8, 3, 33, 3, 33, 120, 0.5, 0.9, 0.02, 0.6),     # (mu = 1 lands residuals exactly on the slab edge)
-    (16, 6, 256, 8, 256, 512, 0.5, 0.5, 0.01, 0.5),  # the differentiation-form shape: 8 checkpoint
-                                                     # segments, one warp per window slot at W = 8
+    (16, 6, 256, 8, 256, 512, 0.5, 0.5, 0.01, 0.5),  # the differentiation-form shape (one warp per user)
+    (4, 2, 40, 36, 40, 150, 0.6, 0.5, 0.05, 0.5),    # window above 32 slots: one CTA per user
 ]
 
 
@@ -118,3 +118,26 @@ def test_grad_batch_equals_instances_one_at_a_time():
         assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max()), (got, ref)
         dc = (one.dclin0[i] - cg.grad).abs().max().item()
         assert dc <= 1e-4 * max(1.0, cg.grad.abs().max().item())
+
+
+@pytest.mark.parametrize("M,K,P,W,D", [(8, 3, 70, 6, 12), (16, 6, 64, 8, 64), (4, 2, 33, 5, 3), (4, 2, 60, 32, 30),
+                                        (4, 2, 60, 40, 21)])
+def test_train_backward_batched_equals_single_calls(M, K, P, W, D):
+    """apsm_train_backward_batched (one launch per kernel over users x instances) gives each
+    instance's gradients bit for bit as its own apsm_train_backward call (FIFO eviction included;
+    2D = W + 1 in two cases; W = 32 is the widest window of the warp-per-user form, W = 40 runs the
+    CTA-per-user form)."""
+    n = 5
+    p = apsm.Params(M=M, K=K, window=W, dict_cap=D, sigma=0.6, mu=0.7, eps=0.02, w_L=0.4)
+    xs = [synth.make_instance(M, K, P, 16, 10.0, instance=950 + i) for i in range(n)]
+    rp = torch.stack([to_dev(x.rx_pilot) for x in xs])
+    sp = torch.stack([to_dev(x.sym_pilot) for x in xs])
+    g = torch.Generator(device="cpu").manual_seed(5)
+    A = apsm.dict_alloc(p)
+    dg = (0.1 * torch.randn((n, A, 2, K), generator=g)).cuda()
+    dc = (0.1 * torch.randn((n, M, K), dtype=torch.complex64, generator=g)).cuda()
+    c0 = (0.05 * torch.randn((n, M, K), dtype=torch.complex64, generator=g)).cuda()
+    ds, dc0 = apsm.train_backward_batched(p, rp, sp, dg, dc, clin0=c0)
+    for i in range(n):
+        ds1, dc01 = apsm.train_backward(p, rp[i], sp[i], dg[i], dc[i], clin0=c0[i])
+        assert torch.equal(ds[i], ds1) and torch.equal(dc0[i], dc01), i
