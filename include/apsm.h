@@ -343,6 +343,24 @@ apsm_status apsm_train_backward_batched(const apsm_params *p, int32_t n, const f
                                         void *stream);
 
 /*
+ * apsm_train_backward_batched in two calls on one workspace, so that the first can run before
+ * the loss gradient exists (e.g. beside the detection and its adjoint):
+ *   _forward: the kernel tables and the forward pass of the recurrence of every instance, whose
+ *             per-step terms it keeps in the workspace (arguments as for apsm_train_backward_batched);
+ *   _reverse: the reverse sweep over that workspace, given dgamma and dclin; the same results, bit
+ *             for bit, as apsm_train_backward_batched.
+ * rx_pilot, P, n and the parameters must be those of the _forward call on the same workspace, and
+ * _forward must precede _reverse in stream order.  All pointers DEVICE.
+ */
+apsm_status apsm_train_backward_batched_forward(const apsm_params *p, int32_t n, const float *rx_pilot,
+                                                const float *sym_pilot, int32_t P, const float *clin0,
+                                                void *workspace, size_t workspace_bytes, void *stream);
+apsm_status apsm_train_backward_batched_reverse(const apsm_params *p, int32_t n, const float *rx_pilot, int32_t P,
+                                                const float *dgamma, const float *dclin, float *dscalars,
+                                                float *dclin0, void *workspace, size_t workspace_bytes,
+                                                void *stream);
+
+/*
  * Load a given filter into a state (detection with fixed, externally trained coefficients):
  * entries [n][M] complex, gamma [n][2][K], clin [M][K] complex and target [n][K] complex (the
  * entries' training targets, read only if training continues from this state; NULL: zero), all

@@ -87,6 +87,8 @@ def load_library(path: str | None = None):
         lib.apsm_train_backward.argtypes = [P, vp, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.apsm_train_backward_batched_workspace_bytes.argtypes = [P, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
         lib.apsm_train_backward_batched.argtypes = [P, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
+        lib.apsm_train_backward_batched_forward.argtypes = [P, i32, vp, vp, i32, vp, vp, ctypes.c_size_t, vp]
+        lib.apsm_train_backward_batched_reverse.argtypes = [P, i32, vp, i32, vp, vp, vp, vp, vp, ctypes.c_size_t, vp]
         lib.apsm_tune_set.argtypes = [i32, i32, i32, i32, i32, i32, i32]
         lib.apsm_tune_clear.argtypes = []
         lib.apsm_batch_workspace_bytes.argtypes = [ctypes.POINTER(_CInstance), i32, ctypes.POINTER(ctypes.c_size_t)]
@@ -104,6 +106,7 @@ def load_library(path: str | None = None):
                   "apsm_detect_backward", "apsm_tune_set", "apsm_tune_clear", "apsm_batch_create",
                   "apsm_train_backward_workspace_bytes", "apsm_train_backward",
                   "apsm_train_backward_batched_workspace_bytes", "apsm_train_backward_batched",
+                  "apsm_train_backward_batched_forward", "apsm_train_backward_batched_reverse",
                   "apsm_batch_launch", "apsm_batch_destroy", "apsm_check_wait_timeout",
                   "apsm_train_continue_workspace_bytes", "apsm_train_continue", "apsm_linear_init",
                   "apsm_set_option", "apsm_batch_workspace_bytes", "apsm_batch_launch_detect",
@@ -457,6 +460,44 @@ def train_backward_batched(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.T
     return dscalars, dclin0
 
 
+def train_backward_batched_forward(p: Params, rx_pilot: torch.Tensor, sym_pilot: torch.Tensor,
+                                   workspace: torch.Tensor, *, clin0: torch.Tensor | None = None):
+    """apsm_train_backward_batched_forward: the tables and the forward pass of the training
+    adjoint of n instances, kept in `workspace` for train_backward_batched_reverse."""
+    lib = load_library()
+    n, P = int(rx_pilot.shape[0]), int(rx_pilot.shape[1])
+    _dev(rx_pilot, torch.complex64, (n, P, p.M), "rx_pilot")
+    _dev(sym_pilot, torch.complex64, (n, P, p.K), "sym_pilot")
+    if clin0 is not None:
+        _dev(clin0, torch.complex64, (n, p.M, p.K), "clin0")
+    _check(lib.apsm_train_backward_batched_forward(ctypes.byref(p.c()), n, _ptr(rx_pilot), _ptr(sym_pilot), P,
+                                                   _ptr(clin0), _ptr(workspace), workspace.numel(), _stream()),
+           "apsm_train_backward_batched_forward")
+
+
+def train_backward_batched_reverse(p: Params, rx_pilot: torch.Tensor, dgamma: torch.Tensor, dclin: torch.Tensor,
+                                   workspace: torch.Tensor, *, dscalars: torch.Tensor | None = None,
+                                   dclin0: torch.Tensor | None = None):
+    """apsm_train_backward_batched_reverse: the reverse sweep over a workspace filled by
+    train_backward_batched_forward; returns (dscalars [n][4], dclin0 [n][M][K])."""
+    lib = load_library()
+    n, P = int(rx_pilot.shape[0]), int(rx_pilot.shape[1])
+    _dev(rx_pilot, torch.complex64, (n, P, p.M), "rx_pilot")
+    _dev(dgamma, torch.float32, (n, dict_alloc(p), 2, p.K), "dgamma")
+    _dev(dclin, torch.complex64, (n, p.M, p.K), "dclin")
+    if dscalars is None:
+        dscalars = torch.empty((n, 4), dtype=torch.float32, device=rx_pilot.device)
+    if dclin0 is None:
+        dclin0 = torch.empty((n, p.M, p.K), dtype=torch.complex64, device=rx_pilot.device)
+    _dev(dscalars, torch.float32, (n, 4), "dscalars")
+    _dev(dclin0, torch.complex64, (n, p.M, p.K), "dclin0")
+    _check(lib.apsm_train_backward_batched_reverse(ctypes.byref(p.c()), n, _ptr(rx_pilot), P, _ptr(dgamma),
+                                                   _ptr(dclin), _ptr(dscalars), _ptr(dclin0), _ptr(workspace),
+                                                   workspace.numel(), _stream()),
+           "apsm_train_backward_batched_reverse")
+    return dscalars, dclin0
+
+
 class TrainDetectFunction(torch.autograd.Function):
     """soft = detect(train(pilots; c_0, sigma, mu, eps, w_L), rx): the APSM recurrence unrolled over
     the pilots and the detection of the data vectors, differentiable with respect to the initial
@@ -494,10 +535,11 @@ class GradBatch:
     dsoft = 2 (soft - target), apsm_detect_backward, apsm_train_backward) of many independent
     instances with the same parameters, on `lanes` CUDA streams with no host synchronisation
     between instances; with graph=True the whole pass is captured once and replayed as one CUDA
-    graph.  When every instance has the same pilot count, the training adjoints run as
-    apsm_train_backward_batched calls over chunks of `chunk` instances (default: all of them), each
-    on its own stream as soon as its instances' detection adjoints are done, so that they overlap
-    the per-instance work of the next chunks.  Every buffer is allocated here, once.  Per-instance results stay on the device:
+    graph.  When every instance has the same pilot count, the training adjoints run batched over
+    chunks of `chunk` instances (default: all of them), each chunk on a stream of its own: the
+    forward part (apsm_train_backward_batched_forward, which needs only the pilots) from the
+    start, beside the per-instance work, and the reverse sweep as soon as the chunk's detection
+    adjoints are done.  Every buffer is allocated here, once.  Per-instance results stay on the device:
     loss [n] (sum |soft - target|^2), dscalars [n][4] (d sigma, d mu, d eps, d w_L) and
     dclin0 [n][M][K]; grads() sums them over the instances in instance order.  Each instance's
     results equal those of the same calls made one instance at a time, bit for bit.
@@ -588,15 +630,21 @@ class GradBatch:
         self.dst[i, 0] += b["dsd"][0]
         self.dst[i, 3] += b["dsd"][1]
 
-    def _chunk_backward(self, lo, hi):
-        """Training adjoints of instances lo..hi-1 in one batched call (on the current stream)."""
+    def _chunk_forward(self, lo, hi):
+        """Forward part of the training adjoints of instances lo..hi-1 (on the current stream)."""
         sl = slice(lo, hi)
         torch.stack([x[0] for x in self.inst[sl]], out=self.rxp_all[sl])
         torch.stack([x[1] for x in self.inst[sl]], out=self.symp_all[sl])
         self.clin0_all[sl].copy_(self.clin0.expand_as(self.clin0_all[sl]))
-        ws = self.ws_bb[lo * self.ws_per:hi * self.ws_per]
-        train_backward_batched(self.p, self.rxp_all[sl], self.symp_all[sl], self.dgamma[sl], self.dclin[sl],
-                               clin0=self.clin0_all[sl], workspace=ws, dscalars=self.dst[sl], dclin0=self.dclin0[sl])
+        train_backward_batched_forward(self.p, self.rxp_all[sl], self.symp_all[sl],
+                                       self.ws_bb[lo * self.ws_per:hi * self.ws_per], clin0=self.clin0_all[sl])
+
+    def _chunk_reverse(self, lo, hi):
+        """Reverse sweep of the training adjoints of instances lo..hi-1 (on the current stream)."""
+        sl = slice(lo, hi)
+        train_backward_batched_reverse(self.p, self.rxp_all[sl], self.dgamma[sl], self.dclin[sl],
+                                       self.ws_bb[lo * self.ws_per:hi * self.ws_per], dscalars=self.dst[sl],
+                                       dclin0=self.dclin0[sl])
         self.dst[sl, 0] += self.dsd[sl, 0]  # sigma and w_L also enter through the detection
         self.dst[sl, 3] += self.dsd[sl, 1]
 
@@ -606,13 +654,16 @@ class GradBatch:
             s.wait_stream(main)
         if self.batched:
             for (lo, hi), bs in zip(self.chunks, self.bstreams):
+                with torch.cuda.stream(bs):
+                    self._chunk_forward(lo, hi)
+            for (lo, hi), bs in zip(self.chunks, self.bstreams):
                 for i in range(lo, hi):
                     with torch.cuda.stream(self.streams[i % self.lanes]):
                         self._instance(i)
                 for i in range(lo, hi):
                     bs.wait_stream(self.streams[i % self.lanes])
                 with torch.cuda.stream(bs):
-                    self._chunk_backward(lo, hi)
+                    self._chunk_reverse(lo, hi)
         else:
             for i in range(len(self.inst)):
                 with torch.cuda.stream(self.streams[i % self.lanes]):

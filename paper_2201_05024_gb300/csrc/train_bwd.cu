@@ -47,15 +47,16 @@ struct Tape {  // one window slot of one step
 
 struct TrainBwdArgs {
     int M, K, W, D, P;
+    int Sp;                 // row stride of the tables: 2P rounded up to a multiple of 4
     float sigma, mu, eps, wL, wG, k2;
     const float2 *rx;       // [P][M]
     const float2 *sym;      // [P][K]
     const float2 *clin0;    // [M][K] or null
     const float *dgamma;    // [A][2][K] adjoint of the final coefficients (ring layout)
     const float2 *dclin;    // [M][K] adjoint of the final linear filter
-    float *ltab;            // [2P][2P] x_i . x_j
-    float *gtab;            // [2P][2P] kappa_G(x_i, x_j)
-    float *gdtab;           // [2P][2P] kappa_G(x_i, x_j) ||x_i - x_j||^2
+    float *ltab;            // [2P][Sp] x_i . x_j
+    float *gtab;            // [2P][Sp] kappa_G(x_i, x_j)
+    float *gdtab;           // [2P][Sp] kappa_G(x_i, x_j) ||x_i - x_j||^2
     Tape *tape;             // [K][2P][W]
     float *snap;            // [K][P - D][W] R at the eviction steps (P > D only)
     float *scal;            // [K][4] per-user sigma, mu, eps, w_L adjoints
@@ -64,6 +65,7 @@ struct TrainBwdArgs {
     // instance i of a batch: the pointers above advanced by i times these (elements; ws_stride in
     // bytes for the workspace regions ltab, gtab, gdtab, tape, snap, scal)
     size_t st_rx, st_sym, st_clin0, st_dgamma, st_mk, ws_stride;
+    int mode;  // 1: tables' forward pass (tape), 2: reverse sweep, 3: both
 };
 
 // The arguments of instance i (blockIdx.y of every launch below).
@@ -88,10 +90,16 @@ __device__ __forceinline__ TrainBwdArgs for_instance(const TrainBwdArgs &a0, int
 
 __global__ void train_bwd_tables_kernel(const TrainBwdArgs a0) {
     const TrainBwdArgs a = for_instance(a0, blockIdx.y);
-    const int S = 2 * a.P;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)S * S;
+    const int S = 2 * a.P, Sp = a.Sp;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < (long long)S * Sp;
          idx += (long long)gridDim.x * blockDim.x) {
-        const int i0 = (int)(idx / S), j0 = (int)(idx % S);
+        const int i0 = (int)(idx / Sp), j0 = (int)(idx % Sp);
+        if (j0 >= S) {  // row padding
+            a.ltab[idx] = 0.f;
+            a.gtab[idx] = 0.f;
+            a.gdtab[idx] = 0.f;
+            continue;
+        }
         const int i = min(i0, j0), j = max(i0, j0);  // both halves from one ordering: exactly symmetric
         float dot, d2;
         sample_pair(a.rx + (size_t)(i >> 1) * a.M, a.rx + (size_t)(j >> 1) * a.M, a.M, i & 1, j & 1, dot, d2);
@@ -131,14 +139,20 @@ __device__ __forceinline__ int ring_slot(int b, int off, int R) {
 
 // Loads issued a step ahead of their use: predicated rather than followed by a select, so that no
 // instruction waits on the data before it is used; volatile, so that they stay ahead of the barriers.
+// (the predicate is set inside the asm, so no branch surrounds the load)
 __device__ __forceinline__ float ldg_if(bool c, const float *p) {  // read-only data of earlier kernels
     float v = 0.f;
-    if (c) asm volatile("ld.global.nc.f32 %0, [%1];" : "+f"(v) : "l"(p));
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q ld.global.nc.f32 %0, [%1];\n\t}"
+                 : "+f"(v)
+                 : "l"(p), "r"((int)c));
     return v;
 }
-__device__ __forceinline__ float ld_if(bool c, const float *p) {  // data this kernel wrote
-    float v = 0.f;
-    if (c) asm volatile("ld.global.f32 %0, [%1];" : "+f"(v) : "l"(p) : "memory");
+__device__ __forceinline__ float2 ld2_if(bool c, const float *p) {  // data this kernel wrote; 8-byte aligned
+    float2 v = make_float2(0.f, 0.f);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q ld.global.v2.f32 {%0, %1}, [%2];\n\t}"
+                 : "+f"(v.x), "+f"(v.y)
+                 : "l"(p), "r"((int)c)
+                 : "memory");
     return v;
 }
 
@@ -173,7 +187,7 @@ __device__ __forceinline__ void band_fetch(BandPf &b, const TrainBwdArgs &a, int
     for (int q = 0; q < 2; ++q) {
         const int t = (int)threadIdx.x + q * kBwdThreads, j = s0 + t;
         const bool ok = r >= 0 && r < S && t <= W && j >= 0 && j < S;
-        const size_t x = ok ? (size_t)r * S + j : 0;
+        const size_t x = ok ? (size_t)r * a.Sp + j : 0;
         b.g[q] = ldg_if(ok, a.gtab + x);
         b.d[q] = ldg_if(ok, a.gdtab + x);
         b.l[q] = ldg_if(ok, a.ltab + x);
@@ -258,7 +272,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
 
     for (int i = tid; i < S; i += T) {
         gam[i] = 0.f;
-        nrm[i] = a.ltab[(size_t)i * S + i];  // ||x_i||^2
+        nrm[i] = a.ltab[(size_t)i * a.Sp + i];  // ||x_i||^2
     }
     for (int m = tid; m < M; m += T) {
         const float2 c = a.clin0 ? a.clin0[m * K + k] : make_float2(0.f, 0.f);
@@ -267,14 +281,16 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
     }
     RowPf pf;
     BandPf bp;
+    float xn = 0.f;
+    if (a.mode & 1) {
     sW = pmod(-W - 1, W);
     sR = pmod(-W - 1, WR);
     band_fetch(bp, a, S, W, 0, -W);
     band_store(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W));
     band_fetch(bp, a, S, W, 1, 1 - W);
-    if (S > 1) row_fetch(pf, a.gtab + S, a.gdtab + S, first_centre(1), 1);
+    if (S > 1) row_fetch(pf, a.gtab + a.Sp, a.gdtab + a.Sp, first_centre(1), 1);
     if (tid < L2) xw[slotR(0, 0) * L2 + tid] = xcomp(a.rx, M, 0, tid);
-    float xn = xc(1);
+    xn = xc(1);
     float bn = target_at(tid == T - 1 && S > 1, 1);  // the target of the next arrival, a step early
     if (tid == 0) pb[0] = target_at(true, 0);
     __syncthreads();
@@ -307,7 +323,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
                 xn = xc(jn + 1);
             }
             const int lo = first_centre(jn);
-            const float *grow = a.gtab + (size_t)jn * S, *drow = a.gdtab + (size_t)jn * S;
+            const float *grow = a.gtab + (size_t)jn * a.Sp, *drow = a.gdtab + (size_t)jn * a.Sp;
             float ys = 0.f, ds = 0.f;
 #pragma unroll
             for (int q = 0; q < kPf; ++q) {
@@ -323,7 +339,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
             }
             reduce3(ys, ds, ws);
             if (jn + 1 < S)
-                row_fetch(pf, a.gtab + (size_t)(jn + 1) * S, a.gdtab + (size_t)(jn + 1) * S, first_centre(jn + 1),
+                row_fetch(pf, a.gtab + (size_t)(jn + 1) * a.Sp, a.gdtab + (size_t)(jn + 1) * a.Sp, first_centre(jn + 1),
                           jn + 1);
         }
         // the window's projections (Eq. beta), all from f_n
@@ -382,7 +398,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
                     }
                 }
                 if (j != jn) {
-                    const float *grow = a.gtab + (size_t)j * S, *drow = a.gdtab + (size_t)j * S;
+                    const float *grow = a.gtab + (size_t)j * a.Sp, *drow = a.gdtab + (size_t)j * a.Sp;
                     for (int i = e_lo; i < e_hi; ++i) {  // centres leaving before step n+1
                         const float gi = i >= jlo ? cb[i - jlo] : gam[i];
                         ay = fmaf(-gi, __ldg(grow + i), ay);
@@ -397,8 +413,25 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
         __syncthreads();
     }
 
+    }  // forward
+    if (!(a.mode & 2)) return;
+
     // ---- reverse sweep: R = 0, wbar = dL/dw of the final state ------------------------------------
-    // (kg, kl and xw still hold the last W + 1 samples)
+    __syncthreads();
+    {  // kernel values and components of the last W + 1 samples (as the forward left them)
+        const int j0 = max(0, S - W - 1), nr = S - j0;
+        for (int t = tid; t < nr * nr; t += T) {
+            const int i = j0 + t / nr, j = j0 + t % nr;
+            const size_t x = (size_t)i * a.Sp + j;
+            const int u = (i % WR) * WR + j % WR;
+            kg[u] = a.gtab[x];
+            kl[u] = a.ltab[x];
+        }
+        for (int t = tid; t < nr * L2; t += T) {
+            const int j = j0 + t / L2, m = t % L2;
+            xw[(j % WR) * L2 + m] = xcomp(a.rx, M, j, m);
+        }
+    }
     for (int i = tid; i < S; i += T) gam[i] = 0.f;
     for (int m = tid; m < M; m += T) {
         const float2 d = a.dclin[m * K + k];
@@ -423,7 +456,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
         py[j % W] = d + final_at(j);
     }
     const int je0 = S - 1 - W;  // the first entrant
-    if (je0 >= 0) row_fetch(pf, a.gtab + (size_t)je0 * S, nullptr, je0 + 2, pull_hi(S - 1));
+    if (je0 >= 0) row_fetch(pf, a.gtab + (size_t)je0 * a.Sp, nullptr, je0 + 2, pull_hi(S - 1));
     band_fetch(bp, a, S, W, je0, je0);
     xn = xc(je0);
     const int t_fa = L2 % T;  // the thread that updates the entrant's abar
@@ -431,12 +464,8 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
     Tape tnext;
     auto tape_at = [&](Tape &t, bool ok, int n) {
         const float *f = reinterpret_cast<const float *>(tape + (ok ? (size_t)n * W + tid : 0));
-        t.beta = ld_if(ok, f);
-        t.s = ld_if(ok, f + 1);
-        t.kappa = ld_if(ok, f + 2);
-        t.dotw = ld_if(ok, f + 3);
-        t.gauss = ld_if(ok, f + 4);
-        t.gd2 = ld_if(ok, f + 5);
+        const float2 u0 = ld2_if(ok, f), u1 = ld2_if(ok, f + 2), u2 = ld2_if(ok, f + 4);
+        t = Tape{u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
     };
     if (tid < W) tape_at(tnext, tid < S - max(0, S - W), S - 1);
     sW = pmod(S - 1 - W - 1, W);
@@ -474,7 +503,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
             const int lo = je + 2, hi = pull_hi(n), e = evict_step(je);
             const int s_lo = e <= S - 1 ? e - W + 1 : S;  // centres whose R holds steps >= e
             const float *sv = snap + (size_t)((e >> 1) - D) * W;
-            const float *grow = a.gtab + (size_t)je * S;
+            const float *grow = a.gtab + (size_t)je * a.Sp;
             float gs = 0.f;
 #pragma unroll
             for (int qq = 0; qq < kPf; ++qq) {
@@ -484,7 +513,7 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
             for (int i = lo + tid + kPf * T; i < hi; i += T)
                 gs = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], __ldg(grow + i), gs);
             reduce3(gs, ls, 0.f);
-            if (je - 1 >= 0) row_fetch(pf, a.gtab + (size_t)(je - 1) * S, nullptr, je + 1, pull_hi(n - 1));
+            if (je - 1 >= 0) row_fetch(pf, a.gtab + (size_t)(je - 1) * a.Sp, nullptr, je + 1, pull_hi(n - 1));
         }
         if (tid < nJ) {  // slot tid: its scalar terms and its coefficients for the state adjoint
             const Tape tp = tnext;
@@ -563,21 +592,34 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
 // The same recurrence and adjoint as train_bwd_kernel, for windows of at most 32 slots: one warp
 // per user (lane o = window slot o), the users of one instance in one CTA, and no block barrier
 // inside the step loop -- each step synchronises one warp only.  The O(S) sums of a step take
-// kPfW entries per lane from registers loaded a step ahead (the rest directly).
-constexpr int kPfW = 16;
+// 4 kPfV entries per lane (float4 loads) from registers loaded a step ahead (the rest directly).
+constexpr int kPfV = 4;  // float4 of a row per lane and table fetched a step ahead (512 entries)
 
+__device__ __forceinline__ float4 ldg4_if(bool c, const float *p) {  // p 16-byte aligned
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];\n\t}"
+                 : "+f"(v.x), "+f"(v.y), "+f"(v.z), "+f"(v.w)
+                 : "l"(p), "r"((int)c));
+    return v;
+}
+
+// Entries lo4 + 4 (lane + 32 q) + 0..3 (q < kPfV, lo4 = lo rounded down to a multiple of 4, the
+// first of the four below hi) of one or two table rows (rows are padded to a multiple of 4 floats).
 struct RowPfW {
-    float g[kPfW], d[kPfW];
+    float4 g[kPfV], d[kPfV];
 };
 
 __device__ __forceinline__ void row_fetch_w(RowPfW &f, const float *grow, const float *drow, int lo, int hi, int lane) {
+    const int lo4 = lo & ~3;
 #pragma unroll
-    for (int q = 0; q < kPfW; ++q) {
-        const int i = lo + lane + 32 * q;
-        f.g[q] = ldg_if(i < hi, grow + i);
-        f.d[q] = ldg_if(drow != nullptr && i < hi, drow + i);
+    for (int q = 0; q < kPfV; ++q) {
+        const int i0 = lo4 + 4 * (lane + 32 * q);
+        f.g[q] = ldg4_if(i0 < hi, grow + i0);
+        f.d[q] = ldg4_if(drow != nullptr && i0 < hi, drow + i0);
     }
 }
+
+__device__ __forceinline__ float f4(const float4 &v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
 
 // band of row r, entries s0 + t for t = lane (and lane + 32 when W = 32), inside [0, S)
 template <int NQ>
@@ -586,7 +628,7 @@ __device__ __forceinline__ void band_fetch_w(BandPf &b, const TrainBwdArgs &a, i
     for (int q = 0; q < NQ; ++q) {
         const int t = lane + 32 * q, j = s0 + t;
         const bool ok = r >= 0 && r < S && t <= W && j >= 0 && j < S;
-        const size_t x = ok ? (size_t)r * S + j : 0;
+        const size_t x = ok ? (size_t)r * a.Sp + j : 0;
         b.g[q] = ldg_if(ok, a.gtab + x);
         b.d[q] = ldg_if(ok, a.gdtab + x);
         b.l[q] = ldg_if(ok, a.ltab + x);
@@ -656,7 +698,7 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
         return ldg_if(ok, reinterpret_cast<const float *>(a.sym + (ok ? (size_t)(j >> 1) * K + k : 0)) + (j & 1));
     };
 
-    for (int i = threadIdx.x; i < S; i += blockDim.x) nrm[i] = a.ltab[(size_t)i * S + i];  // ||x_i||^2
+    for (int i = threadIdx.x; i < S; i += blockDim.x) nrm[i] = a.ltab[(size_t)i * a.Sp + i];  // ||x_i||^2
     __syncthreads();  // the only block barrier: nrm is shared by the users
     for (int i = lane; i < S; i += 32) gam[i] = 0.f;
     for (int m = lane; m < M; m += 32) {
@@ -667,12 +709,13 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
     RowPfW pf;
     BandPf bp;
     float xn[4];
+    if (a.mode & 1) {
     sW = pmod(-W - 1, W);
     sR = pmod(-W - 1, WR);
     band_fetch_w<NQ>(bp, a, S, W, 0, -W, lane);
     band_store_w<NQ>(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W), lane);
     band_fetch_w<NQ>(bp, a, S, W, 1, 1 - W, lane);
-    if (S > 1) row_fetch_w(pf, a.gtab + S, a.gdtab + S, first_centre(1), 1, lane);
+    if (S > 1) row_fetch_w(pf, a.gtab + a.Sp, a.gdtab + a.Sp, first_centre(1), 1, lane);
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const int m = lane + 32 * c;
@@ -715,25 +758,32 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
                     xn[c] = xc(jn + 1, m);
                 }
             }
-            const int lo = first_centre(jn);
+            const int lo = first_centre(jn), lo4 = lo & ~3;
             float y2[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // two chains of sums
 #pragma unroll
-            for (int q = 0; q < kPfW; ++q) {
-                const int i = lo + lane + 32 * q;
-                if (i < jn) {
-                    y2[q & 1] = fmaf(gam[i], pf.g[q], y2[q & 1]);
-                    d2[q & 1] = fmaf(gam[i], pf.d[q], d2[q & 1]);
+            for (int q = 0; q < kPfV; ++q) {
+                const int i0 = lo4 + 4 * (lane + 32 * q);
+                if (i0 < jn) {
+                    const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int i = i0 + e;
+                        if (i >= lo && i < jn) {
+                            y2[e & 1] = fmaf(f4(gm, e), f4(pf.g[q], e), y2[e & 1]);
+                            d2[e & 1] = fmaf(f4(gm, e), f4(pf.d[q], e), d2[e & 1]);
+                        }
+                    }
                 }
             }
-            const float *grow = a.gtab + (size_t)jn * S, *drow = a.gdtab + (size_t)jn * S;
-            for (int i = lo + lane + 32 * kPfW; i < jn; i += 32) {
+            const float *grow = a.gtab + (size_t)jn * a.Sp, *drow = a.gdtab + (size_t)jn * a.Sp;
+            for (int i = max(lo, lo4 + 4 * 32 * kPfV) + lane; i < jn; i += 32) {
                 y2[0] = fmaf(gam[i], __ldg(grow + i), y2[0]);
                 d2[0] = fmaf(gam[i], __ldg(drow + i), d2[0]);
             }
             ys = y2[0] + y2[1];
             ds = d2[0] + d2[1];
             if (jn + 1 < S)
-                row_fetch_w(pf, a.gtab + (size_t)(jn + 1) * S, a.gdtab + (size_t)(jn + 1) * S, first_centre(jn + 1),
+                row_fetch_w(pf, a.gtab + (size_t)(jn + 1) * a.Sp, a.gdtab + (size_t)(jn + 1) * a.Sp, first_centre(jn + 1),
                             jn + 1, lane);
             ys = warp_sum(ys);
             ds = warp_sum(ds);
@@ -795,7 +845,7 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
                 }
             }
             if (j != jn) {
-                const float *grow = a.gtab + (size_t)j * S, *drow = a.gdtab + (size_t)j * S;
+                const float *grow = a.gtab + (size_t)j * a.Sp, *drow = a.gdtab + (size_t)j * a.Sp;
                 for (int i = e_lo; i < e_hi; ++i) {
                     const float gi = i >= jlo ? cb[i - jlo] : gam[i];
                     ay = fmaf(-gi, __ldg(grow + i), ay);
@@ -809,7 +859,25 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
         __syncwarp();
     }
 
+    }  // forward
+    if (!(a.mode & 2)) return;
+
     // ---- reverse sweep ---------------------------------------------------------------------------------
+    {  // kernel values and components of the last W + 1 samples (as the forward left them)
+        const int j0 = max(0, S - W - 1), nr = S - j0;
+        for (int t = lane; t < nr * nr; t += 32) {
+            const int i = j0 + t / nr, j = j0 + t % nr;
+            const size_t x = (size_t)i * a.Sp + j;
+            const int u = (i % WR) * WR + j % WR;
+            kg[u] = a.gtab[x];
+            kl[u] = a.ltab[x];
+        }
+        for (int t = lane; t < nr * L2; t += 32) {
+            const int j = j0 + t / L2, m = t % L2;
+            xw[(j % WR) * L2 + m] = xcomp(a.rx, M, j, m);
+        }
+    }
+    __syncwarp();
     for (int i = lane; i < S; i += 32) gam[i] = 0.f;  // R
     for (int m = lane; m < M; m += 32) {
         const float2 d = a.dclin[m * K + k];
@@ -833,7 +901,7 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
         py[j % W] = d + final_at(j);
     }
     const int je0 = S - 1 - W;
-    if (je0 >= 0) row_fetch_w(pf, a.gtab + (size_t)je0 * S, nullptr, je0 + 2, pull_hi(S - 1), lane);
+    if (je0 >= 0) row_fetch_w(pf, a.gtab + (size_t)je0 * a.Sp, nullptr, je0 + 2, pull_hi(S - 1), lane);
     band_fetch_w<NQ>(bp, a, S, W, je0, je0, lane);
 #pragma unroll
     for (int c = 0; c < 4; ++c) xn[c] = xc(je0, lane + 32 * c);
@@ -841,12 +909,8 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
     Tape tnext;
     auto tape_at = [&](Tape &t, bool ok, int n) {
         const float *f = reinterpret_cast<const float *>(tape + (ok ? (size_t)n * W + lane : 0));
-        t.beta = ld_if(ok, f);
-        t.s = ld_if(ok, f + 1);
-        t.kappa = ld_if(ok, f + 2);
-        t.dotw = ld_if(ok, f + 3);
-        t.gauss = ld_if(ok, f + 4);
-        t.gd2 = ld_if(ok, f + 5);
+        const float2 u0 = ld2_if(ok, f), u1 = ld2_if(ok, f + 2), u2 = ld2_if(ok, f + 4);
+        t = Tape{u0.x, u0.y, u1.x, u1.y, u2.x, u2.y};
     };
     tape_at(tnext, lane < S - max(0, S - W), S - 1);
     sW = pmod(S - 1 - W - 1, W);
@@ -880,17 +944,28 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
             const int lo = je + 2, hi = pull_hi(n), e = evict_step(je);
             const int s_lo = e <= S - 1 ? e - W + 1 : S;
             const float *sv = snap + (size_t)((e >> 1) - D) * W;
-            const float *grow = a.gtab + (size_t)je * S;
+            const float *grow = a.gtab + (size_t)je * a.Sp;
+            const int lo4 = lo & ~3;
             float g2[2] = {0.f, 0.f};
 #pragma unroll
-            for (int qq = 0; qq < kPfW; ++qq) {
-                const int i = lo + lane + 32 * qq;
-                if (i < hi) g2[qq & 1] = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], pf.g[qq], g2[qq & 1]);
+            for (int qq = 0; qq < kPfV; ++qq) {
+                const int i0 = lo4 + 4 * (lane + 32 * qq);
+                if (i0 < hi) {
+                    const float4 rm = *reinterpret_cast<const float4 *>(gam + i0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int i = i0 + e;
+                        if (i >= lo && i < hi) {
+                            const float r = i >= s_lo ? f4(rm, e) - sv[i - s_lo] : f4(rm, e);
+                            g2[e & 1] = fmaf(r, f4(pf.g[qq], e), g2[e & 1]);
+                        }
+                    }
+                }
             }
-            for (int i = lo + lane + 32 * kPfW; i < hi; i += 32)
+            for (int i = max(lo, lo4 + 4 * 32 * kPfV) + lane; i < hi; i += 32)
                 g2[0] = fmaf(i >= s_lo ? gam[i] - sv[i - s_lo] : gam[i], __ldg(grow + i), g2[0]);
             gs = g2[0] + g2[1];
-            if (je - 1 >= 0) row_fetch_w(pf, a.gtab + (size_t)(je - 1) * S, nullptr, je + 1, pull_hi(n - 1), lane);
+            if (je - 1 >= 0) row_fetch_w(pf, a.gtab + (size_t)(je - 1) * a.Sp, nullptr, je + 1, pull_hi(n - 1), lane);
             gs = warp_sum(gs);
             ls = warp_sum(ls);
         }
@@ -994,12 +1069,13 @@ BwdLayout bwd_layout(const apsm_params *p, int P) {
     const size_t S = 2 * (size_t)P;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
+    const size_t Sp = (S + 3) & ~size_t(3);
     b.ltab = off;
-    off = al(off + sizeof(float) * S * S);
+    off = al(off + sizeof(float) * S * Sp);
     b.gtab = off;
-    off = al(off + sizeof(float) * S * S);
+    off = al(off + sizeof(float) * S * Sp);
     b.gdtab = off;
-    off = al(off + sizeof(float) * S * S);
+    off = al(off + sizeof(float) * S * Sp);
     b.tape = off;
     off = al(off + sizeof(Tape) * (size_t)p->K * S * p->window);
     b.snap = off;
@@ -1014,15 +1090,18 @@ BwdLayout bwd_layout(const apsm_params *p, int P) {
 
 namespace {
 
-// The calls of one batch of n instances (n = 1 for apsm_train_backward).
+// The calls of one batch of n instances (n = 1 for apsm_train_backward).  mode 1: the tables and
+// the forward pass (the tape, kept in the workspace); 2: the reverse sweep over a workspace that
+// mode 1 filled; 3: both.
 apsm_status train_bwd_run(const apsm_params *p, int n, const float *rx_pilot, const float *sym_pilot, int32_t P,
                           const float *clin0, const float *dgamma, const float *dclin, float *dscalars, float *dclin0,
-                          void *workspace, size_t workspace_bytes, void *stream) {
+                          void *workspace, size_t workspace_bytes, void *stream, int mode) {
     size_t dummy = 0;
     apsm_status s = apsm_train_workspace_bytes(p, 0, &dummy);
     if (s != APSM_OK) return s;
-    if (n < 1 || n > 65535 || P < 1 || !rx_pilot || !sym_pilot || !dgamma || !dclin || !dscalars || !dclin0)
-        return APSM_ERR_INVALID_ARG;
+    if (n < 1 || n > 65535 || P < 1 || !rx_pilot) return APSM_ERR_INVALID_ARG;
+    if ((mode & 1) && !sym_pilot) return APSM_ERR_INVALID_ARG;
+    if ((mode & 2) && (!dgamma || !dclin || !dscalars || !dclin0)) return APSM_ERR_INVALID_ARG;
     if (P > 8192) return APSM_ERR_UNSUPPORTED;
     if (p->weights != APSM_Q_UNIFORM) return APSM_ERR_UNSUPPORTED;  // the adjoint of q = 1/|J_n| only
     const BwdLayout b = bwd_layout(p, P);
@@ -1051,6 +1130,7 @@ apsm_status train_bwd_run(const apsm_params *p, int n, const float *rx_pilot, co
     a.W = p->window;
     a.D = p->dict_cap;
     a.P = P;
+    a.Sp = (2 * P + 3) & ~3;
     a.sigma = p->sigma;
     a.mu = p->mu;
     a.eps = p->eps;
@@ -1076,9 +1156,10 @@ apsm_status train_bwd_run(const apsm_params *p, int n, const float *rx_pilot, co
     a.st_dgamma = (size_t)round_up(p->dict_cap, kTileEntries) * 2 * p->K;
     a.st_mk = (size_t)p->M * p->K;
     a.ws_stride = b.total;
-    const long long pairs = 4LL * P * P;
+    a.mode = mode;
+    const long long pairs = 2LL * P * a.Sp;
     const int blocks = (int)std::min<long long>(std::max(1, 4096 / n), (pairs + 255) / 256);
-    train_bwd_tables_kernel<<<dim3(blocks, n), 256, 0, strm>>>(a);
+    if (mode & 1) train_bwd_tables_kernel<<<dim3(blocks, n), 256, 0, strm>>>(a);
     if (warp_form) {
         auto kern = p->window <= 8 ? train_bwd_warp_kernel<8>
                     : p->window <= 16 ? train_bwd_warp_kernel<16> : train_bwd_warp_kernel<32>;
@@ -1091,8 +1172,8 @@ apsm_status train_bwd_run(const apsm_params *p, int n, const float *rx_pilot, co
             return APSM_ERR_CUDA;
         train_bwd_kernel<<<dim3(p->K, n), kBwdThreads, smem, strm>>>(a);
     }
-    train_bwd_sum_kernel<<<dim3(1, n), 32, 0, strm>>>(a);
-    g_launches += 3;
+    if (mode & 2) train_bwd_sum_kernel<<<dim3(1, n), 32, 0, strm>>>(a);
+    g_launches += 1 + (mode & 1) + ((mode & 2) >> 1);
     return cudaGetLastError() == cudaSuccess ? APSM_OK : APSM_ERR_CUDA;
 }
 
@@ -1117,7 +1198,7 @@ apsm_status apsm_train_backward(const apsm_params *p, const float *rx_pilot, con
                                 const float *clin0, const float *dgamma, const float *dclin, float *dscalars,
                                 float *dclin0, void *workspace, size_t workspace_bytes, void *stream) {
     return train_bwd_run(p, 1, rx_pilot, sym_pilot, P, clin0, dgamma, dclin, dscalars, dclin0, workspace,
-                         workspace_bytes, stream);
+                         workspace_bytes, stream, 3);
 }
 
 apsm_status apsm_train_backward_batched(const apsm_params *p, int32_t n, const float *rx_pilot, const float *sym_pilot,
@@ -1125,7 +1206,22 @@ apsm_status apsm_train_backward_batched(const apsm_params *p, int32_t n, const f
                                         float *dscalars, float *dclin0, void *workspace, size_t workspace_bytes,
                                         void *stream) {
     return train_bwd_run(p, n, rx_pilot, sym_pilot, P, clin0, dgamma, dclin, dscalars, dclin0, workspace,
-                         workspace_bytes, stream);
+                         workspace_bytes, stream, 3);
+}
+
+apsm_status apsm_train_backward_batched_forward(const apsm_params *p, int32_t n, const float *rx_pilot,
+                                                const float *sym_pilot, int32_t P, const float *clin0,
+                                                void *workspace, size_t workspace_bytes, void *stream) {
+    return train_bwd_run(p, n, rx_pilot, sym_pilot, P, clin0, nullptr, nullptr, nullptr, nullptr, workspace,
+                         workspace_bytes, stream, 1);
+}
+
+apsm_status apsm_train_backward_batched_reverse(const apsm_params *p, int32_t n, const float *rx_pilot, int32_t P,
+                                                const float *dgamma, const float *dclin, float *dscalars,
+                                                float *dclin0, void *workspace, size_t workspace_bytes,
+                                                void *stream) {
+    return train_bwd_run(p, n, rx_pilot, nullptr, P, nullptr, dgamma, dclin, dscalars, dclin0, workspace,
+                         workspace_bytes, stream, 2);
 }
 
 }  // extern "C"

@@ -3,6 +3,8 @@ mu, eps, w_L and the initial linear filter, through training (reverse sweep of t
 detection, against FP64 central finite differences of the oracle.  A finite difference is used
 only where no branch of Eq. beta flips between the two perturbed runs (the loss has kinks
 there); the number of usable checks is asserted."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -124,7 +126,8 @@ def test_grad_batch_equals_instances_one_at_a_time():
                                         (4, 2, 60, 40, 21)])
 def test_train_backward_batched_equals_single_calls(M, K, P, W, D):
     """apsm_train_backward_batched (one launch per kernel over users x instances) gives each
-    instance's gradients bit for bit as its own apsm_train_backward call (FIFO eviction included;
+    instance's gradients bit for bit as its own apsm_train_backward call, and so does the two-call
+    form (forward part, then reverse sweep, on one workspace) (FIFO eviction included;
     2D = W + 1 in two cases; W = 32 is the widest window of the warp-per-user form, W = 40 runs the
     CTA-per-user form)."""
     n = 5
@@ -138,6 +141,12 @@ def test_train_backward_batched_equals_single_calls(M, K, P, W, D):
     dc = (0.1 * torch.randn((n, M, K), dtype=torch.complex64, generator=g)).cuda()
     c0 = (0.05 * torch.randn((n, M, K), dtype=torch.complex64, generator=g)).cuda()
     ds, dc0 = apsm.train_backward_batched(p, rp, sp, dg, dc, clin0=c0)
+    nb = ctypes.c_size_t()
+    apsm.load_library().apsm_train_backward_batched_workspace_bytes(ctypes.byref(p.c()), P, n, ctypes.byref(nb))
+    ws = torch.empty((nb.value,), dtype=torch.uint8, device="cuda")
+    apsm.train_backward_batched_forward(p, rp, sp, ws, clin0=c0)  # the two-call form
+    ds2, dc02 = apsm.train_backward_batched_reverse(p, rp, dg, dc, ws)
+    assert torch.equal(ds2, ds) and torch.equal(dc02, dc0)
     for i in range(n):
         ds1, dc01 = apsm.train_backward(p, rp[i], sp[i], dg[i], dc[i], clin0=c0[i])
         assert torch.equal(ds[i], ds1) and torch.equal(dc0[i], dc01), i
