@@ -660,3 +660,19 @@ def test_detect_right_behind_training_on_a_fresh_state(M, K, P, D, engine):
             assert torch.equal(soft, ref) and torch.equal(hard, ref_h)
     finally:
         apsm.tune_clear()
+
+
+@pytest.mark.parametrize("balanced", [False, True])
+def test_train_detect_host_equals_device_calls(balanced):
+    """train_detect_host (host buffers in and out) gives the device path's soft and hard outputs
+    bit for bit, in the plain and the balanced detection form."""
+    M, K, P, W, D, N = 16, 6, 200, 16, 200, 5000
+    inst = synth.make_instance(M, K, P, N, 10.0, instance=77)
+    p = apsm.Params(M=M, K=K, window=W, dict_cap=D, sigma=0.5, mu=0.5, eps=0.01, w_L=0.5)
+    ws = apsm.detect_workspace(p, N) if balanced else None
+    st = apsm.State(p)
+    apsm.train(p, to_dev(inst.rx_pilot), to_dev(inst.sym_pilot), st)
+    soft_d, hard_d = apsm.detect(p, st, to_dev(inst.rx_data), workspace=ws)
+    hp, hs, hd = (torch.from_numpy(a).pin_memory() for a in (inst.rx_pilot, inst.sym_pilot, inst.rx_data))
+    soft_h, hard_h = apsm.train_detect_host(p, hp, hs, hd, workspace=ws)
+    assert torch.equal(soft_h, soft_d.cpu()) and torch.equal(hard_h, hard_d.cpu())
