@@ -655,11 +655,11 @@ __device__ __forceinline__ void band_store_w(const BandPf &b, float *kg, float *
     }
 }
 
-// floats of one warp's region: gamma / R [S], kg, kd, kl [(W+1)^2], xw [(W+1)][2M], py, pd, pw,
-// pb, ca, cb [W], w / wbar [2M]
+// floats of one warp's region: gamma / R [S rounded up to 4, zero padded], kg, kd, kl [(W+1)^2],
+// xw [(W+1)][2M], py, pd, pw, pb, ca, cb [W], w / wbar [2M]
 __host__ __device__ inline int bwd_warp_floats(int S, int W, int L2) {
     const int WR = W + 1;
-    return (S + 3 * WR * WR + WR * L2 + 6 * W + L2 + 3) & ~3;
+    return (((S + 3) & ~3) + 3 * WR * WR + WR * L2 + 6 * W + L2 + 3) & ~3;
 }
 
 // WM: a bound on the window (8, 16 or 32) over which the O(W) loops are unrolled, so that their
@@ -671,9 +671,10 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
     constexpr int NQ = WM >= 32 ? 2 : 1;  // band entries per lane (W + 1 <= 32 NQ)
     const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
     const int M = a.M, K = a.K, W = a.W, D = a.D, P = a.P, S = 2 * P, L2 = 2 * M, WR = W + 1;
-    float *nrm = sm;
-    float *gam = nrm + ((S + 3) & ~3) + k * bwd_warp_floats(S, W, L2);
-    float *kg = gam + S, *kd = kg + WR * WR, *kl = kd + WR * WR, *xw = kl + WR * WR;
+    float *nrm = sm, *rk = nrm + ((S + 3) & ~3);  // ||x_j||^2 and 1 / kappa_jj, shared by the users
+    float *gam = rk + ((S + 3) & ~3) + k * bwd_warp_floats(S, W, L2);
+    const int S4 = (S + 3) & ~3;
+    float *kg = gam + S4, *kd = kg + WR * WR, *kl = kd + WR * WR, *xw = kl + WR * WR;
     float *py = xw + WR * L2, *pd = py + W, *pw = pd + W, *pb = pw + W, *ca = pb + W, *cb = ca + W, *w = cb + W;
     Tape *tape = a.tape + (size_t)k * S * W;
     float *snap = a.snap + (size_t)k * (P > D ? P - D : 0) * W;
@@ -698,9 +699,13 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
         return ldg_if(ok, reinterpret_cast<const float *>(a.sym + (ok ? (size_t)(j >> 1) * K + k : 0)) + (j & 1));
     };
 
-    for (int i = threadIdx.x; i < S; i += blockDim.x) nrm[i] = a.ltab[(size_t)i * a.Sp + i];  // ||x_i||^2
-    __syncthreads();  // the only block barrier: nrm is shared by the users
-    for (int i = lane; i < S; i += 32) gam[i] = 0.f;
+    for (int i = threadIdx.x; i < S; i += blockDim.x) {
+        nrm[i] = a.ltab[(size_t)i * a.Sp + i];  // ||x_i||^2
+        const float kap = fmaf(a.wL, nrm[i], a.wG);
+        rk[i] = kap != 0.f ? 1.f / kap : 0.f;
+    }
+    __syncthreads();  // the only block barrier: nrm and rk are shared by the users
+    for (int i = lane; i < S4; i += 32) gam[i] = 0.f;
     for (int m = lane; m < M; m += 32) {
         const float2 c = a.clin0 ? a.clin0[m * K + k] : make_float2(0.f, 0.f);
         w[m] = c.x;
@@ -760,17 +765,31 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
             }
             const int lo = first_centre(jn), lo4 = lo & ~3;
             float y2[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // two chains of sums
+            if (lo == 0) {  // nothing evicted yet: gamma is zero from jn on (padding included)
 #pragma unroll
-            for (int q = 0; q < kPfV; ++q) {
-                const int i0 = lo4 + 4 * (lane + 32 * q);
-                if (i0 < jn) {
-                    const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+                for (int q = 0; q < kPfV; ++q) {
+                    const int i0 = 4 * (lane + 32 * q);
+                    if (i0 < jn) {
+                        const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+                        y2[0] = fmaf(gm.x, pf.g[q].x, fmaf(gm.z, pf.g[q].z, y2[0]));
+                        y2[1] = fmaf(gm.y, pf.g[q].y, fmaf(gm.w, pf.g[q].w, y2[1]));
+                        d2[0] = fmaf(gm.x, pf.d[q].x, fmaf(gm.z, pf.d[q].z, d2[0]));
+                        d2[1] = fmaf(gm.y, pf.d[q].y, fmaf(gm.w, pf.d[q].w, d2[1]));
+                    }
+                }
+            } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int i = i0 + e;
-                        if (i >= lo && i < jn) {
-                            y2[e & 1] = fmaf(f4(gm, e), f4(pf.g[q], e), y2[e & 1]);
-                            d2[e & 1] = fmaf(f4(gm, e), f4(pf.d[q], e), d2[e & 1]);
+                for (int q = 0; q < kPfV; ++q) {
+                    const int i0 = lo4 + 4 * (lane + 32 * q);
+                    if (i0 < jn) {
+                        const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int i = i0 + e;
+                            if (i >= lo && i < jn) {
+                                y2[e & 1] = fmaf(f4(gm, e), f4(pf.g[q], e), y2[e & 1]);
+                                d2[e & 1] = fmaf(f4(gm, e), f4(pf.d[q], e), d2[e & 1]);
+                            }
                         }
                     }
                 }
@@ -794,11 +813,11 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
             const float dw = pw[r], yg = py[r], gd = pd[r];
             const float y = fmaf(a.wL, dw, a.wG * yg);
             const float e = y - pb[r];
-            const float kap = fmaf(a.wL, nrm[j], a.wG);
+            const float kap = fmaf(a.wL, nrm[j], a.wG), r_k = rk[j];
             float beta = 0.f, s = 0.f;
             if (kap != 0.f) {
-                if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
-                else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
+                if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) * r_k; }
+                else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) * r_k; }
             }
             tape[(size_t)n * W + lane] = Tape{beta, s, kap, dw, yg, gd};
             ca[lane] = mq * beta;
@@ -878,7 +897,7 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
         }
     }
     __syncwarp();
-    for (int i = lane; i < S; i += 32) gam[i] = 0.f;  // R
+    for (int i = lane; i < S4; i += 32) gam[i] = 0.f;  // R
     for (int m = lane; m < M; m += 32) {
         const float2 d = a.dclin[m * K + k];
         w[m] = d.x;
@@ -887,7 +906,9 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
     const int alive0 = max(0, P - D);
     auto final_at = [&](int j) {
         const bool ok = j >= 0 && (j >> 1) >= alive0;
-        return ldg_if(ok, a.dgamma + (ok ? ((size_t)((j >> 1) % D) * 2 + (j & 1)) * K + k : 0));
+        int t = j >> 1;  // its ring slot: t mod D (t < D unless entries were evicted)
+        if (P > D) t %= D;
+        return ldg_if(ok, a.dgamma + (ok ? ((size_t)t * 2 + (j & 1)) * K + k : 0));
     };
     auto pull_hi = [&](int n) {
         const int e = evict_step(n - W);
@@ -947,17 +968,29 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
             const float *grow = a.gtab + (size_t)je * a.Sp;
             const int lo4 = lo & ~3;
             float g2[2] = {0.f, 0.f};
+            if (hi == S && s_lo >= S) {  // no eviction after the entrant: R is zero below lo and past S
 #pragma unroll
-            for (int qq = 0; qq < kPfV; ++qq) {
-                const int i0 = lo4 + 4 * (lane + 32 * qq);
-                if (i0 < hi) {
-                    const float4 rm = *reinterpret_cast<const float4 *>(gam + i0);
+                for (int qq = 0; qq < kPfV; ++qq) {
+                    const int i0 = lo4 + 4 * (lane + 32 * qq);
+                    if (i0 < hi) {
+                        const float4 rm = *reinterpret_cast<const float4 *>(gam + i0);
+                        g2[0] = fmaf(rm.x, pf.g[qq].x, fmaf(rm.z, pf.g[qq].z, g2[0]));
+                        g2[1] = fmaf(rm.y, pf.g[qq].y, fmaf(rm.w, pf.g[qq].w, g2[1]));
+                    }
+                }
+            } else {
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int i = i0 + e;
-                        if (i >= lo && i < hi) {
-                            const float r = i >= s_lo ? f4(rm, e) - sv[i - s_lo] : f4(rm, e);
-                            g2[e & 1] = fmaf(r, f4(pf.g[qq], e), g2[e & 1]);
+                for (int qq = 0; qq < kPfV; ++qq) {
+                    const int i0 = lo4 + 4 * (lane + 32 * qq);
+                    if (i0 < hi) {
+                        const float4 rm = *reinterpret_cast<const float4 *>(gam + i0);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int i = i0 + e;
+                            if (i >= lo && i < hi) {
+                                const float r = i >= s_lo ? f4(rm, e) - sv[i - s_lo] : f4(rm, e);
+                                g2[e & 1] = fmaf(r, f4(pf.g[qq], e), g2[e & 1]);
+                            }
                         }
                     }
                 }
@@ -978,7 +1011,7 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
             const float bbar = a.mu * q * ab;
             float cwo = 0.f, cgo = 0.f;
             if (tp.s != 0.f) {
-                const float ybar = -bbar / tp.kappa;
+                const float ybar = -bbar * rk[j];
                 eps_bar += tp.s * ybar;
                 wl_bar += (ybar * tp.beta) * (nrm[j] - 1.f);
                 wl_bar += ybar * (tp.dotw - tp.gauss);
@@ -1110,7 +1143,7 @@ apsm_status train_bwd_run(const apsm_params *p, int n, const float *rx_pilot, co
     const size_t smem = train_bwd_smem(p->M, p->window, P);
     // one warp per user when the window fits the lanes and every user's rings fit one CTA
     const size_t smem_w =
-        sizeof(float) * ((size_t)((2 * P + 3) & ~3) + (size_t)p->K * bwd_warp_floats(2 * P, p->window, 2 * p->M));
+        sizeof(float) * (2 * (size_t)((2 * P + 3) & ~3) + (size_t)p->K * bwd_warp_floats(2 * P, p->window, 2 * p->M));
     const bool warp_form = p->window <= 32 && smem_w <= 227 * 1024;
     if (!warp_form && smem > 227 * 1024) return APSM_ERR_UNSUPPORTED;
     int dev = 0;
