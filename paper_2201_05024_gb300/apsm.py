@@ -556,7 +556,15 @@ class GradBatch:
         self.clin0 = clin0
         self.states, self.buf = [], []
         Ps = {int(x[0].shape[0]) for x in self.inst}
+        Ns = {int(x[2].shape[0]) for x in self.inst}
         self.batched = backward and len(Ps) == 1
+        # equal data counts: one batched loss (soft, dsoft and targets as [n][N][K] arrays)
+        self.batched_loss = self.batched and len(Ns) == 1
+        if self.batched_loss:
+            N0 = next(iter(Ns))
+            self.soft_all = torch.empty((n, N0, p.K), dtype=torch.complex64, device=dev)
+            self.dsoft_all = torch.empty_like(self.soft_all)
+            self.sd_all = torch.empty_like(self.soft_all)
         A = dict_alloc(p)
         self.dgamma = torch.empty((n, A, 2, p.K), dtype=torch.float32, device=dev)
         self.dclin = torch.empty((n, p.M, p.K), dtype=torch.complex64, device=dev)
@@ -585,8 +593,9 @@ class GradBatch:
                 ws_t=torch.empty((max(nb_t.value, 1),), dtype=torch.uint8, device=dev),
                 ws_d=torch.empty((max(nb_d.value, 1),), dtype=torch.uint8, device=dev),
                 ws_b=None if self.batched else torch.empty((max(nb_b.value, 1),), dtype=torch.uint8, device=dev),
-                soft=torch.empty((N, p.K), dtype=torch.complex64, device=dev),
-                dsoft=torch.empty((N, p.K), dtype=torch.complex64, device=dev),
+                soft=self.soft_all[i] if self.batched_loss else torch.empty((N, p.K), dtype=torch.complex64, device=dev),
+                dsoft=self.dsoft_all[i] if self.batched_loss else torch.empty((N, p.K), dtype=torch.complex64,
+                                                                              device=dev),
                 dgamma=self.dgamma[i], dclin=self.dclin[i], dsd=self.dsd[i]))
         self.loss = torch.zeros((n,), dtype=torch.float32, device=dev)
         self.dst = torch.zeros((n, 4), dtype=torch.float32, device=dev)
@@ -604,20 +613,24 @@ class GradBatch:
                 self._run()
             self.graph = g
 
-    def _instance(self, i):
+    def _instance(self, i, part=3):
+        """part 1: train and detect; part 2: loss (unless batched), detection adjoint and (unless
+        batched) training adjoint; 3: both."""
         lib = load_library()
         p, (rp, sp, rd, sd), st, b = self.p, self.inst[i], self.states[i], self.buf[i]
         P, N = int(rp.shape[0]), int(rd.shape[0])
         c, strm = st.c(), _stream()
-        _check(lib.apsm_train(ctypes.byref(p.c()), _ptr(rp), _ptr(sp), P, _ptr(self.clin0), ctypes.byref(c),
-                              _ptr(b["ws_t"]), b["ws_t"].numel(), None, strm), "apsm_train")
-        _check(lib.apsm_detect(ctypes.byref(p.c()), ctypes.byref(c), _ptr(rd), N, _ptr(b["soft"]), None, strm),
-               "apsm_detect")
-        if not self.backward:
+        if part & 1:
+            _check(lib.apsm_train(ctypes.byref(p.c()), _ptr(rp), _ptr(sp), P, _ptr(self.clin0), ctypes.byref(c),
+                                  _ptr(b["ws_t"]), b["ws_t"].numel(), None, strm), "apsm_train")
+            _check(lib.apsm_detect(ctypes.byref(p.c()), ctypes.byref(c), _ptr(rd), N, _ptr(b["soft"]), None, strm),
+                   "apsm_detect")
+        if not self.backward or not part & 2:
             return
-        torch.sub(b["soft"], sd, out=b["dsoft"])
-        self.loss[i] = b["dsoft"].abs().square().sum()
-        b["dsoft"].mul_(2.0)
+        if not self.batched_loss:
+            torch.sub(b["soft"], sd, out=b["dsoft"])
+            self.loss[i] = b["dsoft"].abs().square().sum()
+            b["dsoft"].mul_(2.0)
         _check(lib.apsm_detect_backward(ctypes.byref(p.c()), ctypes.byref(c), _ptr(rd), N, _ptr(b["dsoft"]),
                                         _ptr(b["dgamma"]), _ptr(b["dclin"]), _ptr(b["dsd"]), _ptr(b["ws_d"]),
                                         b["ws_d"].numel(), strm), "apsm_detect_backward")
@@ -656,10 +669,22 @@ class GradBatch:
             for (lo, hi), bs in zip(self.chunks, self.bstreams):
                 with torch.cuda.stream(bs):
                     self._chunk_forward(lo, hi)
+            if self.batched_loss:  # train and detect everywhere, then one loss for all instances
+                torch.stack([x[3] for x in self.inst], out=self.sd_all)
+                for i in range(len(self.inst)):
+                    with torch.cuda.stream(self.streams[i % self.lanes]):
+                        self._instance(i, 1)
+                for s in self.streams:
+                    main.wait_stream(s)
+                torch.sub(self.soft_all, self.sd_all, out=self.dsoft_all)
+                self.loss.copy_(self.dsoft_all.abs().square().sum(dim=(1, 2)))
+                self.dsoft_all.mul_(2.0)
+                for s in self.streams:
+                    s.wait_stream(main)
             for (lo, hi), bs in zip(self.chunks, self.bstreams):
                 for i in range(lo, hi):
                     with torch.cuda.stream(self.streams[i % self.lanes]):
-                        self._instance(i)
+                        self._instance(i, 2 if self.batched_loss else 3)
                 for i in range(lo, hi):
                     bs.wait_stream(self.streams[i % self.lanes])
                 with torch.cuda.stream(bs):
