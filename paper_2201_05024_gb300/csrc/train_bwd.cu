@@ -71,7 +71,9 @@ struct TrainBwdArgs {
 // The arguments of instance i (blockIdx.y of every launch below).
 __device__ __forceinline__ TrainBwdArgs for_instance(const TrainBwdArgs &a0, int i) {
     TrainBwdArgs a = a0;
-    auto adv = [&](auto *ptr) { return reinterpret_cast<decltype(ptr)>(reinterpret_cast<unsigned char *>(ptr) + i * a0.ws_stride); };
+    auto adv = [&](auto *ptr) {
+        return reinterpret_cast<decltype(ptr)>(reinterpret_cast<unsigned char *>(ptr) + i * a0.ws_stride);
+    };
     a.rx += i * a.st_rx;
     a.sym += i * a.st_sym;
     if (a.clin0) a.clin0 += i * a.st_clin0;
@@ -283,135 +285,135 @@ __global__ void __launch_bounds__(kBwdThreads, 6) train_bwd_kernel(const TrainBw
     BandPf bp;
     float xn = 0.f;
     if (a.mode & 1) {
-    sW = pmod(-W - 1, W);
-    sR = pmod(-W - 1, WR);
-    band_fetch(bp, a, S, W, 0, -W);
-    band_store(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W));
-    band_fetch(bp, a, S, W, 1, 1 - W);
-    if (S > 1) row_fetch(pf, a.gtab + a.Sp, a.gdtab + a.Sp, first_centre(1), 1);
-    if (tid < L2) xw[slotR(0, 0) * L2 + tid] = xcomp(a.rx, M, 0, tid);
-    xn = xc(1);
-    float bn = target_at(tid == T - 1 && S > 1, 1);  // the target of the next arrival, a step early
-    if (tid == 0) pb[0] = target_at(true, 0);
-    __syncthreads();
+        sW = pmod(-W - 1, W);
+        sR = pmod(-W - 1, WR);
+        band_fetch(bp, a, S, W, 0, -W);
+        band_store(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W));
+        band_fetch(bp, a, S, W, 1, 1 - W);
+        if (S > 1) row_fetch(pf, a.gtab + a.Sp, a.gdtab + a.Sp, first_centre(1), 1);
+        if (tid < L2) xw[slotR(0, 0) * L2 + tid] = xcomp(a.rx, M, 0, tid);
+        xn = xc(1);
+        float bn = target_at(tid == T - 1 && S > 1, 1);  // the target of the next arrival, a step early
+        if (tid == 0) pb[0] = target_at(true, 0);
+        __syncthreads();
 
-    // ---- forward: sample 0 arrives with no live centre --------------------------------------------
-    reduce3(0.f, 0.f, tid < L2 ? w[tid] * xw[slotR(0, 0) * L2 + tid] : 0.f);
-    __syncthreads();
-    if (tid == 0) {
-        py[0] = 0.f;
-        pd[0] = 0.f;
-        pw[0] = total(2);
-    }
-    __syncthreads();
-    for (int n = 0; n < S; ++n, sW = ring_slot(sW, 1, W), sR = ring_slot(sR, 1, WR)) {
-        const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, jn = n + 1;
-        const float mq = nJ == W ? mqW : a.mu / (float)nJ;
-        const float b_jn = bn;
-        if (warp == NW - 1) bn = target_at(tid == T - 1 && jn + 1 < S, jn + 1);
-        // the next sample's prediction from the live centres, before this step's update
-        if (jn < S) {
-            if (tid <= W) {
-                band_store(bp, kg, kd, kl, S, W, jn, jn - W, slotR(n, jn), slotR(n, jn - W));
-                band_fetch(bp, a, S, W, jn + 1, jn + 1 - W);
-            }
-            float ws = 0.f;
-            if (tid < L2) {
-                const float x = xsign(jn, xn);
-                xw[slotR(n, jn) * L2 + tid] = x;
-                ws = w[tid] * x;
-                xn = xc(jn + 1);
-            }
-            const int lo = first_centre(jn);
-            const float *grow = a.gtab + (size_t)jn * a.Sp, *drow = a.gdtab + (size_t)jn * a.Sp;
-            float ys = 0.f, ds = 0.f;
+        // ---- forward: sample 0 arrives with no live centre --------------------------------------------
+        reduce3(0.f, 0.f, tid < L2 ? w[tid] * xw[slotR(0, 0) * L2 + tid] : 0.f);
+        __syncthreads();
+        if (tid == 0) {
+            py[0] = 0.f;
+            pd[0] = 0.f;
+            pw[0] = total(2);
+        }
+        __syncthreads();
+        for (int n = 0; n < S; ++n, sW = ring_slot(sW, 1, W), sR = ring_slot(sR, 1, WR)) {
+            const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, jn = n + 1;
+            const float mq = nJ == W ? mqW : a.mu / (float)nJ;
+            const float b_jn = bn;
+            if (warp == NW - 1) bn = target_at(tid == T - 1 && jn + 1 < S, jn + 1);
+            // the next sample's prediction from the live centres, before this step's update
+            if (jn < S) {
+                if (tid <= W) {
+                    band_store(bp, kg, kd, kl, S, W, jn, jn - W, slotR(n, jn), slotR(n, jn - W));
+                    band_fetch(bp, a, S, W, jn + 1, jn + 1 - W);
+                }
+                float ws = 0.f;
+                if (tid < L2) {
+                    const float x = xsign(jn, xn);
+                    xw[slotR(n, jn) * L2 + tid] = x;
+                    ws = w[tid] * x;
+                    xn = xc(jn + 1);
+                }
+                const int lo = first_centre(jn);
+                const float *grow = a.gtab + (size_t)jn * a.Sp, *drow = a.gdtab + (size_t)jn * a.Sp;
+                float ys = 0.f, ds = 0.f;
 #pragma unroll
-            for (int q = 0; q < kPf; ++q) {
-                const int i = lo + tid + q * T;
-                if (i < jn) {
-                    ys = fmaf(gam[i], pf.g[q], ys);
-                    ds = fmaf(gam[i], pf.d[q], ds);
+                for (int q = 0; q < kPf; ++q) {
+                    const int i = lo + tid + q * T;
+                    if (i < jn) {
+                        ys = fmaf(gam[i], pf.g[q], ys);
+                        ds = fmaf(gam[i], pf.d[q], ds);
+                    }
                 }
+                for (int i = lo + tid + kPf * T; i < jn; i += T) {
+                    ys = fmaf(gam[i], __ldg(grow + i), ys);
+                    ds = fmaf(gam[i], __ldg(drow + i), ds);
+                }
+                reduce3(ys, ds, ws);
+                if (jn + 1 < S)
+                    row_fetch(pf, a.gtab + (size_t)(jn + 1) * a.Sp, a.gdtab + (size_t)(jn + 1) * a.Sp,
+                              first_centre(jn + 1), jn + 1);
             }
-            for (int i = lo + tid + kPf * T; i < jn; i += T) {
-                ys = fmaf(gam[i], __ldg(grow + i), ys);
-                ds = fmaf(gam[i], __ldg(drow + i), ds);
+            // the window's projections (Eq. beta), all from f_n
+            if (tid < nJ) {
+                const int j = jlo + tid, r = slotW(n, j);
+                const float dw = pw[r], yg = py[r], gd = pd[r];
+                const float y = fmaf(a.wL, dw, a.wG * yg);
+                const float e = y - pb[r];
+                const float kap = fmaf(a.wL, nrm[j], a.wG);
+                float beta = 0.f, s = 0.f;
+                if (kap != 0.f) {
+                    if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
+                    else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
+                }
+                tape[(size_t)n * W + tid] = Tape{beta, s, kap, dw, yg, gd};
+                ca[tid] = mq * beta;
+                cb[tid] = gam[j] + mq * beta;  // the coefficient after the step
             }
-            reduce3(ys, ds, ws);
-            if (jn + 1 < S)
-                row_fetch(pf, a.gtab + (size_t)(jn + 1) * a.Sp, a.gdtab + (size_t)(jn + 1) * a.Sp, first_centre(jn + 1),
-                          jn + 1);
-        }
-        // the window's projections (Eq. beta), all from f_n
-        if (tid < nJ) {
-            const int j = jlo + tid, r = slotW(n, j);
-            const float dw = pw[r], yg = py[r], gd = pd[r];
-            const float y = fmaf(a.wL, dw, a.wG * yg);
-            const float e = y - pb[r];
-            const float kap = fmaf(a.wL, nrm[j], a.wG);
-            float beta = 0.f, s = 0.f;
-            if (kap != 0.f) {
-                if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) / kap; }
-                else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) / kap; }
-            }
-            tape[(size_t)n * W + tid] = Tape{beta, s, kap, dw, yg, gd};
-            ca[tid] = mq * beta;
-            cb[tid] = gam[j] + mq * beta;  // the coefficient after the step
-        }
-        __syncthreads();
-        // Eq. apsm: coefficients, linear part, and the carried predictions of J_{n+1}.  With
-        // 2D = W + 1 the oldest centre of J_n leaves before step n+1: the arrival jn takes no term
-        // of it, and the other samples drop its coefficient after this step's update.
-        if (tid < nJ) gam[jlo + tid] = cb[tid];
-        if (tid == T - 1 && jn < S) pb[slotW(n, jn)] = b_jn;
-        const int t_lo = max(0, n - W + 2), n_t = jn < S ? jn - t_lo + 1 : 0;
-        const int e_lo = first_centre(n), e_hi = jn < S ? first_centre(jn) : e_lo;  // leave before step n+1
-        const int s_lo = slotR(n, jlo);
-        for (int u = tid; u < L2 + n_t; u += T) {
-            if (u < L2) {
-                float acc = w[u];
-                int si = s_lo;
+            __syncthreads();
+            // Eq. apsm: coefficients, linear part, and the carried predictions of J_{n+1}.  With
+            // 2D = W + 1 the oldest centre of J_n leaves before step n+1: the arrival jn takes no term
+            // of it, and the other samples drop its coefficient after this step's update.
+            if (tid < nJ) gam[jlo + tid] = cb[tid];
+            if (tid == T - 1 && jn < S) pb[slotW(n, jn)] = b_jn;
+            const int t_lo = max(0, n - W + 2), n_t = jn < S ? jn - t_lo + 1 : 0;
+            const int e_lo = first_centre(n), e_hi = jn < S ? first_centre(jn) : e_lo;  // leave before step n+1
+            const int s_lo = slotR(n, jlo);
+            for (int u = tid; u < L2 + n_t; u += T) {
+                if (u < L2) {
+                    float acc = w[u];
+                    int si = s_lo;
 #pragma unroll 4
-                for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) acc = fmaf(ca[o], xw[si * L2 + u], acc);
-                w[u] = acc;
-            } else {
-                const int j = t_lo + (u - L2), r = slotW(n, j), sj = slotR(n, j) * WR;
-                float ay, ad, aw;
-                if (j == jn) {
-                    ay = total(0);
-                    ad = total(1);
-                    aw = total(2);
+                    for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) acc = fmaf(ca[o], xw[si * L2 + u], acc);
+                    w[u] = acc;
                 } else {
-                    ay = py[r];
-                    ad = pd[r];
-                    aw = pw[r];
-                }
-                const int o_lo = j == jn ? max(0, e_hi - jlo) : 0;  // sources still live at jn
-                int si = s_lo;
+                    const int j = t_lo + (u - L2), r = slotW(n, j), sj = slotR(n, j) * WR;
+                    float ay, ad, aw;
+                    if (j == jn) {
+                        ay = total(0);
+                        ad = total(1);
+                        aw = total(2);
+                    } else {
+                        ay = py[r];
+                        ad = pd[r];
+                        aw = pw[r];
+                    }
+                    const int o_lo = j == jn ? max(0, e_hi - jlo) : 0;  // sources still live at jn
+                    int si = s_lo;
 #pragma unroll 4
-                for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) {
-                    const float c = ca[o];
-                    aw = fmaf(c, kl[sj + si], aw);
-                    if (o >= o_lo) {
-                        ay = fmaf(c, kg[sj + si], ay);
-                        ad = fmaf(c, kd[sj + si], ad);
+                    for (int o = 0; o < nJ; ++o, si = ring_slot(si, 1, WR)) {
+                        const float c = ca[o];
+                        aw = fmaf(c, kl[sj + si], aw);
+                        if (o >= o_lo) {
+                            ay = fmaf(c, kg[sj + si], ay);
+                            ad = fmaf(c, kd[sj + si], ad);
+                        }
                     }
-                }
-                if (j != jn) {
-                    const float *grow = a.gtab + (size_t)j * a.Sp, *drow = a.gdtab + (size_t)j * a.Sp;
-                    for (int i = e_lo; i < e_hi; ++i) {  // centres leaving before step n+1
-                        const float gi = i >= jlo ? cb[i - jlo] : gam[i];
-                        ay = fmaf(-gi, __ldg(grow + i), ay);
-                        ad = fmaf(-gi, __ldg(drow + i), ad);
+                    if (j != jn) {
+                        const float *grow = a.gtab + (size_t)j * a.Sp, *drow = a.gdtab + (size_t)j * a.Sp;
+                        for (int i = e_lo; i < e_hi; ++i) {  // centres leaving before step n+1
+                            const float gi = i >= jlo ? cb[i - jlo] : gam[i];
+                            ay = fmaf(-gi, __ldg(grow + i), ay);
+                            ad = fmaf(-gi, __ldg(drow + i), ad);
+                        }
                     }
+                    py[r] = ay;
+                    pd[r] = ad;
+                    pw[r] = aw;
                 }
-                py[r] = ay;
-                pd[r] = ad;
-                pw[r] = aw;
             }
+            __syncthreads();
         }
-        __syncthreads();
-    }
 
     }  // forward
     if (!(a.mode & 2)) return;
@@ -715,168 +717,168 @@ __global__ void __launch_bounds__(32 * kWarpUsersMax) train_bwd_warp_kernel(cons
     BandPf bp;
     float xn[4];
     if (a.mode & 1) {
-    sW = pmod(-W - 1, W);
-    sR = pmod(-W - 1, WR);
-    band_fetch_w<NQ>(bp, a, S, W, 0, -W, lane);
-    band_store_w<NQ>(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W), lane);
-    band_fetch_w<NQ>(bp, a, S, W, 1, 1 - W, lane);
-    if (S > 1) row_fetch_w(pf, a.gtab + a.Sp, a.gdtab + a.Sp, first_centre(1), 1, lane);
+        sW = pmod(-W - 1, W);
+        sR = pmod(-W - 1, WR);
+        band_fetch_w<NQ>(bp, a, S, W, 0, -W, lane);
+        band_store_w<NQ>(bp, kg, kd, kl, S, W, 0, -W, slotR(0, 0), slotR(0, -W), lane);
+        band_fetch_w<NQ>(bp, a, S, W, 1, 1 - W, lane);
+        if (S > 1) row_fetch_w(pf, a.gtab + a.Sp, a.gdtab + a.Sp, first_centre(1), 1, lane);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int m = lane + 32 * c;
-        if (m < L2) xw[slotR(0, 0) * L2 + m] = xcomp(a.rx, M, 0, m);
-        xn[c] = xc(1, m);
-    }
-    float bn = target_at(lane == 0 && S > 1, 1);  // the next arrival's target, a step early
-    if (lane == 0) pb[0] = target_at(true, 0);
-    __syncwarp();
-    {
-        float ws = 0.f;
-        for (int m = lane; m < L2; m += 32) ws = fmaf(w[m], xw[slotR(0, 0) * L2 + m], ws);
-        ws = warp_sum(ws);
-        if (lane == 0) {
-            py[0] = 0.f;
-            pd[0] = 0.f;
-            pw[0] = ws;
+        for (int c = 0; c < 4; ++c) {
+            const int m = lane + 32 * c;
+            if (m < L2) xw[slotR(0, 0) * L2 + m] = xcomp(a.rx, M, 0, m);
+            xn[c] = xc(1, m);
         }
-    }
-    __syncwarp();
-
-    // ---- forward ---------------------------------------------------------------------------------------
-    for (int n = 0; n < S; ++n, sW = ring_slot(sW, 1, W), sR = ring_slot(sR, 1, WR)) {
-        const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, jn = n + 1;
-        const float mq = nJ == W ? mqW : a.mu / (float)nJ;
-        const float b_jn = bn;
-        bn = target_at(lane == 0 && jn + 1 < S, jn + 1);
-        float ys = 0.f, ds = 0.f, ws = 0.f;  // the arrival's sums from the state before this step
-        if (jn < S) {
-            band_store_w<NQ>(bp, kg, kd, kl, S, W, jn, jn - W, slotR(n, jn), slotR(n, jn - W), lane);
-            band_fetch_w<NQ>(bp, a, S, W, jn + 1, jn + 1 - W, lane);
-            const int sx = slotR(n, jn) * L2;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int m = lane + 32 * c;
-                if (m < L2) {
-                    const float x = xsign(jn, m, xn[c]);
-                    xw[sx + m] = x;
-                    ws = fmaf(w[m], x, ws);
-                    xn[c] = xc(jn + 1, m);
-                }
+        float bn = target_at(lane == 0 && S > 1, 1);  // the next arrival's target, a step early
+        if (lane == 0) pb[0] = target_at(true, 0);
+        __syncwarp();
+        {
+            float ws = 0.f;
+            for (int m = lane; m < L2; m += 32) ws = fmaf(w[m], xw[slotR(0, 0) * L2 + m], ws);
+            ws = warp_sum(ws);
+            if (lane == 0) {
+                py[0] = 0.f;
+                pd[0] = 0.f;
+                pw[0] = ws;
             }
-            const int lo = first_centre(jn), lo4 = lo & ~3;
-            float y2[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // two chains of sums
-            if (lo == 0) {  // nothing evicted yet: gamma is zero from jn on (padding included)
+        }
+        __syncwarp();
+
+        // ---- forward ---------------------------------------------------------------------------------------
+        for (int n = 0; n < S; ++n, sW = ring_slot(sW, 1, W), sR = ring_slot(sR, 1, WR)) {
+            const int jlo = max(0, n - W + 1), nJ = n - jlo + 1, jn = n + 1;
+            const float mq = nJ == W ? mqW : a.mu / (float)nJ;
+            const float b_jn = bn;
+            bn = target_at(lane == 0 && jn + 1 < S, jn + 1);
+            float ys = 0.f, ds = 0.f, ws = 0.f;  // the arrival's sums from the state before this step
+            if (jn < S) {
+                band_store_w<NQ>(bp, kg, kd, kl, S, W, jn, jn - W, slotR(n, jn), slotR(n, jn - W), lane);
+                band_fetch_w<NQ>(bp, a, S, W, jn + 1, jn + 1 - W, lane);
+                const int sx = slotR(n, jn) * L2;
 #pragma unroll
-                for (int q = 0; q < kPfV; ++q) {
-                    const int i0 = 4 * (lane + 32 * q);
-                    if (i0 < jn) {
-                        const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
-                        y2[0] = fmaf(gm.x, pf.g[q].x, fmaf(gm.z, pf.g[q].z, y2[0]));
-                        y2[1] = fmaf(gm.y, pf.g[q].y, fmaf(gm.w, pf.g[q].w, y2[1]));
-                        d2[0] = fmaf(gm.x, pf.d[q].x, fmaf(gm.z, pf.d[q].z, d2[0]));
-                        d2[1] = fmaf(gm.y, pf.d[q].y, fmaf(gm.w, pf.d[q].w, d2[1]));
+                for (int c = 0; c < 4; ++c) {
+                    const int m = lane + 32 * c;
+                    if (m < L2) {
+                        const float x = xsign(jn, m, xn[c]);
+                        xw[sx + m] = x;
+                        ws = fmaf(w[m], x, ws);
+                        xn[c] = xc(jn + 1, m);
                     }
                 }
-            } else {
+                const int lo = first_centre(jn), lo4 = lo & ~3;
+                float y2[2] = {0.f, 0.f}, d2[2] = {0.f, 0.f};  // two chains of sums
+                if (lo == 0) {  // nothing evicted yet: gamma is zero from jn on (padding included)
 #pragma unroll
-                for (int q = 0; q < kPfV; ++q) {
-                    const int i0 = lo4 + 4 * (lane + 32 * q);
-                    if (i0 < jn) {
-                        const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+                    for (int q = 0; q < kPfV; ++q) {
+                        const int i0 = 4 * (lane + 32 * q);
+                        if (i0 < jn) {
+                            const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+                            y2[0] = fmaf(gm.x, pf.g[q].x, fmaf(gm.z, pf.g[q].z, y2[0]));
+                            y2[1] = fmaf(gm.y, pf.g[q].y, fmaf(gm.w, pf.g[q].w, y2[1]));
+                            d2[0] = fmaf(gm.x, pf.d[q].x, fmaf(gm.z, pf.d[q].z, d2[0]));
+                            d2[1] = fmaf(gm.y, pf.d[q].y, fmaf(gm.w, pf.d[q].w, d2[1]));
+                        }
+                    }
+                } else {
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int i = i0 + e;
-                            if (i >= lo && i < jn) {
-                                y2[e & 1] = fmaf(f4(gm, e), f4(pf.g[q], e), y2[e & 1]);
-                                d2[e & 1] = fmaf(f4(gm, e), f4(pf.d[q], e), d2[e & 1]);
+                    for (int q = 0; q < kPfV; ++q) {
+                        const int i0 = lo4 + 4 * (lane + 32 * q);
+                        if (i0 < jn) {
+                            const float4 gm = *reinterpret_cast<const float4 *>(gam + i0);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int i = i0 + e;
+                                if (i >= lo && i < jn) {
+                                    y2[e & 1] = fmaf(f4(gm, e), f4(pf.g[q], e), y2[e & 1]);
+                                    d2[e & 1] = fmaf(f4(gm, e), f4(pf.d[q], e), d2[e & 1]);
+                                }
                             }
                         }
                     }
                 }
+                const float *grow = a.gtab + (size_t)jn * a.Sp, *drow = a.gdtab + (size_t)jn * a.Sp;
+                for (int i = max(lo, lo4 + 4 * 32 * kPfV) + lane; i < jn; i += 32) {
+                    y2[0] = fmaf(gam[i], __ldg(grow + i), y2[0]);
+                    d2[0] = fmaf(gam[i], __ldg(drow + i), d2[0]);
+                }
+                ys = y2[0] + y2[1];
+                ds = d2[0] + d2[1];
+                if (jn + 1 < S)
+                    row_fetch_w(pf, a.gtab + (size_t)(jn + 1) * a.Sp, a.gdtab + (size_t)(jn + 1) * a.Sp,
+                                first_centre(jn + 1), jn + 1, lane);
+                ys = warp_sum(ys);
+                ds = warp_sum(ds);
+                ws = warp_sum(ws);
             }
-            const float *grow = a.gtab + (size_t)jn * a.Sp, *drow = a.gdtab + (size_t)jn * a.Sp;
-            for (int i = max(lo, lo4 + 4 * 32 * kPfV) + lane; i < jn; i += 32) {
-                y2[0] = fmaf(gam[i], __ldg(grow + i), y2[0]);
-                d2[0] = fmaf(gam[i], __ldg(drow + i), d2[0]);
+            if (lane < nJ) {  // the window's projections (Eq. beta), all from f_n
+                const int j = jlo + lane, r = slotW(n, j);
+                const float dw = pw[r], yg = py[r], gd = pd[r];
+                const float y = fmaf(a.wL, dw, a.wG * yg);
+                const float e = y - pb[r];
+                const float kap = fmaf(a.wL, nrm[j], a.wG), r_k = rk[j];
+                float beta = 0.f, s = 0.f;
+                if (kap != 0.f) {
+                    if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) * r_k; }
+                    else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) * r_k; }
+                }
+                tape[(size_t)n * W + lane] = Tape{beta, s, kap, dw, yg, gd};
+                ca[lane] = mq * beta;
+                cb[lane] = gam[j] + mq * beta;  // the coefficient after the step
             }
-            ys = y2[0] + y2[1];
-            ds = d2[0] + d2[1];
-            if (jn + 1 < S)
-                row_fetch_w(pf, a.gtab + (size_t)(jn + 1) * a.Sp, a.gdtab + (size_t)(jn + 1) * a.Sp, first_centre(jn + 1),
-                            jn + 1, lane);
-            ys = warp_sum(ys);
-            ds = warp_sum(ds);
-            ws = warp_sum(ws);
-        }
-        if (lane < nJ) {  // the window's projections (Eq. beta), all from f_n
-            const int j = jlo + lane, r = slotW(n, j);
-            const float dw = pw[r], yg = py[r], gd = pd[r];
-            const float y = fmaf(a.wL, dw, a.wG * yg);
-            const float e = y - pb[r];
-            const float kap = fmaf(a.wL, nrm[j], a.wG), r_k = rk[j];
-            float beta = 0.f, s = 0.f;
-            if (kap != 0.f) {
-                if (e < -a.eps) { s = 1.f; beta = (-e - a.eps) * r_k; }
-                else if (e > a.eps) { s = -1.f; beta = (-e + a.eps) * r_k; }
-            }
-            tape[(size_t)n * W + lane] = Tape{beta, s, kap, dw, yg, gd};
-            ca[lane] = mq * beta;
-            cb[lane] = gam[j] + mq * beta;  // the coefficient after the step
-        }
-        __syncwarp();
-        // Eq. apsm: coefficients, linear part, carried predictions of J_{n+1} (2D = W + 1: the oldest
-        // centre of J_n leaves before step n+1)
-        if (lane < nJ) gam[jlo + lane] = cb[lane];
-        if (lane == 0 && jn < S) pb[slotW(n, jn)] = b_jn;
-        const int s_lo = slotR(n, jlo);
-        for (int m = lane; m < L2; m += 32) {
-            float acc = w[m];
+            __syncwarp();
+            // Eq. apsm: coefficients, linear part, carried predictions of J_{n+1} (2D = W + 1: the oldest
+            // centre of J_n leaves before step n+1)
+            if (lane < nJ) gam[jlo + lane] = cb[lane];
+            if (lane == 0 && jn < S) pb[slotW(n, jn)] = b_jn;
+            const int s_lo = slotR(n, jlo);
+            for (int m = lane; m < L2; m += 32) {
+                float acc = w[m];
 #pragma unroll
-            for (int o = 0; o < WM; ++o)
-                if (o < nJ) acc = fmaf(ca[o], xw[wrap(s_lo + o) * L2 + m], acc);
-            w[m] = acc;
-        }
-        const int t_lo = max(0, n - W + 2), n_t = jn < S ? jn - t_lo + 1 : 0;
-        const int e_lo = first_centre(n), e_hi = jn < S ? first_centre(jn) : e_lo;
-        if (lane < n_t) {
-            const int j = t_lo + lane, r = slotW(n, j), sj = slotR(n, j) * WR;
-            float ay, ad, aw;
-            if (j == jn) {
-                ay = ys;
-                ad = ds;
-                aw = ws;
-            } else {
-                ay = py[r];
-                ad = pd[r];
-                aw = pw[r];
+                for (int o = 0; o < WM; ++o)
+                    if (o < nJ) acc = fmaf(ca[o], xw[wrap(s_lo + o) * L2 + m], acc);
+                w[m] = acc;
             }
-            const int o_lo = j == jn ? max(0, e_hi - jlo) : 0;
+            const int t_lo = max(0, n - W + 2), n_t = jn < S ? jn - t_lo + 1 : 0;
+            const int e_lo = first_centre(n), e_hi = jn < S ? first_centre(jn) : e_lo;
+            if (lane < n_t) {
+                const int j = t_lo + lane, r = slotW(n, j), sj = slotR(n, j) * WR;
+                float ay, ad, aw;
+                if (j == jn) {
+                    ay = ys;
+                    ad = ds;
+                    aw = ws;
+                } else {
+                    ay = py[r];
+                    ad = pd[r];
+                    aw = pw[r];
+                }
+                const int o_lo = j == jn ? max(0, e_hi - jlo) : 0;
 #pragma unroll
-            for (int o = 0; o < WM; ++o) {
-                if (o < nJ) {
-                    const int si = sj + wrap(s_lo + o);
-                    const float c = ca[o];
-                    aw = fmaf(c, kl[si], aw);
-                    if (o >= o_lo) {
-                        ay = fmaf(c, kg[si], ay);
-                        ad = fmaf(c, kd[si], ad);
+                for (int o = 0; o < WM; ++o) {
+                    if (o < nJ) {
+                        const int si = sj + wrap(s_lo + o);
+                        const float c = ca[o];
+                        aw = fmaf(c, kl[si], aw);
+                        if (o >= o_lo) {
+                            ay = fmaf(c, kg[si], ay);
+                            ad = fmaf(c, kd[si], ad);
+                        }
                     }
                 }
-            }
-            if (j != jn) {
-                const float *grow = a.gtab + (size_t)j * a.Sp, *drow = a.gdtab + (size_t)j * a.Sp;
-                for (int i = e_lo; i < e_hi; ++i) {
-                    const float gi = i >= jlo ? cb[i - jlo] : gam[i];
-                    ay = fmaf(-gi, __ldg(grow + i), ay);
-                    ad = fmaf(-gi, __ldg(drow + i), ad);
+                if (j != jn) {
+                    const float *grow = a.gtab + (size_t)j * a.Sp, *drow = a.gdtab + (size_t)j * a.Sp;
+                    for (int i = e_lo; i < e_hi; ++i) {
+                        const float gi = i >= jlo ? cb[i - jlo] : gam[i];
+                        ay = fmaf(-gi, __ldg(grow + i), ay);
+                        ad = fmaf(-gi, __ldg(drow + i), ad);
+                    }
                 }
+                py[r] = ay;
+                pd[r] = ad;
+                pw[r] = aw;
             }
-            py[r] = ay;
-            pd[r] = ad;
-            pw[r] = aw;
+            __syncwarp();
         }
-        __syncwarp();
-    }
 
     }  // forward
     if (!(a.mode & 2)) return;
