@@ -150,3 +150,32 @@ def test_train_backward_batched_equals_single_calls(M, K, P, W, D):
     for i in range(n):
         ds1, dc01 = apsm.train_backward(p, rp[i], sp[i], dg[i], dc[i], clin0=c0[i])
         assert torch.equal(ds[i], ds1) and torch.equal(dc0[i], dc01), i
+
+
+@pytest.mark.parametrize("uneven", ["data", "pilots"])
+def test_grad_batch_uneven_instances(uneven):
+    """GradBatch with unequal data counts (batched training adjoints, a loss per instance) or
+    unequal pilot counts (the per-instance training adjoint): every instance's loss and gradients
+    match the instance-at-a-time autograd path."""
+    M, K, W, D = 8, 3, 6, 64
+    shapes = [(70, 300), (70, 200), (70, 257)] if uneven == "data" else [(70, 300), (50, 300), (33, 300)]
+    xs = [synth.make_instance(M, K, P, N, 10.0, instance=960 + i) for i, (P, N) in enumerate(shapes)]
+    data = [(to_dev(x.rx_pilot), to_dev(x.sym_pilot), to_dev(x.rx_data), to_dev(x.sym_data)) for x in xs]
+    p = apsm.Params(M=M, K=K, window=W, dict_cap=D, sigma=0.6, mu=0.7, eps=0.02, w_L=0.4)
+    c0 = torch.zeros((M, K), dtype=torch.complex64, device="cuda")
+    gb = apsm.GradBatch(p, data, c0, lanes=2, graph=True)
+    assert gb.batched == (uneven == "data") and not gb.batched_loss
+    gb.run()
+    torch.cuda.synchronize()
+    for i, (rp, sp, rd, sd) in enumerate(data):
+        cg = c0.clone().requires_grad_(True)
+        th = [torch.tensor(v, dtype=torch.float64, requires_grad=True) for v in (p.sigma, p.mu, p.eps, p.w_L)]
+        soft = apsm.train_detect_autograd(p, rp, sp, rd, cg, *th)
+        loss = (soft - sd).abs().pow(2).sum()
+        loss.backward()
+        lv = float(loss.detach())
+        assert abs(float(gb.loss[i]) - lv) <= 1e-5 * max(1.0, abs(lv))
+        ref = np.array([float(t.grad) for t in th])
+        got = gb.dst[i].double().cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max()), (got, ref)
+        assert (gb.dclin0[i] - cg.grad).abs().max().item() <= 1e-4 * max(1.0, cg.grad.abs().max().item())
