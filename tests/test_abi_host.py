@@ -230,3 +230,41 @@ def test_set_option_validation(lib):
     assert lib.apsm_set_option(0, 0) == apsm.APSM_ERR_INVALID_ARG
     assert lib.apsm_set_option(1, 2) == apsm.APSM_ERR_INVALID_ARG
     assert lib.apsm_set_option(7, 1) == apsm.APSM_ERR_INVALID_ARG
+
+
+def test_train_backward_validation_before_device(lib):
+    """apsm_train_backward and its batched and two-call forms reject bad arguments on the host."""
+    from paper_2201_05024_gb300 import apsm
+    p = params(window=8, dict_cap=256).c()
+    vp = ctypes.c_void_p
+    one, nb = ctypes.c_size_t(), ctypes.c_size_t()
+    assert lib.apsm_train_backward_workspace_bytes(ctypes.byref(p), 256, ctypes.byref(one)) == apsm.APSM_OK
+    assert lib.apsm_train_backward_batched_workspace_bytes(ctypes.byref(p), 256, 5, ctypes.byref(nb)) == apsm.APSM_OK
+    assert one.value > 0 and one.value % 256 == 0 and nb.value == 5 * one.value
+    assert lib.apsm_train_backward_batched_workspace_bytes(ctypes.byref(p), 256, 0, ctypes.byref(nb)) == 1
+    assert lib.apsm_train_backward_batched_workspace_bytes(ctypes.byref(p), -1, 2, ctypes.byref(nb)) == 1
+    assert lib.apsm_train_backward_batched_workspace_bytes(ctypes.byref(p), 256, 2, None) == 1
+    a = vp(256)
+    ws, big = vp(1 << 20), 1 << 40
+
+    def batched(n, rx=a, sym=a, P=256, dg=a, dc=a, ds=a, d0=a, w=ws, wb=big):
+        return lib.apsm_train_backward_batched(ctypes.byref(p), n, rx, sym, P, None, dg, dc, ds, d0, w, wb, None)
+
+    assert batched(0) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(70000) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(2, rx=None) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(2, sym=None) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(2, dg=None) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(2, d0=None) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(2, P=0) == apsm.APSM_ERR_INVALID_ARG
+    assert batched(2, P=9000) == apsm.APSM_ERR_UNSUPPORTED
+    assert batched(2, wb=nb.value // 5) == apsm.APSM_ERR_WORKSPACE      # room for one instance only
+    assert batched(2, w=vp((1 << 20) + 64)) == apsm.APSM_ERR_INVALID_ARG  # not 256-byte aligned
+    # the two-call form checks only what each half uses
+    assert lib.apsm_train_backward_batched_forward(ctypes.byref(p), 2, a, None, 256, None, ws, big, None) == 1
+    assert lib.apsm_train_backward_batched_reverse(ctypes.byref(p), 2, a, 256, None, a, a, a, ws, big, None) == 1
+    assert lib.apsm_train_backward_batched_reverse(ctypes.byref(p), 2, a, 256, a, a, a, a, ws, 16, None) == \
+        apsm.APSM_ERR_WORKSPACE
+    pv = params(window=8, dict_cap=256, weights="violated").c()  # the adjoint covers uniform weights only
+    assert lib.apsm_train_backward(ctypes.byref(pv), a, a, 256, None, a, a, a, a, ws, big, None) == \
+        apsm.APSM_ERR_UNSUPPORTED
